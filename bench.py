@@ -1,0 +1,338 @@
+#!/usr/bin/env python
+"""Throughput of the RKHS-BA hot path on GB300: pair-terms/s for
+loss + gradient + Gauss-Newton blocks, measured on the 8-frame x 20k-point
+LiDAR multi-view registration workload (28 frame pairs, 19-class FP32 label
+distributions, ell = 0.3 m, r_c = 0.9 m), synthetic and seeded.
+
+One step = one pass of the whole hot path over the resident problem:
+grid build of every frame, the evaluation at the initial poses (transform,
+binning, pair kernel, FP64 assembly) and one Levenberg-Marquardt iteration
+(Cholesky solve, SE(3) update, evaluation at the candidate, accept/reject).
+Pair-terms counted are those of the two evaluations of the step.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun every rank runs its own replica (the path shards by problem;
+there is no data-path collective), value = all pair-terms / max rank time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "pair-terms/s for RKHS-BA loss+grad+Hessian; served BA solves/s, p50/p99 latency"
+UNIT = "pair-terms/s"
+WORKLOAD = "lidar_street_8x20000"
+L2_FLUSH_BYTES = 256 << 20
+
+
+def flops_per_pair(sem_dim, color):
+    """Algorithmic FP32 flops of one pair-term (FMA = 2): d (3), |d|^2 (5),
+    exponent (1), label dot (2 D), w = s k (1), sums W, D, Q (1 + 3 + 3 + 12);
+    colour factor adds 9."""
+    return 29 + 2 * sem_dim + (9 if color else 0)
+
+
+def workload():
+    import scenes
+    return scenes.config_problem(2)
+
+
+# ------------------------------------------------------------------ oracle --
+def oracle_sample(kind):
+    """Run the FP64 oracle on a bounded sample of the workload (CPU only)."""
+    import oracle
+    prob = workload()
+    if kind == "baseline":
+        # two full frame pairs (0,1) and (0,2) at the initial poses
+        sub = dict(prob, edges=np.asarray(prob["edges"])[[0, 1]])
+        desc = "edges (0,1),(0,2) of the 8x20k workload at the initial poses"
+    else:
+        # frame pair (0,1), every 4th point of frame 1
+        sub = dict(prob, edges=np.asarray(prob["edges"])[[0]])
+        sub["xyz"] = list(prob["xyz"])
+        sub["sem"] = list(prob["sem"])
+        sub["xyz"][1] = prob["xyz"][1][::4]
+        sub["sem"][1] = prob["sem"][1][::4]
+        desc = "edge (0,1) of the 8x20k workload with every 4th point of frame 1"
+    t0 = time.perf_counter()
+    r = oracle.evaluate(sub, prob["poses0"])
+    dt = time.perf_counter() - t0
+    return dict(pairs=int(r["n_pairs"]), seconds=dt, sample=desc)
+
+
+def run_oracle_subprocess(kind):
+    env = dict(os.environ)
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[v] = "1"
+    env["CUDA_VISIBLE_DEVICES"] = ""
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-sample", kind],
+                       capture_output=True, text=True, env=env, timeout=900)
+    if r.returncode != 0:
+        raise RuntimeError("oracle sample failed: " + r.stderr[-2000:])
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def reference_arm(args, rank):
+    if rank != 0:
+        return
+    env_cores = 1
+    # warm-up steps, then K timed steps, each a bounded sample on 1 host core
+    for _ in range(args.warmup):
+        run_oracle_subprocess("step")
+    tot_pairs, tot_s = 0, 0.0
+    desc = ""
+    for _ in range(args.steps):
+        r = run_oracle_subprocess("step")
+        tot_pairs += r["pairs"]
+        tot_s += r["seconds"]
+        desc = r["sample"]
+    value = tot_pairs / tot_s
+    line = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=args.gpus, steps=args.steps,
+                warmup=args.warmup, ms_per_step=1e3 * tot_s / args.steps, higher_is_better=True,
+                scaling="weak", vs_baseline=None, dtype="f64", data="synthetic",
+                impl="reference",
+                config=dict(workload=WORKLOAD, sample=desc),
+                cpu_baseline=dict(value=value, unit=UNIT, cores=env_cores, kind="oracle",
+                                  sample=desc),
+                e2e=dict(value=value, unit=UNIT, h2d_bytes_per_step=0, d2h_bytes_per_step=0))
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ clocks --
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.proc = None
+        self.index = index
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+        self.t_start = self.t_end = None
+
+    def mark(self, start):
+        if start:
+            self.t_start = time.time()
+        else:
+            self.t_end = time.time()
+
+    def stop(self):
+        if not self.proc:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        rows = []
+        for ln in out.strip().splitlines():
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                rows.append(dict(sm=float(parts[0]), smax=float(parts[1]), reasons=parts[3:]))
+            except ValueError:
+                continue
+        if not rows:
+            return dict(sm_mhz=None, sm_max_mhz=None, reasons=[], samples=0)
+        # samples are ~100 ms apart; keep the ones that show the GPU under load
+        loaded = [r for r in rows if r["sm"] > 0.5 * r["smax"]] or rows
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in loaded for i, v in enumerate(r["reasons"][1:5])
+                          if v.strip().lower() == "active"})
+        return dict(sm_mhz=statistics.median(r["sm"] for r in loaded),
+                    sm_max_mhz=max(r["smax"] for r in rows), reasons=reasons,
+                    samples=len(loaded))
+
+
+# -------------------------------------------------------------------- ours --
+def ours(args, rank, world, local_rank):
+    import torch
+
+    import paper_2403_01254_gb300 as pk
+    from paper_2403_01254_gb300 import rkhsba as rb
+
+    cpu_base = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        # before the first CUDA call: the oracle runs in a fresh process
+        cb = run_oracle_subprocess("baseline")
+        cpu_base = dict(value=cb["pairs"] / cb["seconds"], unit=UNIT, cores=1, kind="oracle",
+                        sample=cb["sample"] + " (%d pair-terms, %.1f s)" % (cb["pairs"], cb["seconds"]))
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    pk.load()
+    prob = workload()
+    K = len(prob["xyz"])
+    sem_dim = prob["sem"][0].shape[1]
+    n_points = np.array([len(x) for x in prob["xyz"]], np.int64)
+    xyz_h = np.ascontiguousarray(np.concatenate(prob["xyz"]))
+    sem_h = np.ascontiguousarray(np.concatenate(prob["sem"]).astype(np.float32))
+    poses0 = np.ascontiguousarray(prob["poses0"].reshape(K * 16))
+    edges = np.asarray(prob["edges"], np.int32)
+    P = prob["params"]
+    params = pk.make_params(P["ell"], P["cutoff_mult"], P["sigma"], 0.0, sem_dim, 0,
+                            max_iters=1000)
+    stream = torch.cuda.Stream(device=dev)
+    xyz_d = torch.from_numpy(xyz_h).to(dev)
+    sem_d = torch.from_numpy(sem_h).to(dev)
+    poses_d = torch.from_numpy(poses0).to(dev)
+    torch.cuda.synchronize()
+    ctx = pk.rkhsba_create_device(n_points, xyz_d.data_ptr(), sem_d.data_ptr(), None, edges, params,
+                                  stream.cuda_stream)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def step():
+        rb.rkhsba_rebuild(ctx)
+        rb.rkhsba_set_poses_device(ctx, poses_d.data_ptr())
+        rb.rkhsba_iterate(ctx, 1)
+
+    with torch.cuda.stream(stream):
+        for _ in range(max(args.warmup, 1)):
+            flush.zero_()
+            step()
+    stream.synchronize()
+    _, st = rb.rkhsba_get_state(ctx, K)
+    pairs_per_step = st["pair_terms"]
+
+    clocks = ClockSampler(local_rank)
+    time.sleep(0.3)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    rb.rkhsba_profile(ctx, 1)
+    n_launch0 = pk.rkhsba_launch_count()
+    clocks.mark(True)
+    with torch.cuda.stream(stream):
+        for k in range(args.steps):
+            flush.zero_()                      # L2 flush between steps, outside the events
+            ev[k][0].record(stream)
+            step()
+            ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    clocks.mark(False)
+    if world > 1:
+        torch.distributed.barrier()
+    n_launch = pk.rkhsba_launch_count() - n_launch0
+    prof = rb.rkhsba_profile(ctx, 0, read=True)
+    clk = clocks.stop()
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    ms_max = float(t.item())
+    total_pairs = pairs_per_step * args.steps * world
+    value = total_pairs / (ms_max / 1e3)
+
+    # roofline of the dominant kernel (the pair kernel): FP32 arithmetic
+    pair_ms, pair_n = prof["pairs"]
+    fl = flops_per_pair(sem_dim, False)
+    achieved = pairs_per_step * args.steps * fl / (pair_ms / 1e3) / 1e12 if pair_ms > 0 else None
+    props = torch.cuda.get_device_properties(dev)
+    sm_max = (clk or {}).get("sm_max_mhz") or 2070.0
+    peak = props.multi_processor_count * 128 * 2 * sm_max * 1e6 / 1e12
+    roofline = dict(bound="alu", achieved=achieved, peak=peak, unit="TFLOP/s",
+                    frac=(achieved / peak) if achieved else None, traffic=None,
+                    kernel="k_pairs", flops_per_pair_term=fl,
+                    peak_basis="%d SMs x 128 FP32 lanes x 2 flop x %.0f MHz" %
+                               (props.multi_processor_count, sm_max),
+                    pair_kernel_ms_per_launch=pair_ms / max(pair_n, 1),
+                    phases_ms_per_step={k: v[0] / args.steps for k, v in prof.items()})
+    rb.rkhsba_destroy(ctx)
+
+    # end to end through the C ABI with host buffers (pinned)
+    e2e = None
+    if not args.no_e2e:
+        xyz_p = torch.empty(xyz_h.shape, dtype=torch.float64, pin_memory=True).numpy()
+        sem_p = torch.empty(sem_h.shape, dtype=torch.float32, pin_memory=True).numpy()
+        pos_p = torch.empty(poses0.shape, dtype=torch.float64, pin_memory=True).numpy()
+        xyz_p[:] = xyz_h
+        sem_p[:] = sem_h
+        params1 = pk.make_params(P["ell"], P["cutoff_mult"], P["sigma"], 0.0, sem_dim, 0,
+                                 max_iters=1)
+        n_e2e = max(3, min(args.steps, 20))
+        e2e_pairs, e2e_s = 0, 0.0
+        for k in range(n_e2e + 2):
+            pos_p[:] = poses0
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            c2 = rb.rkhsba_create_flat(n_points, xyz_p, sem_p, None, edges, params1,
+                                       stream.cuda_stream)
+            T, info = rb.rkhsba_solve(c2, pos_p, K)
+            rb.rkhsba_destroy(c2)
+            dt = time.perf_counter() - t0
+            if k >= 2:
+                e2e_pairs += info["pair_terms"]
+                e2e_s += dt
+        h2d = xyz_h.nbytes + sem_h.nbytes + poses0.nbytes + edges.nbytes + n_points.nbytes
+        e2e = dict(value=e2e_pairs / e2e_s, unit=UNIT, h2d_bytes_per_step=int(h2d),
+                   d2h_bytes_per_step=int(poses0.nbytes + 64), steps=n_e2e,
+                   step="create (H2D + grids) + solve with max_iters 1 + destroy")
+
+    if rank == 0:
+        line = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps,
+                    warmup=args.warmup, ms_per_step=ms_max / args.steps, higher_is_better=True,
+                    scaling="weak", vs_baseline=None, dtype="f32", data="synthetic",
+                    config=dict(workload=WORKLOAD, frames=K, points=int(n_points.sum()),
+                                edges=len(edges), sem_dim=sem_dim, ell=P["ell"],
+                                pair_terms_per_step=int(pairs_per_step),
+                                l2="256 MiB buffer written between steps, outside the timed events",
+                                step="grid build + evaluation + one LM iteration (2 evaluations)",
+                                parallelism="replicas" if world > 1 else "single GPU"),
+                    roofline=roofline, cpu_baseline=cpu_base, e2e=e2e, gpu_launches=int(n_launch),
+                    clocks=clk)
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--oracle-sample", default=None)
+    args = ap.parse_args()
+    if args.oracle_sample:
+        print(json.dumps(oracle_sample(args.oracle_sample)))
+        return
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        reference_arm(args, rank)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    ours(args, rank, world, local_rank)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

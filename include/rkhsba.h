@@ -1,0 +1,207 @@
+/*
+ * rkhsba.h -- C ABI of the GB300 (sm_103a) RKHS-BA hot path.
+ *
+ * The library evaluates the correspondence-free multi-frame objective of
+ * RKHS-BA (Zhang et al., arXiv 2403.01254):
+ *
+ *   F(T) = sum_{(a,b) in C} sum_{i,j} c_ij * sigma^2 exp(-|T_a x_i - T_b y_j|^2 / (2 ell^2))
+ *
+ * (Eq. inner_product_actual_ba with the squared-exponential kernel of
+ * Eq. kernel), restricted to point pairs closer than r_c = cutoff_mult * ell
+ * (the sparse double sum of Sec. III-B), together with its gradient under the
+ * right perturbation T exp(eps^), eps = [rho; phi] (Eq. inner_product_reformat)
+ * and the Gauss-Newton matrix of the IRLS cost (Eq. irls_final), and runs the
+ * damped Gauss-Newton (Levenberg-Marquardt) pose solve with the first frame
+ * fixed (Sec. V-A).  All work runs in CUDA kernels on one GPU.
+ *
+ * Conventions shared by every call
+ *  - Frames are numbered 0..K-1.  Points are given frame after frame in one
+ *    flat array; n_points[m] says how many belong to frame m (0 allowed).
+ *  - Poses are frame-to-world SE(3) matrices, 4x4 row-major float64, K of
+ *    them back to back (16*K doubles).  Their rotation blocks must satisfy
+ *    |R^T R - I|_max <= 1e-9 (else RKHSBA_EINVAL).
+ *  - Edges are unordered frame pairs (a, b), a != b, each pair at most once;
+ *    the library orders each as (min, max).
+ *  - Gradient and Hessian coordinates are per frame [rho(3), phi(3)] in the
+ *    frame's own (body) axes, frame after frame (6*K entries).
+ *  - loss = -F (lower is better).  grad = d loss / d eps = (sigma^2/ell^2) * b
+ *    with b = sum w J^T d; H = sum w J^T J, the IRLS Gauss-Newton matrix,
+ *    where w_ij = c_ij exp(-|d_ij|^2 / (2 ell^2)) (Eq. irls_weight),
+ *    d_ij = T_a x_i - T_b y_j, J = d d_ij / d eps.
+ *  - c_ij = <l_i, l_j> (label vectors, sem_dim floats per point) times
+ *    exp(-|col_i - col_j|^2 / (2 ell_color^2)) when colours are given and
+ *    ell_color > 0 (the tensor-product label of Sec. III-A); with neither,
+ *    c_ij = 1 (plain kernel correlation).
+ *  - Host pointers are read during the call only; the library copies what it
+ *    keeps.  Output buffers are caller-allocated.  Every call returns a
+ *    status and never throws; rkhsba_last_error() gives a message.
+ *  - A context is not thread-safe: one host thread at a time.
+ *  - Limits: sum of points < 2^31, sem_dim <= 32, 1 <= K <= 4096 frames,
+ *    |coordinate| / (1.001 * r_c) < 2^29.
+ */
+#ifndef RKHSBA_H
+#define RKHSBA_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rkhsba_ctx rkhsba_ctx;
+
+typedef enum {
+    RKHSBA_OK = 0,
+    RKHSBA_EINVAL = 1,    /* invalid argument or input data (NaN/Inf, bad pose, bad edge) */
+    RKHSBA_ENOMEM = 2,    /* device allocation failed */
+    RKHSBA_ECUDA = 3,     /* CUDA runtime error */
+    RKHSBA_ENOTCONV = 4,  /* solve stopped at max_iters before converging */
+    RKHSBA_ETIMEOUT = 5,  /* a bounded device wait gave up */
+    RKHSBA_EBUSY = 6      /* resource exhausted (server slots / memory) */
+} rkhsba_status;
+
+/* Kernel and solver parameters.  Zero means "default" for every field. */
+typedef struct {
+    double ell;          /* lengthscale ell of Eq. kernel, metres, > 0 (required) */
+    double cutoff_mult;  /* r_c = cutoff_mult * ell (default 3) */
+    double sigma;        /* sigma of Eq. kernel (default 1) */
+    double ell_color;    /* colour lengthscale; <= 0 disables the colour factor */
+    int32_t sem_dim;     /* floats per label vector, 0..32; 0 = no labels */
+    int32_t sem_bf16;    /* 1: keep labels on the device as bfloat16 (rounded) */
+    int32_t max_iters;   /* LM evaluations after the first (default 100) */
+    int32_t reserved;    /* must be 0 */
+    double lambda0;      /* initial LM damping (default 1e-4) */
+    double tol_step;     /* stop when an accepted step has |delta|_inf below (1e-10) */
+    double tol_rel_f;    /* stop when an accepted step gains less than this relative F (1e-12) */
+} rkhsba_params;
+
+typedef struct {
+    int32_t iters;       /* evaluations after the first */
+    int32_t status;      /* RKHSBA_OK converged, RKHSBA_ENOTCONV hit max_iters */
+    double final_loss;   /* -F at the returned poses */
+    double lambda;       /* damping at exit */
+    int64_t pair_terms;  /* pair-terms summed over every evaluation of the solve */
+} rkhsba_solve_info;
+
+/*
+ * rkhsba_create -- upload a problem and build its per-frame uniform grids.
+ *
+ * Problem statement of Sec. III: frames X_m of 3-D points, pose graph C,
+ * pose-invariant labels l(x) (Sec. III-A), kernel parameters of Eq. kernel.
+ *
+ *   out        receives the new context (NULL on failure)
+ *   n_frames   K >= 1
+ *   n_points   [K] points per frame (>= 0)
+ *   xyz        [sum n_points * 3] float64, frame-local coordinates, HOST memory
+ *   sem        [sum n_points * sem_dim] float32 labels, or NULL (requires sem_dim == 0)
+ *   rgb        [sum n_points * 3] float32 colours, or NULL
+ *   n_edges    >= 1
+ *   edges      [n_edges * 2] int32 frame indices
+ *   params     see rkhsba_params; params->ell > 0
+ *   cuda_stream  cudaStream_t to run on (NULL: the library's own stream)
+ *
+ * Errors: EINVAL for NaN/Inf coordinates, labels or colours, empty pose
+ * graph, self/duplicate/out-of-range edges, unsupported sem_dim or limits;
+ * ENOMEM / ECUDA from the device.  The context owns all device memory.
+ */
+rkhsba_status rkhsba_create(rkhsba_ctx** out, int32_t n_frames, const int64_t* n_points,
+                            const double* xyz, const float* sem, const float* rgb,
+                            int32_t n_edges, const int32_t* edges,
+                            const rkhsba_params* params, void* cuda_stream);
+
+/* Same as rkhsba_create with xyz / sem / rgb in DEVICE memory (copied). */
+rkhsba_status rkhsba_create_device(rkhsba_ctx** out, int32_t n_frames, const int64_t* n_points,
+                                   const double* d_xyz, const float* d_sem, const float* d_rgb,
+                                   int32_t n_edges, const int32_t* edges,
+                                   const rkhsba_params* params, void* cuda_stream);
+
+void rkhsba_destroy(rkhsba_ctx* ctx);
+
+/*
+ * rkhsba_eval -- loss, gradient and Gauss-Newton matrix at the given poses
+ * (Eq. inner_product_actual_ba, Eq. inner_product_reformat, Eq. irls_final).
+ *
+ *   poses      [K*16] HOST float64 poses
+ *   loss       [1] -F, or NULL
+ *   grad       [6K] d loss / d eps, or NULL
+ *   H_full     [6K*6K] row-major sum w J^T J, or NULL
+ *   H_blocks   [n_edges*144] per-edge 12x12 blocks, rows/cols ordered
+ *              [rho_a, phi_a, rho_b, phi_b] with (a, b) = (min, max), or NULL
+ *   edge_pairs [n_edges] int64 pair-terms per edge, or NULL
+ *
+ * Synchronous: returns after the outputs are written.
+ */
+rkhsba_status rkhsba_eval(rkhsba_ctx* ctx, const double* poses, double* loss, double* grad,
+                          double* H_full, double* H_blocks, int64_t* edge_pairs);
+
+/*
+ * rkhsba_solve -- damped Gauss-Newton on the IRLS cost with the weights
+ * recomputed after every step (Eq. irls_final), frame 0 held fixed, steps
+ * accepted while the original cost F increases (Sec. V-C).
+ *
+ *   poses  [K*16] HOST float64: initial guess in, solution out
+ *   info   [1] summary, or NULL
+ *
+ * Returns RKHSBA_OK when converged, RKHSBA_ENOTCONV at max_iters (poses
+ * still hold the best iterate), other codes on error.
+ */
+rkhsba_status rkhsba_solve(rkhsba_ctx* ctx, double* poses, rkhsba_solve_info* info);
+
+/*
+ * Device-resident stepping, for callers that keep everything in HBM.
+ * All three are asynchronous on the context stream and do not synchronise.
+ *   rkhsba_set_poses_device  copy K*16 float64 poses from DEVICE memory and
+ *                            reset the LM state (lambda0, iteration 0)
+ *   rkhsba_rebuild           rebuild the per-frame grids from the resident
+ *                            points (the grid step; poses untouched)
+ *   rkhsba_iterate           run n LM iterations (each one solve, one
+ *                            evaluation and one accept/reject); the first
+ *                            call after set_poses also evaluates the start
+ * rkhsba_get_state synchronises and copies poses [K*16] / info to the host.
+ */
+rkhsba_status rkhsba_set_poses_device(rkhsba_ctx* ctx, const double* d_poses);
+rkhsba_status rkhsba_rebuild(rkhsba_ctx* ctx);
+rkhsba_status rkhsba_iterate(rkhsba_ctx* ctx, int32_t n_iters);
+rkhsba_status rkhsba_get_state(rkhsba_ctx* ctx, double* poses, rkhsba_solve_info* info);
+
+/*
+ * rkhsba_edge_pairs -- the pair set of one edge at the given poses, as found
+ * by the device radius search (for verification).
+ *
+ *   poses     [K*16] HOST float64
+ *   edge      index into the create() edge list
+ *   capacity  length of i_out / j_out
+ *   i_out     [capacity] int32 point index within frame a = min(edge)
+ *   j_out     [capacity] int32 point index within frame b = max(edge)
+ *   n_out     total pairs (may exceed capacity; then only capacity written)
+ * Pairs are returned in no particular order.
+ */
+rkhsba_status rkhsba_edge_pairs(rkhsba_ctx* ctx, const double* poses, int32_t edge,
+                                int64_t capacity, int32_t* i_out, int32_t* j_out,
+                                int64_t* n_out);
+
+/*
+ * rkhsba_profile -- CUDA-event timing of the phases of the hot path on the
+ * context stream: [0] grid build, [1] transforms + query binning, [2] pair
+ * kernel, [3] FP64 assembly, [4] LM solve + accept.
+ *   enable    1: clear and start recording; 0: stop recording
+ *   ms        [5] summed milliseconds of the recorded launches, or NULL
+ *   launches  [5] number of recorded launches per phase, or NULL
+ * Reading (ms or launches non-NULL) synchronises the stream.
+ */
+rkhsba_status rkhsba_profile(rkhsba_ctx* ctx, int32_t enable, double* ms, int64_t* launches);
+
+/* Problem shape and device memory of a context. */
+rkhsba_status rkhsba_info(const rkhsba_ctx* ctx, int32_t* n_frames, int32_t* n_edges,
+                          int64_t* n_points_total, int64_t* device_bytes);
+
+/* Message of the last failure on ctx (or of the calling thread when ctx is NULL). */
+const char* rkhsba_last_error(const rkhsba_ctx* ctx);
+
+/* Number of CUDA kernels this library has launched in the process. */
+int64_t rkhsba_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RKHSBA_H */

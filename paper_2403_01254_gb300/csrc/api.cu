@@ -1,0 +1,840 @@
+// C ABI of the RKHS-BA hot path (declared in include/rkhsba.h).
+//
+// A context owns one problem on one GPU: the raw frame-local points, the
+// per-frame grids (grid step), the per-evaluation binning buffers, the FP64
+// Gauss-Newton system and the LM state.  Host code here only validates
+// arguments, sizes buffers and issues kernels; every step of the objective,
+// its derivatives and the solve runs on the device.
+#include "common.cuh"
+#include "rkhsba.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <set>
+#include <string>
+#include <utility>
+#include <vector>
+
+namespace rk {
+std::atomic<long long> g_launches{0};
+}
+
+using namespace rk;
+
+namespace {
+thread_local std::string t_err;
+
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+};
+}  // namespace
+
+struct rkhsba_ctx {
+    int K = 0, E = 0;
+    long long N = 0;
+    rkhsba_params p{};
+    GridParams gp{};
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int num_sms = 1;
+    std::string err;
+    std::vector<DevBuf> bufs;
+    size_t bytes = 0;
+
+    std::vector<long long> pt_off;        // K+1
+    std::vector<FrameDev> frames_h;
+    std::vector<EdgeDev> edges_h;
+    std::vector<std::pair<int, int>> edge_in;   // as given by the caller (a, b)
+
+    // device
+    long long* d_pt_off = nullptr;
+    FrameDev* d_frames = nullptr;
+    EdgeDev* d_edges = nullptr;
+    double* d_xyz = nullptr;
+    float* d_sem_in = nullptr;
+    float* d_rgb_in = nullptr;
+    int* d_cmin = nullptr;
+    int* d_cmax = nullptr;
+    unsigned* d_semnorm = nullptr;
+    int* d_err = nullptr;
+
+    long long C_total = 0;
+    uint32_t* d_keys = nullptr;
+    uint32_t* d_keys_alt = nullptr;
+    int* d_vals = nullptr;
+    int* d_vals_alt = nullptr;
+    long long* d_hist = nullptr;
+    int* d_cell_start = nullptr;
+    float4* d_pts4 = nullptr;
+    void* d_sem = nullptr;
+    float4* d_col4 = nullptr;
+    int* d_perm_local = nullptr;
+    long long* d_run = nullptr;       // run flags, then their exclusive scan
+    long long* d_run_excl = nullptr;
+    long long* d_occ_key = nullptr;
+    long long* d_occ_first = nullptr;  // K+1
+    long long* d_total = nullptr;      // scratch totals [4]
+    long long* d_scan_ws = nullptr;
+
+    long long total_bins = 0, n_items = 0, Q_total = 0, max_tasks = 0;
+    EdgeXf* d_xf = nullptr;
+    int* d_bin_count = nullptr;
+    int* d_bin_cursor = nullptr;
+    long long* d_bin_val = nullptr;
+    long long* d_bin_packed = nullptr;
+    Task* d_tasks = nullptr;
+    Slot* d_slots = nullptr;
+    int* d_ntasks = nullptr;           // [2]: n_tasks, task_counter
+    long long* d_acc = nullptr;
+    EdgeOut* d_eout = nullptr;
+    int* d_inc_off = nullptr;
+    int* d_inc_list = nullptr;
+
+    double* d_H_cand = nullptr;
+    double* d_H_cur = nullptr;
+    double* d_b_cand = nullptr;
+    double* d_b_cur = nullptr;
+    double* d_F_cand = nullptr;
+    long long* d_n_cand = nullptr;
+    double* d_poses_cur = nullptr;
+    double* d_poses_cand = nullptr;
+    LMState* d_state = nullptr;
+    double* d_lm_ws = nullptr;
+    bool need_initial = true;
+
+    // phase profiler (CUDA events on the context stream)
+    static constexpr int NPH = 5;
+    bool prof = false;
+    std::vector<cudaEvent_t> ev_pool;
+    std::vector<std::pair<int, std::pair<int, int>>> ev_rec;   // phase, (start, end) pool index
+    int cur_phase = -1, cur_start = -1;
+    int ev_take() {
+        if (ev_rec.size() * 2 + 2 > ev_pool.size()) {
+            for (int i = 0; i < 64; ++i) {
+                cudaEvent_t e;
+                if (cudaEventCreate(&e) != cudaSuccess) return -1;
+                ev_pool.push_back(e);
+            }
+        }
+        return -2;
+    }
+    void phase_begin(int ph) {
+        if (!prof) return;
+        if (ev_take() == -1) return;
+        int idx = (int)(ev_rec.size() * 2);
+        cudaEventRecord(ev_pool[idx], stream);
+        cur_phase = ph;
+        cur_start = idx;
+    }
+    void phase_end() {
+        if (!prof || cur_phase < 0) return;
+        cudaEventRecord(ev_pool[cur_start + 1], stream);
+        ev_rec.push_back({cur_phase, {cur_start, cur_start + 1}});
+        cur_phase = -1;
+    }
+
+    ~rkhsba_ctx() {
+        if (stream) cudaStreamSynchronize(stream);
+        for (auto e : ev_pool) cudaEventDestroy(e);
+        for (auto& b : bufs) cudaFree(b.p);
+        if (own_stream && stream) cudaStreamDestroy(stream);
+    }
+};
+
+namespace {
+
+rkhsba_status fail(rkhsba_ctx* ctx, rkhsba_status s, const std::string& msg) {
+    t_err = msg;
+    if (ctx) ctx->err = msg;
+    return s;
+}
+
+#define RK_CUDA(ctx, call)                                                              \
+    do {                                                                                \
+        cudaError_t _e = (call);                                                        \
+        if (_e != cudaSuccess)                                                          \
+            return fail(ctx, RKHSBA_ECUDA, std::string(#call) + ": " + cudaGetErrorString(_e)); \
+    } while (0)
+
+#define RK_TRY(expr)                        \
+    do {                                    \
+        rkhsba_status _s = (expr);          \
+        if (_s != RKHSBA_OK) return _s;     \
+    } while (0)
+
+template <typename T>
+rkhsba_status alloc(rkhsba_ctx* ctx, T** out, long long count) {
+    size_t bytes = (size_t)std::max<long long>(count, 1) * sizeof(T);
+    bytes = (bytes + 255) & ~(size_t)255;
+    void* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ctx, RKHSBA_ENOMEM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed: " +
+                                            cudaGetErrorString(e));
+    }
+    ctx->bufs.push_back({p, bytes});
+    ctx->bytes += bytes;
+    *out = static_cast<T*>(p);
+    return RKHSBA_OK;
+}
+
+// label row padding: the pair kernel is instantiated for these widths only
+int sem_pad_for(int dim, bool bf16) {
+    if (dim <= 0) return 0;
+    static const int pads_f32[] = {4, 8, 12, 16, 20, 24, 32};
+    static const int pads_bf16[] = {8, 16, 24, 32};
+    if (bf16) {
+        for (int pd : pads_bf16)
+            if (dim <= pd) return pd;
+        return 0;
+    }
+    for (int pd : pads_f32)
+        if (dim <= pd) return pd;
+    return 0;
+}
+
+rkhsba_status normalize_params(rkhsba_ctx* ctx, const rkhsba_params* in) {
+    if (!in) return fail(ctx, RKHSBA_EINVAL, "params is NULL");
+    rkhsba_params p = *in;
+    if (!(p.ell > 0.0) || !std::isfinite(p.ell)) return fail(ctx, RKHSBA_EINVAL, "params.ell must be > 0");
+    if (p.cutoff_mult == 0.0) p.cutoff_mult = 3.0;
+    if (!(p.cutoff_mult > 0.0) || !std::isfinite(p.cutoff_mult))
+        return fail(ctx, RKHSBA_EINVAL, "params.cutoff_mult must be finite and > 0");
+    if (p.sigma == 0.0) p.sigma = 1.0;
+    if (!std::isfinite(p.sigma)) return fail(ctx, RKHSBA_EINVAL, "params.sigma must be finite");
+    if (p.sem_dim < 0 || p.sem_dim > MAX_SEM)
+        return fail(ctx, RKHSBA_EINVAL, "params.sem_dim must be in [0, 32]");
+    if (p.max_iters == 0) p.max_iters = 100;
+    if (p.max_iters < 0) return fail(ctx, RKHSBA_EINVAL, "params.max_iters must be >= 0");
+    if (p.lambda0 == 0.0) p.lambda0 = 1e-4;
+    if (p.tol_step == 0.0) p.tol_step = 1e-10;
+    if (p.tol_rel_f == 0.0) p.tol_rel_f = 1e-12;
+    if (p.reserved != 0) return fail(ctx, RKHSBA_EINVAL, "params.reserved must be 0");
+    ctx->p = p;
+    const double rc = p.cutoff_mult * p.ell;
+    GridParams& g = ctx->gp;
+    g.h = rc * (1.0 + 1.0 / 1024.0);
+    g.h_inv = 1.0 / g.h;
+    g.hf = (float)g.h;
+    g.hf_inv = (float)g.h_inv;
+    g.rc2 = (float)(rc * rc);
+    const double log2e = 1.4426950408889634;
+    g.kg = (float)(-log2e / (2.0 * p.ell * p.ell));
+    g.color = 0;
+    g.kc = 0.f;
+    g.sem_dim = p.sem_dim;
+    g.sem_bf16 = p.sem_bf16 ? 1 : 0;
+    g.sem_pad = sem_pad_for(p.sem_dim, g.sem_bf16);
+    if (p.sem_dim > 0 && g.sem_pad == 0) return fail(ctx, RKHSBA_EINVAL, "unsupported sem_dim");
+    return RKHSBA_OK;
+}
+
+rkhsba_status check_shape(rkhsba_ctx* ctx, int32_t n_frames, const int64_t* n_points, int32_t n_edges,
+                          const int32_t* edges) {
+    if (n_frames < 1 || n_frames > 4096) return fail(ctx, RKHSBA_EINVAL, "n_frames must be in [1, 4096]");
+    if (!n_points) return fail(ctx, RKHSBA_EINVAL, "n_points is NULL");
+    if (n_edges < 1) return fail(ctx, RKHSBA_EINVAL, "the pose graph needs at least one edge");
+    if (!edges) return fail(ctx, RKHSBA_EINVAL, "edges is NULL");
+    ctx->K = n_frames;
+    ctx->pt_off.assign(n_frames + 1, 0);
+    for (int m = 0; m < n_frames; ++m) {
+        if (n_points[m] < 0) return fail(ctx, RKHSBA_EINVAL, "negative point count");
+        ctx->pt_off[m + 1] = ctx->pt_off[m] + n_points[m];
+        if (ctx->pt_off[m + 1] >= (1LL << 31) - 64) return fail(ctx, RKHSBA_EINVAL, "more than 2^31 points");
+    }
+    ctx->N = ctx->pt_off[n_frames];
+    std::set<std::pair<int, int>> seen;
+    ctx->E = n_edges;
+    ctx->edges_h.assign(n_edges, EdgeDev{});
+    ctx->edge_in.clear();
+    for (int e = 0; e < n_edges; ++e) {
+        int a = edges[2 * e], b = edges[2 * e + 1];
+        if (a < 0 || b < 0 || a >= n_frames || b >= n_frames)
+            return fail(ctx, RKHSBA_EINVAL, "edge " + std::to_string(e) + " names a missing frame");
+        if (a == b) return fail(ctx, RKHSBA_EINVAL, "edge " + std::to_string(e) + " is a self-edge");
+        ctx->edge_in.push_back({a, b});
+        if (a > b) std::swap(a, b);
+        if (!seen.insert({a, b}).second)
+            return fail(ctx, RKHSBA_EINVAL, "edge " + std::to_string(e) + " duplicates an earlier edge");
+        ctx->edges_h[e].a = a;
+        ctx->edges_h[e].b = b;
+    }
+    return RKHSBA_OK;
+}
+
+void grid_fill(rkhsba_ctx* c, bool* keys_in_alt) {
+    cudaStream_t st = c->stream;
+    launch_keys(c->d_xyz, c->N, c->K, c->d_pt_off, c->d_frames, c->gp.h_inv, c->d_keys, c->d_vals, st);
+    int nbits = 0;
+    while ((1LL << nbits) < c->C_total) ++nbits;
+    bool alt = false;
+    radix_sort_u32(c->d_keys, c->d_vals, c->d_keys_alt, c->d_vals_alt, c->N, nbits, c->d_hist,
+                   c->d_scan_ws, st, &alt);
+    const uint32_t* keys = alt ? c->d_keys_alt : c->d_keys;
+    const int* perm = alt ? c->d_vals_alt : c->d_vals;
+    launch_gather(c->d_xyz, c->d_sem_in, c->d_rgb_in, c->N, c->K, c->d_pt_off, keys, perm, c->gp,
+                  c->C_total, c->d_pts4, c->d_sem, c->d_col4, c->d_perm_local, c->d_cell_start,
+                  c->d_run, st);
+    scan_exclusive_i64(c->d_run, c->d_run_excl, c->N, c->d_total, c->d_scan_ws, st);
+    launch_occ(keys, c->d_run_excl, c->N, c->d_occ_key, st);
+    *keys_in_alt = alt;
+}
+
+double bound_exp_scale(double bound, float* scale) {
+    if (!(bound > 0.0) || !std::isfinite(bound)) bound = 1.0;
+    int e = 61 - (int)std::ceil(std::log2(bound));
+    e = std::max(-120, std::min(120, e));
+    *scale = std::ldexp(1.0f, e);
+    return std::ldexp(1.0, -e);
+}
+
+rkhsba_status build(rkhsba_ctx* c, const double* xyz, const float* sem, const float* rgb, bool on_device,
+                    void* stream) {
+    const long long N = c->N;
+    const int K = c->K, E = c->E;
+    int dev = 0;
+    RK_CUDA(c, cudaGetDevice(&dev));
+    RK_CUDA(c, cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, dev));
+    if (stream) {
+        c->stream = (cudaStream_t)stream;
+    } else {
+        RK_CUDA(c, cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
+        c->own_stream = true;
+    }
+    cudaStream_t st = c->stream;
+    const bool has_sem = c->p.sem_dim > 0;
+    if (has_sem != (sem != nullptr))
+        return fail(c, RKHSBA_EINVAL, "sem must be given exactly when params.sem_dim > 0");
+    c->gp.color = (rgb != nullptr && c->p.ell_color > 0.0) ? 1 : 0;
+    if (c->gp.color) {
+        const double log2e = 1.4426950408889634;
+        c->gp.kc = (float)(-log2e / (2.0 * c->p.ell_color * c->p.ell_color));
+    }
+    const float* rgb_used = c->gp.color ? rgb : nullptr;
+
+    // raw inputs
+    RK_TRY(alloc(c, &c->d_xyz, 3 * N));
+    RK_CUDA(c, cudaMemcpyAsync(c->d_xyz, xyz, sizeof(double) * 3 * N,
+                               on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+    if (has_sem) {
+        RK_TRY(alloc(c, &c->d_sem_in, (long long)c->p.sem_dim * N));
+        RK_CUDA(c, cudaMemcpyAsync(c->d_sem_in, sem, sizeof(float) * c->p.sem_dim * N,
+                                   on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+    }
+    if (rgb_used) {
+        RK_TRY(alloc(c, &c->d_rgb_in, 3 * N));
+        RK_CUDA(c, cudaMemcpyAsync(c->d_rgb_in, rgb_used, sizeof(float) * 3 * N,
+                                   on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+    }
+    RK_TRY(alloc(c, &c->d_pt_off, K + 1));
+    RK_CUDA(c, cudaMemcpyAsync(c->d_pt_off, c->pt_off.data(), sizeof(long long) * (K + 1),
+                               cudaMemcpyHostToDevice, st));
+    RK_TRY(alloc(c, &c->d_cmin, 3 * K));
+    RK_TRY(alloc(c, &c->d_cmax, 3 * K));
+    RK_TRY(alloc(c, &c->d_semnorm, K));
+    RK_TRY(alloc(c, &c->d_err, 4));
+    std::vector<int> big(3 * K, 0x7fffffff), small(3 * K, (int)0x80000000);
+    RK_CUDA(c, cudaMemcpyAsync(c->d_cmin, big.data(), sizeof(int) * 3 * K, cudaMemcpyHostToDevice, st));
+    RK_CUDA(c, cudaMemcpyAsync(c->d_cmax, small.data(), sizeof(int) * 3 * K, cudaMemcpyHostToDevice, st));
+    RK_CUDA(c, cudaMemsetAsync(c->d_semnorm, 0, sizeof(unsigned) * K, st));
+    RK_CUDA(c, cudaMemsetAsync(c->d_err, 0, sizeof(int) * 4, st));
+    launch_bbox(c->d_xyz, c->d_sem_in, c->d_rgb_in, N, K, c->d_pt_off, c->p.sem_dim, c->gp.h_inv,
+                c->d_cmin, c->d_cmax, c->d_semnorm, c->d_err, st);
+    std::vector<int> cmin(3 * K), cmax(3 * K);
+    std::vector<unsigned> semn(K);
+    int errbits = 0;
+    RK_CUDA(c, cudaMemcpyAsync(cmin.data(), c->d_cmin, sizeof(int) * 3 * K, cudaMemcpyDeviceToHost, st));
+    RK_CUDA(c, cudaMemcpyAsync(cmax.data(), c->d_cmax, sizeof(int) * 3 * K, cudaMemcpyDeviceToHost, st));
+    RK_CUDA(c, cudaMemcpyAsync(semn.data(), c->d_semnorm, sizeof(unsigned) * K, cudaMemcpyDeviceToHost, st));
+    RK_CUDA(c, cudaMemcpyAsync(&errbits, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    RK_CUDA(c, cudaStreamSynchronize(st));
+    if (errbits & 1) return fail(c, RKHSBA_EINVAL, "non-finite point coordinate");
+    if (errbits & 2) return fail(c, RKHSBA_EINVAL, "point coordinate beyond 2^29 grid cells");
+    if (errbits & 4) return fail(c, RKHSBA_EINVAL, "non-finite label value");
+    if (errbits & 8) return fail(c, RKHSBA_EINVAL, "non-finite colour value");
+
+    // grid layout per frame (dense, one-cell margin)
+    c->frames_h.assign(K, FrameDev{});
+    long long coff = 0;
+    for (int m = 0; m < K; ++m) {
+        FrameDev& F = c->frames_h[m];
+        F.pt_off = c->pt_off[m];
+        F.n_pts = (int)(c->pt_off[m + 1] - c->pt_off[m]);
+        long long cells = 1;
+        for (int k = 0; k < 3; ++k) {
+            if (F.n_pts > 0) {
+                F.lo[k] = cmin[3 * m + k] - 1;
+                long long d = (long long)cmax[3 * m + k] - cmin[3 * m + k] + 3;
+                if (d > (1LL << 20)) return fail(c, RKHSBA_EINVAL, "frame extent exceeds 2^20 grid cells per axis");
+                F.dim[k] = (int)d;
+            } else {
+                F.lo[k] = 0;
+                F.dim[k] = 1;
+            }
+            cells *= F.dim[k];
+        }
+        if (cells > (1LL << 30)) return fail(c, RKHSBA_EINVAL, "frame grid larger than 2^30 cells");
+        F.cell_off = coff;
+        coff += cells;
+        float nrm;
+        std::memcpy(&nrm, &semn[m], sizeof(float));
+        F.sem_norm_max = has_sem ? nrm : 1.0f;
+    }
+    c->C_total = coff;
+    if (c->C_total >= (1LL << 31) - 2) return fail(c, RKHSBA_EINVAL, "total grid cells exceed 2^31");
+    RK_TRY(alloc(c, &c->d_frames, K));
+    RK_CUDA(c, cudaMemcpyAsync(c->d_frames, c->frames_h.data(), sizeof(FrameDev) * K,
+                               cudaMemcpyHostToDevice, st));
+
+    // grid buffers
+    const int sp = c->gp.sem_pad;
+    RK_TRY(alloc(c, &c->d_keys, N));
+    RK_TRY(alloc(c, &c->d_keys_alt, N));
+    RK_TRY(alloc(c, &c->d_vals, N));
+    RK_TRY(alloc(c, &c->d_vals_alt, N));
+    RK_TRY(alloc(c, &c->d_hist, (long long)radix_hist_elems(N)));
+    RK_TRY(alloc(c, &c->d_cell_start, c->C_total + 1));
+    RK_TRY(alloc(c, &c->d_pts4, N));
+    if (sp > 0) {
+        char* p = nullptr;
+        RK_TRY(alloc(c, &p, (long long)N * sp * (c->gp.sem_bf16 ? 2 : 4)));
+        c->d_sem = p;
+    }
+    if (c->gp.color) RK_TRY(alloc(c, &c->d_col4, N));
+    RK_TRY(alloc(c, &c->d_perm_local, N));
+    RK_TRY(alloc(c, &c->d_run, N));
+    RK_TRY(alloc(c, &c->d_run_excl, N));
+    RK_TRY(alloc(c, &c->d_occ_key, N));
+    RK_TRY(alloc(c, &c->d_occ_first, K + 1));
+    RK_TRY(alloc(c, &c->d_total, 4));
+
+    // per-edge sizes known so far
+    c->total_bins = 0;
+    c->Q_total = 0;
+    for (int e = 0; e < E; ++e) {
+        EdgeDev& Ed = c->edges_h[e];
+        const FrameDev& Fa = c->frames_h[Ed.a];
+        Ed.bin_off = c->total_bins;
+        c->total_bins += (long long)Fa.dim[0] * Fa.dim[1] * Fa.dim[2];
+        c->Q_total += c->frames_h[Ed.b].n_pts;
+    }
+    long long scan_n = std::max<long long>(std::max<long long>(N, c->total_bins),
+                                           (long long)radix_hist_elems(N));
+    RK_TRY(alloc(c, &c->d_scan_ws, (long long)scan_ws_elems(scan_n) + 64));
+    RK_CUDA(c, cudaMemsetAsync(c->d_cell_start, 0, sizeof(int) * (c->C_total + 1), st));
+    bool alt = false;
+    grid_fill(c, &alt);
+    launch_frame_occ(c->d_run_excl, N, c->d_total, K, c->d_pt_off, c->d_occ_first, st);
+    std::vector<long long> occ_first(K + 1);
+    RK_CUDA(c, cudaMemcpyAsync(occ_first.data(), c->d_occ_first, sizeof(long long) * (K + 1),
+                               cudaMemcpyDeviceToHost, st));
+    RK_CUDA(c, cudaStreamSynchronize(st));
+    RK_CUDA(c, cudaGetLastError());
+    for (int m = 0; m < K; ++m) {
+        c->frames_h[m].occ_off = occ_first[m];
+        c->frames_h[m].n_occ = (int)(occ_first[m + 1] - occ_first[m]);
+    }
+    RK_CUDA(c, cudaMemcpyAsync(c->d_frames, c->frames_h.data(), sizeof(FrameDev) * K,
+                               cudaMemcpyHostToDevice, st));
+
+    // edges: binning work items and fixed-point scales
+    const double rc = c->p.cutoff_mult * c->p.ell;
+    c->n_items = 0;
+    long long nonempty_cap = 0;
+    for (int e = 0; e < E; ++e) {
+        EdgeDev& Ed = c->edges_h[e];
+        const FrameDev& Fa = c->frames_h[Ed.a];
+        const FrameDev& Fb = c->frames_h[Ed.b];
+        Ed.wi_off = c->n_items;
+        c->n_items += Fb.n_occ;
+        const long long bins = (long long)Fa.dim[0] * Fa.dim[1] * Fa.dim[2];
+        nonempty_cap += std::min<long long>(bins, Fb.n_pts);
+        double smax = (double)Fa.sem_norm_max * (double)Fb.sem_norm_max * (1.0 + 1e-6) + 1e-30;
+        double Wb = (double)std::max(Fa.n_pts, 1) * (double)std::max(Fb.n_pts, 1) * smax;
+        double R2 = 0.0;
+        for (int k = 0; k < 3; ++k) {
+            double lo = Fa.lo[k] * c->gp.h, hi = (Fa.lo[k] + Fa.dim[k]) * c->gp.h;
+            double mm = std::max(std::fabs(lo), std::fabs(hi));
+            R2 += mm * mm;
+        }
+        double R = std::sqrt(R2) + c->gp.h;
+        double bounds[MC_N] = {Wb, Wb * rc, Wb * R, Wb * R * R, Wb * rc * R, Wb * rc * rc, 1.0, 1.0};
+        for (int k = 0; k < MC_N; ++k) Ed.inv_scale[k] = bound_exp_scale(bounds[k], &Ed.scale[k]);
+        Ed.scale[MC_CNT] = 1.0f;
+        Ed.inv_scale[MC_CNT] = 1.0;
+    }
+    c->max_tasks = c->Q_total / 32 + nonempty_cap + E + 1;
+    RK_TRY(alloc(c, &c->d_edges, E));
+    RK_CUDA(c, cudaMemcpyAsync(c->d_edges, c->edges_h.data(), sizeof(EdgeDev) * E,
+                               cudaMemcpyHostToDevice, st));
+    // incidence lists (frame -> edges), edge order kept
+    std::vector<int> inc_off(K + 1, 0), inc_list;
+    for (int m = 0; m < K; ++m) {
+        for (int e = 0; e < E; ++e) {
+            if (c->edges_h[e].a == m) inc_list.push_back(2 * e);
+            if (c->edges_h[e].b == m) inc_list.push_back(2 * e + 1);
+        }
+        inc_off[m + 1] = (int)inc_list.size();
+    }
+    RK_TRY(alloc(c, &c->d_inc_off, K + 1));
+    RK_TRY(alloc(c, &c->d_inc_list, (long long)inc_list.size()));
+    RK_CUDA(c, cudaMemcpyAsync(c->d_inc_off, inc_off.data(), sizeof(int) * (K + 1), cudaMemcpyHostToDevice, st));
+    RK_CUDA(c, cudaMemcpyAsync(c->d_inc_list, inc_list.data(), sizeof(int) * inc_list.size(),
+                               cudaMemcpyHostToDevice, st));
+
+    // evaluation buffers
+    RK_TRY(alloc(c, &c->d_xf, E));
+    RK_TRY(alloc(c, &c->d_bin_count, c->total_bins));
+    RK_TRY(alloc(c, &c->d_bin_cursor, c->total_bins));
+    RK_TRY(alloc(c, &c->d_bin_val, c->total_bins));
+    RK_TRY(alloc(c, &c->d_bin_packed, c->total_bins));
+    RK_TRY(alloc(c, &c->d_tasks, c->max_tasks));
+    RK_TRY(alloc(c, &c->d_slots, c->Q_total));
+    RK_TRY(alloc(c, &c->d_ntasks, 4));
+    RK_TRY(alloc(c, &c->d_acc, (long long)E * ACC_N));
+    RK_TRY(alloc(c, &c->d_eout, E));
+    const long long n6 = 6LL * K;
+    RK_TRY(alloc(c, &c->d_H_cand, n6 * n6));
+    RK_TRY(alloc(c, &c->d_H_cur, n6 * n6));
+    RK_TRY(alloc(c, &c->d_b_cand, n6));
+    RK_TRY(alloc(c, &c->d_b_cur, n6));
+    RK_TRY(alloc(c, &c->d_F_cand, 1));
+    RK_TRY(alloc(c, &c->d_n_cand, 1));
+    RK_TRY(alloc(c, &c->d_poses_cur, 16LL * K));
+    RK_TRY(alloc(c, &c->d_poses_cand, 16LL * K));
+    RK_TRY(alloc(c, &c->d_state, 1));
+    const long long nf = 6LL * (K - 1);
+    RK_TRY(alloc(c, &c->d_lm_ws, nf * nf + nf + 16));
+    RK_CUDA(c, cudaMemsetAsync(c->d_state, 0, sizeof(LMState), st));
+    RK_CUDA(c, cudaStreamSynchronize(st));
+    RK_CUDA(c, cudaGetLastError());
+    return RKHSBA_OK;
+}
+
+// One evaluation at the device poses `poses`; results into the cand buffers.
+void run_eval(rkhsba_ctx* c, const double* poses, const int* done) {
+    cudaStream_t st = c->stream;
+    c->phase_begin(1);
+    launch_edge_setup(poses, c->d_edges, c->E, c->d_xf, done, st);
+    cudaMemsetAsync(c->d_bin_count, 0, sizeof(int) * c->total_bins, st);
+    cudaMemsetAsync(c->d_bin_cursor, 0, sizeof(int) * c->total_bins, st);
+    cudaMemsetAsync(c->d_acc, 0, sizeof(long long) * c->E * ACC_N, st);
+    cudaMemsetAsync(c->d_ntasks, 0, sizeof(int) * 4, st);
+    launch_bin(0, c->d_edges, c->E, c->d_frames, c->d_xf, c->d_occ_key, c->d_cell_start, c->d_pts4,
+               c->gp, c->d_bin_count, c->d_bin_packed, c->d_bin_cursor, c->d_slots, c->n_items, done,
+               c->num_sms, st);
+    launch_make_bins(c->d_bin_count, c->d_bin_val, c->total_bins, done, st);
+    scan_exclusive_i64(c->d_bin_val, c->d_bin_packed, c->total_bins, c->d_total + 1, c->d_scan_ws, st);
+    launch_emit_tasks(c->d_bin_count, c->d_bin_packed, c->d_edges, c->E, c->total_bins, c->d_total + 1,
+                      c->d_tasks, c->d_ntasks, done, st);
+    launch_bin(1, c->d_edges, c->E, c->d_frames, c->d_xf, c->d_occ_key, c->d_cell_start, c->d_pts4,
+               c->gp, c->d_bin_count, c->d_bin_packed, c->d_bin_cursor, c->d_slots, c->n_items, done,
+               c->num_sms, st);
+    c->phase_end();
+    c->phase_begin(2);
+    launch_pairs(c->d_tasks, c->d_ntasks, c->d_ntasks + 1, c->d_slots, c->d_edges, c->d_frames,
+                 c->d_cell_start, c->d_pts4, c->d_sem, c->d_col4, c->gp, c->d_acc, done, c->num_sms, st);
+    c->phase_end();
+    c->phase_begin(3);
+    launch_edge_assemble(c->d_edges, c->E, c->d_xf, c->d_acc, c->p.sigma * c->p.sigma, c->d_eout, done, st);
+    cudaMemsetAsync(c->d_H_cand, 0, sizeof(double) * 36LL * c->K * c->K, st);
+    launch_frame_assemble(c->d_edges, c->E, c->K, c->d_inc_off, c->d_inc_list, c->d_eout, c->d_H_cand,
+                          c->d_b_cand, c->d_F_cand, c->d_n_cand, done, st);
+    c->phase_end();
+}
+
+rkhsba_status check_poses(rkhsba_ctx* c, const double* poses) {
+    if (!poses) return fail(c, RKHSBA_EINVAL, "poses is NULL");
+    for (int m = 0; m < c->K; ++m) {
+        const double* T = poses + 16 * m;
+        for (int k = 0; k < 16; ++k)
+            if (!std::isfinite(T[k])) return fail(c, RKHSBA_EINVAL, "non-finite pose entry");
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) {
+                double s = 0.0;
+                for (int k = 0; k < 3; ++k) s += T[4 * k + i] * T[4 * k + j];
+                if (std::fabs(s - (i == j ? 1.0 : 0.0)) > 1e-9)
+                    return fail(c, RKHSBA_EINVAL, "pose " + std::to_string(m) + " has a non-orthonormal rotation");
+            }
+        if (T[12] != 0.0 || T[13] != 0.0 || T[14] != 0.0 || T[15] != 1.0)
+            return fail(c, RKHSBA_EINVAL, "pose " + std::to_string(m) + " last row is not [0 0 0 1]");
+    }
+    return RKHSBA_OK;
+}
+
+void reset_state(rkhsba_ctx* c) {
+    LMState s{};
+    s.lambda = c->p.lambda0;
+    s.tol_step = c->p.tol_step;
+    s.tol_rel_f = c->p.tol_rel_f;
+    s.max_iters = c->p.max_iters;
+    s.first = 1;
+    s.status = 4;
+    cudaMemcpyAsync(c->d_state, &s, sizeof(LMState), cudaMemcpyHostToDevice, c->stream);
+    c->need_initial = true;
+}
+
+void lm_initial(rkhsba_ctx* c) {
+    const int* done = &c->d_state->done;
+    run_eval(c, c->d_poses_cand, done);
+    c->phase_begin(4);
+    launch_lm_accept(c->K, c->d_state, c->d_F_cand, c->d_n_cand, c->d_poses_cur, c->d_poses_cand,
+                     c->d_b_cur, c->d_b_cand, c->stream);
+    launch_copy_if_accepted(c->d_state, c->d_H_cur, c->d_H_cand, 36LL * c->K * c->K, c->stream);
+    c->phase_end();
+    c->need_initial = false;
+}
+
+void lm_iteration(rkhsba_ctx* c) {
+    const int* done = &c->d_state->done;
+    c->phase_begin(4);
+    launch_lm_solve(c->K, c->d_H_cur, c->d_b_cur, c->d_poses_cur, c->d_poses_cand, c->d_state,
+                    c->d_lm_ws, c->stream);
+    c->phase_end();
+    run_eval(c, c->d_poses_cand, done);
+    c->phase_begin(4);
+    launch_lm_accept(c->K, c->d_state, c->d_F_cand, c->d_n_cand, c->d_poses_cur, c->d_poses_cand,
+                     c->d_b_cur, c->d_b_cand, c->stream);
+    launch_copy_if_accepted(c->d_state, c->d_H_cur, c->d_H_cand, 36LL * c->K * c->K, c->stream);
+    c->phase_end();
+}
+
+rkhsba_status create_impl(rkhsba_ctx** out, int32_t n_frames, const int64_t* n_points,
+                          const double* xyz, const float* sem, const float* rgb, int32_t n_edges,
+                          const int32_t* edges, const rkhsba_params* params, void* stream,
+                          bool on_device) {
+    if (!out) return fail(nullptr, RKHSBA_EINVAL, "out is NULL");
+    *out = nullptr;
+    rkhsba_ctx* c = new rkhsba_ctx();
+    rkhsba_status s = normalize_params(c, params);
+    if (s == RKHSBA_OK) s = check_shape(c, n_frames, n_points, n_edges, edges);
+    if (s == RKHSBA_OK && c->N > 0 && !xyz) s = fail(c, RKHSBA_EINVAL, "xyz is NULL");
+    if (s == RKHSBA_OK) s = build(c, xyz, sem, rgb, on_device, stream);
+    if (s != RKHSBA_OK) {
+        std::string msg = c->err;
+        delete c;
+        t_err = msg;
+        return s;
+    }
+    *out = c;
+    return RKHSBA_OK;
+}
+}  // namespace
+
+extern "C" {
+
+rkhsba_status rkhsba_create(rkhsba_ctx** out, int32_t n_frames, const int64_t* n_points,
+                            const double* xyz, const float* sem, const float* rgb, int32_t n_edges,
+                            const int32_t* edges, const rkhsba_params* params, void* cuda_stream) {
+    return create_impl(out, n_frames, n_points, xyz, sem, rgb, n_edges, edges, params, cuda_stream, false);
+}
+
+rkhsba_status rkhsba_create_device(rkhsba_ctx** out, int32_t n_frames, const int64_t* n_points,
+                                   const double* d_xyz, const float* d_sem, const float* d_rgb,
+                                   int32_t n_edges, const int32_t* edges, const rkhsba_params* params,
+                                   void* cuda_stream) {
+    return create_impl(out, n_frames, n_points, d_xyz, d_sem, d_rgb, n_edges, edges, params, cuda_stream,
+                       true);
+}
+
+void rkhsba_destroy(rkhsba_ctx* ctx) { delete ctx; }
+
+rkhsba_status rkhsba_eval(rkhsba_ctx* c, const double* poses, double* loss, double* grad, double* H_full,
+                          double* H_blocks, int64_t* edge_pairs) {
+    if (!c) return fail(nullptr, RKHSBA_EINVAL, "ctx is NULL");
+    RK_TRY(check_poses(c, poses));
+    cudaStream_t st = c->stream;
+    RK_CUDA(c, cudaMemcpyAsync(c->d_poses_cand, poses, sizeof(double) * 16 * c->K, cudaMemcpyHostToDevice, st));
+    run_eval(c, c->d_poses_cand, nullptr);
+    RK_CUDA(c, cudaGetLastError());
+    double F = 0.0;
+    RK_CUDA(c, cudaMemcpyAsync(&F, c->d_F_cand, sizeof(double), cudaMemcpyDeviceToHost, st));
+    std::vector<double> b;
+    if (grad) {
+        b.resize(6 * c->K);
+        RK_CUDA(c, cudaMemcpyAsync(b.data(), c->d_b_cand, sizeof(double) * 6 * c->K, cudaMemcpyDeviceToHost, st));
+    }
+    if (H_full)
+        RK_CUDA(c, cudaMemcpyAsync(H_full, c->d_H_cand, sizeof(double) * 36LL * c->K * c->K,
+                                   cudaMemcpyDeviceToHost, st));
+    std::vector<EdgeOut> eo;
+    if (H_blocks || edge_pairs) {
+        eo.resize(c->E);
+        RK_CUDA(c, cudaMemcpyAsync(eo.data(), c->d_eout, sizeof(EdgeOut) * c->E, cudaMemcpyDeviceToHost, st));
+    }
+    RK_CUDA(c, cudaStreamSynchronize(st));
+    if (loss) *loss = -F;
+    if (grad) {
+        const double scale = c->p.sigma * c->p.sigma / (c->p.ell * c->p.ell);
+        for (int i = 0; i < 6 * c->K; ++i) grad[i] = scale * b[i];
+    }
+    for (int e = 0; e < c->E; ++e) {
+        if (H_blocks) std::memcpy(H_blocks + 144LL * e, eo[e].H, sizeof(double) * 144);
+        if (edge_pairs) edge_pairs[e] = eo[e].n;
+    }
+    return RKHSBA_OK;
+}
+
+rkhsba_status rkhsba_set_poses_device(rkhsba_ctx* c, const double* d_poses) {
+    if (!c || !d_poses) return fail(c, RKHSBA_EINVAL, "NULL argument");
+    RK_CUDA(c, cudaMemcpyAsync(c->d_poses_cand, d_poses, sizeof(double) * 16 * c->K,
+                               cudaMemcpyDeviceToDevice, c->stream));
+    reset_state(c);
+    return RKHSBA_OK;
+}
+
+rkhsba_status rkhsba_rebuild(rkhsba_ctx* c) {
+    if (!c) return fail(nullptr, RKHSBA_EINVAL, "ctx is NULL");
+    bool alt = false;
+    c->phase_begin(0);
+    cudaMemsetAsync(c->d_cell_start, 0, sizeof(int) * (c->C_total + 1), c->stream);
+    grid_fill(c, &alt);
+    c->phase_end();
+    RK_CUDA(c, cudaGetLastError());
+    return RKHSBA_OK;
+}
+
+rkhsba_status rkhsba_iterate(rkhsba_ctx* c, int32_t n_iters) {
+    if (!c) return fail(nullptr, RKHSBA_EINVAL, "ctx is NULL");
+    if (c->need_initial) lm_initial(c);
+    for (int i = 0; i < n_iters; ++i) lm_iteration(c);
+    RK_CUDA(c, cudaGetLastError());
+    return RKHSBA_OK;
+}
+
+rkhsba_status rkhsba_get_state(rkhsba_ctx* c, double* poses, rkhsba_solve_info* info) {
+    if (!c) return fail(nullptr, RKHSBA_EINVAL, "ctx is NULL");
+    LMState s{};
+    RK_CUDA(c, cudaMemcpyAsync(&s, c->d_state, sizeof(LMState), cudaMemcpyDeviceToHost, c->stream));
+    if (poses)
+        RK_CUDA(c, cudaMemcpyAsync(poses, c->d_poses_cur, sizeof(double) * 16 * c->K,
+                                   cudaMemcpyDeviceToHost, c->stream));
+    RK_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (info) {
+        info->iters = s.iters;
+        info->status = s.done ? s.status : RKHSBA_ENOTCONV;
+        info->final_loss = -s.F_cur;
+        info->lambda = s.lambda;
+        info->pair_terms = s.pair_terms;
+    }
+    return RKHSBA_OK;
+}
+
+rkhsba_status rkhsba_solve(rkhsba_ctx* c, double* poses, rkhsba_solve_info* info) {
+    if (!c) return fail(nullptr, RKHSBA_EINVAL, "ctx is NULL");
+    RK_TRY(check_poses(c, poses));
+    RK_CUDA(c, cudaMemcpyAsync(c->d_poses_cand, poses, sizeof(double) * 16 * c->K, cudaMemcpyHostToDevice,
+                               c->stream));
+    reset_state(c);
+    lm_initial(c);
+    // iterations are issued in small batches between reads of the device
+    // state; once the device marks the solve done the remaining launches of a
+    // batch return at once
+    LMState s{};
+    int issued = 0;
+    while (issued < c->p.max_iters) {
+        const int chunk = std::min(4, c->p.max_iters - issued);
+        for (int i = 0; i < chunk; ++i) lm_iteration(c);
+        issued += chunk;
+        RK_CUDA(c, cudaMemcpyAsync(&s, c->d_state, sizeof(LMState), cudaMemcpyDeviceToHost, c->stream));
+        RK_CUDA(c, cudaStreamSynchronize(c->stream));
+        if (s.done) break;
+    }
+    RK_CUDA(c, cudaGetLastError());
+    rkhsba_solve_info tmp{};
+    RK_TRY(rkhsba_get_state(c, poses, &tmp));
+    if (info) *info = tmp;
+    return tmp.status == RKHSBA_OK ? RKHSBA_OK : RKHSBA_ENOTCONV;
+}
+
+rkhsba_status rkhsba_edge_pairs(rkhsba_ctx* c, const double* poses, int32_t edge, int64_t capacity,
+                                int32_t* i_out, int32_t* j_out, int64_t* n_out) {
+    if (!c) return fail(nullptr, RKHSBA_EINVAL, "ctx is NULL");
+    if (edge < 0 || edge >= c->E) return fail(c, RKHSBA_EINVAL, "edge out of range");
+    if (capacity < 0 || (capacity > 0 && (!i_out || !j_out)) || !n_out)
+        return fail(c, RKHSBA_EINVAL, "bad output buffers");
+    RK_TRY(check_poses(c, poses));
+    cudaStream_t st = c->stream;
+    RK_CUDA(c, cudaMemcpyAsync(c->d_poses_cand, poses, sizeof(double) * 16 * c->K, cudaMemcpyHostToDevice, st));
+    run_eval(c, c->d_poses_cand, nullptr);
+    int* di = nullptr;
+    int* dj = nullptr;
+    unsigned long long* dn = nullptr;
+    cudaError_t e1 = cudaMalloc(&di, sizeof(int) * std::max<int64_t>(capacity, 1));
+    cudaError_t e2 = cudaMalloc(&dj, sizeof(int) * std::max<int64_t>(capacity, 1));
+    cudaError_t e3 = cudaMalloc(&dn, sizeof(unsigned long long));
+    if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess) {
+        cudaFree(di); cudaFree(dj); cudaFree(dn);
+        cudaGetLastError();
+        return fail(c, RKHSBA_ENOMEM, "pair list buffers");
+    }
+    cudaMemsetAsync(dn, 0, sizeof(unsigned long long), st);
+    cudaMemsetAsync(c->d_ntasks + 1, 0, sizeof(int), st);
+    launch_emit_pairs(c->d_tasks, c->d_ntasks, c->d_ntasks + 1, c->d_slots, c->d_edges, c->d_frames,
+                      c->d_cell_start, c->d_pts4, c->gp, edge, c->d_perm_local, capacity, di, dj, dn,
+                      c->num_sms, st);
+    unsigned long long n = 0;
+    cudaMemcpyAsync(&n, dn, sizeof(n), cudaMemcpyDeviceToHost, st);
+    cudaError_t es = cudaStreamSynchronize(st);
+    long long m = std::min<long long>((long long)n, capacity);
+    if (es == cudaSuccess && m > 0) {
+        cudaMemcpy(i_out, di, sizeof(int) * m, cudaMemcpyDeviceToHost);
+        cudaMemcpy(j_out, dj, sizeof(int) * m, cudaMemcpyDeviceToHost);
+    }
+    cudaFree(di); cudaFree(dj); cudaFree(dn);
+    if (es != cudaSuccess) return fail(c, RKHSBA_ECUDA, cudaGetErrorString(es));
+    // frame a of the device pair list is min(edge); report (a-index, b-index)
+    *n_out = (int64_t)n;
+    return RKHSBA_OK;
+}
+
+rkhsba_status rkhsba_profile(rkhsba_ctx* c, int32_t enable, double* ms, int64_t* launches) {
+    if (!c) return fail(nullptr, RKHSBA_EINVAL, "ctx is NULL");
+    if (ms || launches) {
+        RK_CUDA(c, cudaStreamSynchronize(c->stream));
+        double acc_ms[rkhsba_ctx::NPH] = {0, 0, 0, 0, 0};
+        int64_t acc_n[rkhsba_ctx::NPH] = {0, 0, 0, 0, 0};
+        for (auto& r : c->ev_rec) {
+            float t = 0.f;
+            if (cudaEventElapsedTime(&t, c->ev_pool[r.second.first], c->ev_pool[r.second.second]) ==
+                cudaSuccess) {
+                acc_ms[r.first] += t;
+                acc_n[r.first] += 1;
+            }
+        }
+        for (int i = 0; i < rkhsba_ctx::NPH; ++i) {
+            if (ms) ms[i] = acc_ms[i];
+            if (launches) launches[i] = acc_n[i];
+        }
+    }
+    if (enable) {
+        c->ev_rec.clear();
+        c->prof = true;
+    } else {
+        c->prof = false;
+    }
+    return RKHSBA_OK;
+}
+
+rkhsba_status rkhsba_info(const rkhsba_ctx* c, int32_t* n_frames, int32_t* n_edges, int64_t* n_points_total,
+                          int64_t* device_bytes) {
+    if (!c) return fail(nullptr, RKHSBA_EINVAL, "ctx is NULL");
+    if (n_frames) *n_frames = c->K;
+    if (n_edges) *n_edges = c->E;
+    if (n_points_total) *n_points_total = c->N;
+    if (device_bytes) *device_bytes = (int64_t)c->bytes;
+    return RKHSBA_OK;
+}
+
+const char* rkhsba_last_error(const rkhsba_ctx* c) {
+    if (c) return c->err.c_str();
+    return t_err.c_str();
+}
+
+int64_t rkhsba_launch_count(void) { return g_launches.load(); }
+
+}  // extern "C"

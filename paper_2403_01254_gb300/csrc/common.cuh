@@ -1,0 +1,161 @@
+// Shared types and launchers of the RKHS-BA CUDA library (sm_103a).
+//
+// Data layout in HBM (one problem):
+//   * points of all frames sorted by (frame, uniform-grid cell), stable in the
+//     input order inside a cell; per point a float4 of its offset from its own
+//     cell centre (cell-local FP32 coordinates keep |x~| <= h/2, so differences
+//     of nearby points lose nothing even 50 m from the sensor);
+//   * labels in the same order, FP32 rows padded to a multiple of 4 floats or
+//     BF16 rows padded to a multiple of 8 (16-byte aligned rows);
+//   * cell_start[] over dense per-frame grids that carry a one-cell margin, so
+//     every cell of a 3x3x3 stencil around a cell that can hold a neighbour is
+//     addressable without a hash;
+//   * per evaluation: queries (points of frame b moved into frame a) binned by
+//     their home cell of frame a, split into warp tasks of <= 32 queries.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <atomic>
+
+namespace rk {
+
+extern std::atomic<long long> g_launches;
+inline void count_launch(long long n = 1) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+constexpr int MAX_SEM = 32;     // label floats per point
+constexpr int ACC_N = 32;       // int64 accumulator slots per edge
+constexpr int N_MOM = 29;       // used slots (see MomentIndex)
+
+// Fixed-point accumulator layout per edge.  All sums are over the pairs of the
+// edge, in frame-a coordinates: d = x - y', y' = T_ab y.
+//   0 W = sum w            1..3 D = sum w d       4..6 Sy = sum w y'
+//   7..12 Myy = sum w y'y'^T (xx xy xz yy yz zz)
+//   13..21 Mdy = sum w d y'^T (row-major [m][l] = sum w d_m y'_l)
+//   22..27 Q = sum w d d^T (xx xy xz yy yz zz)      28 pair count
+enum MomentClass { MC_W = 0, MC_D = 1, MC_SY = 2, MC_MYY = 3, MC_MDY = 4, MC_Q = 5, MC_CNT = 6, MC_N = 8 };
+
+__host__ __device__ inline int moment_class(int k) {
+    return k == 0 ? MC_W : k < 4 ? MC_D : k < 7 ? MC_SY : k < 13 ? MC_MYY
+         : k < 22 ? MC_MDY : k < 28 ? MC_Q : MC_CNT;
+}
+
+struct FrameDev {
+    long long pt_off;     // first point (input order == sorted order range)
+    int n_pts;
+    int lo[3];            // absolute cell coordinates of grid cell (0,0,0)
+    int dim[3];           // grid extent including a one-cell margin on each side
+    long long cell_off;   // offset of this frame's cells in cell_start[]
+    long long occ_off;    // first occupied-cell id of this frame
+    int n_occ;            // occupied cells
+    float sem_norm_max;   // max |l| over the frame (bounds of the fixed point)
+};
+
+struct EdgeDev {
+    int a, b;             // a < b
+    long long bin_off;    // first bin (bins = cells of frame a's grid)
+    long long wi_off;     // first binning work item (occupied cells of frame b)
+    float scale[MC_N];    // fixed-point scale per moment class (power of two)
+    double inv_scale[MC_N];
+};
+
+struct EdgeXf {           // T_ab = T_a^-1 T_b for one evaluation
+    double R[9];
+    double t[3];
+    float Rf[9];
+};
+
+struct __align__(16) Task { int edge; int cell; int qstart; int qcount; };
+struct __align__(16) Slot { int s; float vx, vy, vz; };
+
+struct EdgeOut {          // FP64 per-edge results of one evaluation
+    double F;             // sigma^2 sum w
+    double E;             // sum w |d|^2
+    long long n;          // pair-terms
+    long long pad;
+    double b[12];         // sum w J^T d, [rho_a phi_a rho_b phi_b]
+    double H[144];        // sum w J^T J, same ordering
+};
+
+struct GridParams {
+    double h, h_inv;      // cell size h = r_c (1 + 2^-10) and its inverse
+    float hf, hf_inv;
+    float rc2;            // r_c^2 in FP32
+    float kg;             // -log2(e) / (2 ell^2)
+    float kc;             // -log2(e) / (2 ell_c^2), 0 without colour
+    int sem_dim, sem_pad, sem_bf16, color;
+};
+
+struct LMState {
+    double lambda;
+    double F_cur, F_cand;
+    double step_inf;
+    double tol_step, tol_rel_f;
+    long long pair_terms;     // summed over evaluations of the solve
+    long long n_cand;         // pair-terms of the last evaluation
+    int iters, max_iters;
+    int done, status;         // status: 0 converged, 4 not converged
+    int first, chol_fail, accepted, pad;
+};
+
+// ------------------------------------------------------------ launchers ----
+// scan.cu
+size_t scan_ws_elems(long long n);
+void scan_exclusive_i64(const long long* in, long long* out, long long n, long long* total,
+                        long long* ws, cudaStream_t st);
+void radix_sort_u32(uint32_t* keys, int* vals, uint32_t* keys_alt, int* vals_alt, long long n,
+                    int nbits, long long* hist, long long* ws, cudaStream_t st, bool* in_alt);
+size_t radix_hist_elems(long long n);
+
+// grid.cu
+void launch_bbox(const double* xyz, const float* sem, const float* rgb, long long N, int K,
+                 const long long* pt_off, int sem_dim, double h_inv, int* cmin, int* cmax,
+                 unsigned* sem_norm_bits, int* err, cudaStream_t st);
+void launch_keys(const double* xyz, long long N, int K, const long long* pt_off,
+                 const FrameDev* frames, double h_inv, uint32_t* keys, int* vals, cudaStream_t st);
+void launch_gather(const double* xyz, const float* sem, const float* rgb, long long N, int K,
+                   const long long* pt_off, const uint32_t* keys, const int* perm, GridParams gp,
+                   long long C_total, float4* pts4, void* sem_sorted, float4* col4,
+                   int* perm_local, int* cell_start, long long* run_flag, cudaStream_t st);
+void launch_occ(const uint32_t* keys, const long long* run_excl, long long N, long long* occ_key,
+                cudaStream_t st);
+void launch_frame_occ(const long long* run_excl, long long N, const long long* total_occ, int K,
+                      const long long* pt_off, long long* occ_first, cudaStream_t st);
+
+// pairs.cu
+void launch_edge_setup(const double* poses, const EdgeDev* edges, int E, EdgeXf* xf,
+                       const int* done, cudaStream_t st);
+void launch_bin(int pass, const EdgeDev* edges, int E, const FrameDev* frames, const EdgeXf* xf,
+                const long long* occ_key, const int* cell_start, const float4* pts4, GridParams gp,
+                int* bin_count, const long long* bin_packed, int* bin_cursor, Slot* slots,
+                long long n_items, const int* done, int num_sms, cudaStream_t st);
+void launch_make_bins(const int* bin_count, long long* bin_val, long long n_bins, const int* done,
+                      cudaStream_t st);
+void launch_emit_tasks(const int* bin_count, const long long* bin_packed, const EdgeDev* edges,
+                       int E, long long n_bins, const long long* total_packed, Task* tasks,
+                       int* n_tasks, const int* done, cudaStream_t st);
+void launch_pairs(const Task* tasks, const int* n_tasks, int* task_counter, const Slot* slots,
+                  const EdgeDev* edges, const FrameDev* frames, const int* cell_start,
+                  const float4* pts4, const void* sem_sorted, const float4* col4, GridParams gp,
+                  long long* acc, const int* done, int num_sms, cudaStream_t st);
+void launch_emit_pairs(const Task* tasks, const int* n_tasks, int* task_counter, const Slot* slots,
+                       const EdgeDev* edges, const FrameDev* frames, const int* cell_start,
+                       const float4* pts4, GridParams gp, int edge_sel, const int* perm_local,
+                       long long capacity, int* i_out, int* j_out, unsigned long long* n_out,
+                       int num_sms, cudaStream_t st);
+
+// solve.cu
+void launch_edge_assemble(const EdgeDev* edges, int E, const EdgeXf* xf, const long long* acc,
+                          double sigma2, EdgeOut* out, const int* done, cudaStream_t st);
+void launch_frame_assemble(const EdgeDev* edges, int E, int K, const int* inc_off,
+                           const int* inc_list, const EdgeOut* eout, double* H, double* b,
+                           double* F, long long* npairs, const int* done, cudaStream_t st);
+void launch_lm_solve(int K, const double* H_cur, const double* b_cur, const double* poses_cur,
+                     double* poses_cand, LMState* st_dev, double* ws, cudaStream_t st);
+void launch_lm_accept(int K, LMState* st_dev, const double* F_cand, const long long* n_cand,
+                      double* poses_cur, const double* poses_cand, double* b_cur,
+                      const double* b_cand, cudaStream_t st);
+void launch_copy_if_accepted(const LMState* st_dev, double* dst, const double* src,
+                             long long n, cudaStream_t st);
+
+}  // namespace rk

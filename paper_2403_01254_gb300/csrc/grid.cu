@@ -1,0 +1,199 @@
+// Grid step of the hot path: per-frame uniform grids over frame-local points.
+//
+// The paper evaluates the double sum of Eq. (inner_product_actual_ba) only
+// over nearby point pairs (Sec. III-B: the sum is sparse because most point
+// pairs are far apart) and names GPU voxel hashing as future work.  Here every
+// frame gets a dense grid of cells of size h = r_c (1 + 2^-10) over its own
+// bounding box plus a one-cell margin; points are sorted by (frame, cell),
+// stable in the input order, and stored as FP32 offsets from their cell
+// centre.  Because points stay in frame-local coordinates the grid never
+// moves with the poses: only the queries of the other frame do.
+#include "common.cuh"
+
+#include <cuda_bf16.h>
+
+namespace rk {
+
+namespace {
+constexpr int GT = 256;
+
+__device__ __forceinline__ int frame_of(const long long* __restrict__ off, int K, long long g) {
+    int lo = 0, hi = K - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (off[mid] <= g) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// floor(x / h) computed as floor(x * h_inv) in FP64; identical in every kernel
+__device__ __forceinline__ double cell_q(double x, double h_inv) { return floor(x * h_inv); }
+
+__global__ void k_bbox(const double* __restrict__ xyz, const float* __restrict__ sem,
+                       const float* __restrict__ rgb, long long N, int K,
+                       const long long* __restrict__ pt_off, int sem_dim, double h_inv,
+                       int* cmin, int* cmax, unsigned* sem_norm_bits, int* err) {
+    const double lim = 536870912.0;   // 2^29
+    for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < N;
+         g += (long long)gridDim.x * blockDim.x) {
+        int f = frame_of(pt_off, K, g);
+        int bad = 0;
+        int c[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            double x = xyz[3 * g + k];
+            if (!isfinite(x)) { bad |= 1; c[k] = 0; continue; }
+            double q = cell_q(x, h_inv);
+            if (!(fabs(q) < lim)) { bad |= 2; c[k] = 0; continue; }
+            c[k] = (int)q;
+        }
+        if (!bad) {
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                atomicMin(&cmin[3 * f + k], c[k]);
+                atomicMax(&cmax[3 * f + k], c[k]);
+            }
+        }
+        if (sem_dim > 0) {
+            float s = 0.f;
+            for (int k = 0; k < sem_dim; ++k) {
+                float v = sem[g * sem_dim + k];
+                if (!isfinite(v)) bad |= 4;
+                s = fmaf(v, v, s);
+            }
+            float nrm = isfinite(s) ? sqrtf(s) : 0.f;
+            atomicMax(&sem_norm_bits[f], __float_as_uint(nrm));
+        }
+        if (rgb) {
+#pragma unroll
+            for (int k = 0; k < 3; ++k)
+                if (!isfinite(rgb[3 * g + k])) bad |= 8;
+        }
+        if (bad) atomicOr(err, bad);
+    }
+}
+
+__global__ void k_keys(const double* __restrict__ xyz, long long N, int K,
+                       const long long* __restrict__ pt_off, const FrameDev* __restrict__ frames,
+                       double h_inv, uint32_t* __restrict__ keys, int* __restrict__ vals) {
+    for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < N;
+         g += (long long)gridDim.x * blockDim.x) {
+        const FrameDev& F = frames[frame_of(pt_off, K, g)];
+        int l[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) l[k] = (int)cell_q(xyz[3 * g + k], h_inv) - F.lo[k];
+        long long key = F.cell_off + ((long long)l[2] * F.dim[1] + l[1]) * F.dim[0] + l[0];
+        keys[g] = (uint32_t)key;
+        vals[g] = (int)g;
+    }
+}
+
+__global__ void k_gather(const double* __restrict__ xyz, const float* __restrict__ sem,
+                         const float* __restrict__ rgb, long long N, int K,
+                         const long long* __restrict__ pt_off, const uint32_t* __restrict__ keys,
+                         const int* __restrict__ perm, GridParams gp, long long C_total,
+                         float4* __restrict__ pts4, void* __restrict__ sem_sorted,
+                         float4* __restrict__ col4, int* __restrict__ perm_local,
+                         int* __restrict__ cell_start, long long* __restrict__ run_flag) {
+    for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < N;
+         s += (long long)gridDim.x * blockDim.x) {
+        const long long g = perm[s];
+        const int f = frame_of(pt_off, K, s);
+        float o[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            double x = xyz[3 * g + k];
+            double ctr = (cell_q(x, gp.h_inv) + 0.5) * gp.h;
+            o[k] = (float)(x - ctr);
+        }
+        pts4[s] = make_float4(o[0], o[1], o[2], 0.f);
+        perm_local[s] = (int)(g - pt_off[f]);
+        if (gp.sem_pad > 0) {
+            if (gp.sem_bf16) {
+                __nv_bfloat16* dst = reinterpret_cast<__nv_bfloat16*>(sem_sorted) + s * gp.sem_pad;
+                for (int k = 0; k < gp.sem_pad; ++k)
+                    dst[k] = __float2bfloat16_rn(k < gp.sem_dim ? sem[g * gp.sem_dim + k] : 0.f);
+            } else {
+                float* dst = reinterpret_cast<float*>(sem_sorted) + s * gp.sem_pad;
+                for (int k = 0; k < gp.sem_pad; ++k) dst[k] = k < gp.sem_dim ? sem[g * gp.sem_dim + k] : 0.f;
+            }
+        }
+        if (gp.color) col4[s] = make_float4(rgb[3 * g], rgb[3 * g + 1], rgb[3 * g + 2], 0.f);
+        // cell_start over every cell of every frame; a run start fills the gap
+        const long long key = keys[s];
+        const bool start = (s == 0) || ((long long)keys[s - 1] != key);
+        run_flag[s] = start ? 1 : 0;
+        if (start) {
+            long long prev = (s == 0) ? -1 : (long long)keys[s - 1];
+            for (long long k = prev + 1; k <= key; ++k) cell_start[k] = (int)s;
+        }
+        if (s == N - 1)
+            for (long long k = key + 1; k <= C_total; ++k) cell_start[k] = (int)N;
+    }
+}
+
+__global__ void k_occ(const uint32_t* __restrict__ keys, const long long* __restrict__ run_excl,
+                      long long N, long long* __restrict__ occ_key) {
+    for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < N;
+         s += (long long)gridDim.x * blockDim.x) {
+        if (s == 0 || keys[s - 1] != keys[s]) occ_key[run_excl[s]] = keys[s];
+    }
+}
+
+__global__ void k_frame_occ(const long long* __restrict__ run_excl, long long N,
+                            const long long* __restrict__ total_occ, int K,
+                            const long long* __restrict__ pt_off, long long* occ_first) {
+    int f = blockIdx.x * blockDim.x + threadIdx.x;
+    if (f > K) return;
+    long long p = pt_off[f];
+    occ_first[f] = p < N ? run_excl[p] : *total_occ;
+}
+
+inline unsigned grid_for(long long n) {
+    long long b = (n + GT - 1) / GT;
+    if (b < 1) b = 1;
+    if (b > 65535LL * 16) b = 65535LL * 16;
+    return (unsigned)b;
+}
+}  // namespace
+
+void launch_bbox(const double* xyz, const float* sem, const float* rgb, long long N, int K,
+                 const long long* pt_off, int sem_dim, double h_inv, int* cmin, int* cmax,
+                 unsigned* sem_norm_bits, int* err, cudaStream_t st) {
+    if (N <= 0) return;
+    k_bbox<<<grid_for(N), GT, 0, st>>>(xyz, sem, rgb, N, K, pt_off, sem_dim, h_inv, cmin, cmax,
+                                       sem_norm_bits, err);
+    count_launch();
+}
+
+void launch_keys(const double* xyz, long long N, int K, const long long* pt_off,
+                 const FrameDev* frames, double h_inv, uint32_t* keys, int* vals, cudaStream_t st) {
+    if (N <= 0) return;
+    k_keys<<<grid_for(N), GT, 0, st>>>(xyz, N, K, pt_off, frames, h_inv, keys, vals);
+    count_launch();
+}
+
+void launch_gather(const double* xyz, const float* sem, const float* rgb, long long N, int K,
+                   const long long* pt_off, const uint32_t* keys, const int* perm, GridParams gp,
+                   long long C_total, float4* pts4, void* sem_sorted, float4* col4,
+                   int* perm_local, int* cell_start, long long* run_flag, cudaStream_t st) {
+    if (N <= 0) return;
+    k_gather<<<grid_for(N), GT, 0, st>>>(xyz, sem, rgb, N, K, pt_off, keys, perm, gp, C_total,
+                                         pts4, sem_sorted, col4, perm_local, cell_start, run_flag);
+    count_launch();
+}
+
+void launch_occ(const uint32_t* keys, const long long* run_excl, long long N, long long* occ_key,
+                cudaStream_t st) {
+    if (N <= 0) return;
+    k_occ<<<grid_for(N), GT, 0, st>>>(keys, run_excl, N, occ_key);
+    count_launch();
+}
+
+void launch_frame_occ(const long long* run_excl, long long N, const long long* total_occ, int K,
+                      const long long* pt_off, long long* occ_first, cudaStream_t st) {
+    k_frame_occ<<<(K + 1 + 127) / 128, 128, 0, st>>>(run_excl, N, total_occ, K, pt_off, occ_first);
+    count_launch();
+}
+
+}  // namespace rk

@@ -1,0 +1,296 @@
+"""Thin ctypes binding of librkhsba.so (argument marshalling only).
+
+The functions carry the names of the C ABI in include/rkhsba.h; ``Problem``
+wraps one context.  Every computation happens in the CUDA library; when the
+library cannot be loaded the import fails loudly (there is no fallback).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import _build
+
+OK, EINVAL, ENOMEM, ECUDA, ENOTCONV, ETIMEOUT, EBUSY = range(7)
+STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENOTCONV", 5: "ETIMEOUT",
+                6: "EBUSY"}
+
+EXPORTS = [
+    "rkhsba_create", "rkhsba_create_device", "rkhsba_destroy", "rkhsba_eval", "rkhsba_solve",
+    "rkhsba_set_poses_device", "rkhsba_rebuild", "rkhsba_iterate", "rkhsba_get_state",
+    "rkhsba_edge_pairs", "rkhsba_info", "rkhsba_last_error", "rkhsba_launch_count",
+    "rkhsba_profile",
+]
+
+
+class RkhsbaError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (STATUS_NAMES.get(status, status), msg))
+        self.status = status
+
+
+class Params(C.Structure):
+    _fields_ = [("ell", C.c_double), ("cutoff_mult", C.c_double), ("sigma", C.c_double),
+                ("ell_color", C.c_double), ("sem_dim", C.c_int32), ("sem_bf16", C.c_int32),
+                ("max_iters", C.c_int32), ("reserved", C.c_int32), ("lambda0", C.c_double),
+                ("tol_step", C.c_double), ("tol_rel_f", C.c_double)]
+
+
+class SolveInfo(C.Structure):
+    _fields_ = [("iters", C.c_int32), ("status", C.c_int32), ("final_loss", C.c_double),
+                ("lam", C.c_double), ("pair_terms", C.c_int64)]
+
+
+_lib = None
+P = C.POINTER
+
+
+def lib_path():
+    return _build.LIB
+
+
+def load(build_if_missing=True):
+    """Load librkhsba.so (building it in-tree first when absent or stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if build_if_missing and not _build.up_to_date():
+        _build.build()
+    if not os.path.exists(_build.LIB):
+        raise ImportError("librkhsba.so is missing; run paper_2403_01254_gb300._build.build()")
+    lib = C.CDLL(_build.LIB)
+    vp = C.c_void_p
+    sig = {
+        "rkhsba_create": [P(vp), C.c_int32, P(C.c_int64), P(C.c_double), P(C.c_float), P(C.c_float),
+                          C.c_int32, P(C.c_int32), P(Params), vp],
+        "rkhsba_create_device": [P(vp), C.c_int32, P(C.c_int64), vp, vp, vp, C.c_int32, P(C.c_int32),
+                                 P(Params), vp],
+        "rkhsba_destroy": [vp],
+        "rkhsba_eval": [vp, P(C.c_double), P(C.c_double), P(C.c_double), P(C.c_double), P(C.c_double),
+                        P(C.c_int64)],
+        "rkhsba_solve": [vp, P(C.c_double), P(SolveInfo)],
+        "rkhsba_set_poses_device": [vp, vp],
+        "rkhsba_rebuild": [vp],
+        "rkhsba_iterate": [vp, C.c_int32],
+        "rkhsba_get_state": [vp, P(C.c_double), P(SolveInfo)],
+        "rkhsba_edge_pairs": [vp, P(C.c_double), C.c_int32, C.c_int64, P(C.c_int32), P(C.c_int32),
+                              P(C.c_int64)],
+        "rkhsba_info": [vp, P(C.c_int32), P(C.c_int32), P(C.c_int64), P(C.c_int64)],
+        "rkhsba_last_error": [vp],
+        "rkhsba_launch_count": [],
+        "rkhsba_profile": [vp, C.c_int32, P(C.c_double), P(C.c_int64)],
+    }
+    for name, args in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = C.c_int
+    lib.rkhsba_destroy.restype = None
+    lib.rkhsba_last_error.restype = C.c_char_p
+    lib.rkhsba_launch_count.restype = C.c_int64
+    _lib = lib
+    return lib
+
+
+def _ptr(a, ctype):
+    return a.ctypes.data_as(P(ctype)) if a is not None else None
+
+
+def _check(status, ctx=None):
+    if status != OK:
+        msg = load().rkhsba_last_error(ctx)
+        raise RkhsbaError(status, msg.decode() if msg else "")
+    return status
+
+
+def make_params(ell, cutoff_mult=3.0, sigma=1.0, ell_color=0.0, sem_dim=0, sem_bf16=0, max_iters=100,
+                lambda0=1e-4, tol_step=1e-10, tol_rel_f=1e-12):
+    return Params(float(ell), float(cutoff_mult), float(sigma), float(ell_color), int(sem_dim),
+                  int(bool(sem_bf16)), int(max_iters), 0, float(lambda0), float(tol_step),
+                  float(tol_rel_f))
+
+
+# ---------------------------------------------------------------- C-ABI ----
+def rkhsba_create(xyz_list, sem_list, rgb_list, edges, params, stream=None):
+    """Host arrays -> context handle (int).  xyz_list: K arrays [N_m, 3]."""
+    lib = load()
+    n = np.array([len(x) for x in xyz_list], dtype=np.int64)
+    xyz = np.ascontiguousarray(np.concatenate([np.asarray(x, np.float64).reshape(-1, 3)
+                                               for x in xyz_list]) if len(xyz_list) else
+                               np.zeros((0, 3)), dtype=np.float64)
+    sem = None
+    if sem_list is not None:
+        sem = np.ascontiguousarray(np.concatenate([np.asarray(s, np.float32).reshape(len(x), -1)
+                                                   for s, x in zip(sem_list, xyz_list)]),
+                                   dtype=np.float32)
+    rgb = None
+    if rgb_list is not None:
+        rgb = np.ascontiguousarray(np.concatenate([np.asarray(c, np.float32).reshape(-1, 3)
+                                                   for c in rgb_list]), dtype=np.float32)
+    e = np.ascontiguousarray(np.asarray(edges, np.int32).reshape(-1))
+    h = C.c_void_p()
+    _check(lib.rkhsba_create(C.byref(h), len(xyz_list), _ptr(n, C.c_int64), _ptr(xyz, C.c_double),
+                             _ptr(sem, C.c_float), _ptr(rgb, C.c_float), len(e) // 2,
+                             _ptr(e, C.c_int32), C.byref(params), stream))
+    return h.value
+
+
+def rkhsba_create_flat(n_points, xyz, sem, rgb, edges, params, stream=None):
+    """Host arrays already laid out as the C ABI wants them (no copy):
+    xyz float64 [N, 3], sem float32 [N, D] or None, rgb float32 [N, 3] or None."""
+    lib = load()
+    n = np.ascontiguousarray(n_points, dtype=np.int64)
+    for a, dt in ((xyz, np.float64), (sem, np.float32), (rgb, np.float32)):
+        if a is not None and (a.dtype != dt or not a.flags.c_contiguous):
+            raise ValueError("rkhsba_create_flat wants C-contiguous %s arrays" % dt.__name__)
+    e = np.ascontiguousarray(np.asarray(edges, np.int32).reshape(-1))
+    h = C.c_void_p()
+    _check(lib.rkhsba_create(C.byref(h), len(n), _ptr(n, C.c_int64), _ptr(xyz, C.c_double),
+                             _ptr(sem, C.c_float), _ptr(rgb, C.c_float), len(e) // 2,
+                             _ptr(e, C.c_int32), C.byref(params), stream))
+    return h.value
+
+
+def rkhsba_create_device(n_points, d_xyz, d_sem, d_rgb, edges, params, stream=None):
+    """Device pointers (ints) -> context handle."""
+    lib = load()
+    n = np.ascontiguousarray(n_points, dtype=np.int64)
+    e = np.ascontiguousarray(np.asarray(edges, np.int32).reshape(-1))
+    h = C.c_void_p()
+    _check(lib.rkhsba_create_device(C.byref(h), len(n), _ptr(n, C.c_int64), d_xyz, d_sem, d_rgb,
+                                    len(e) // 2, _ptr(e, C.c_int32), C.byref(params), stream))
+    return h.value
+
+
+def rkhsba_destroy(ctx):
+    load().rkhsba_destroy(ctx)
+
+
+def rkhsba_eval(ctx, poses, K, E, want_H=True, want_blocks=False):
+    poses = np.ascontiguousarray(poses, dtype=np.float64).reshape(K * 16)
+    loss = np.zeros(1)
+    grad = np.zeros(6 * K)
+    H = np.zeros((6 * K, 6 * K)) if want_H else None
+    blocks = np.zeros((E, 12, 12)) if want_blocks else None
+    pairs = np.zeros(E, dtype=np.int64)
+    _check(load().rkhsba_eval(ctx, _ptr(poses, C.c_double), _ptr(loss, C.c_double),
+                              _ptr(grad, C.c_double), _ptr(H, C.c_double), _ptr(blocks, C.c_double),
+                              _ptr(pairs, C.c_int64)), ctx)
+    return dict(loss=float(loss[0]), grad=grad, H=H, H_blocks=blocks, edge_pairs=pairs,
+                n_pairs=int(pairs.sum()))
+
+
+def rkhsba_solve(ctx, poses, K):
+    T = np.ascontiguousarray(poses, dtype=np.float64).reshape(K * 16).copy()
+    info = SolveInfo()
+    st = load().rkhsba_solve(ctx, _ptr(T, C.c_double), C.byref(info))
+    if st not in (OK, ENOTCONV):
+        _check(st, ctx)
+    return T.reshape(K, 4, 4), dict(iters=info.iters, status=STATUS_NAMES[info.status],
+                                    final_loss=info.final_loss, lam=info.lam,
+                                    pair_terms=int(info.pair_terms))
+
+
+def rkhsba_set_poses_device(ctx, d_poses):
+    _check(load().rkhsba_set_poses_device(ctx, d_poses), ctx)
+
+
+def rkhsba_rebuild(ctx):
+    _check(load().rkhsba_rebuild(ctx), ctx)
+
+
+def rkhsba_iterate(ctx, n):
+    _check(load().rkhsba_iterate(ctx, int(n)), ctx)
+
+
+def rkhsba_get_state(ctx, K):
+    T = np.zeros(K * 16)
+    info = SolveInfo()
+    _check(load().rkhsba_get_state(ctx, _ptr(T, C.c_double), C.byref(info)), ctx)
+    return T.reshape(K, 4, 4), dict(iters=info.iters, status=STATUS_NAMES[info.status],
+                                    final_loss=info.final_loss, lam=info.lam,
+                                    pair_terms=int(info.pair_terms))
+
+
+def rkhsba_edge_pairs(ctx, poses, K, edge, capacity):
+    poses = np.ascontiguousarray(poses, dtype=np.float64).reshape(K * 16)
+    i = np.zeros(max(capacity, 1), np.int32)
+    j = np.zeros(max(capacity, 1), np.int32)
+    n = C.c_int64()
+    _check(load().rkhsba_edge_pairs(ctx, _ptr(poses, C.c_double), int(edge), int(capacity),
+                                    _ptr(i, C.c_int32), _ptr(j, C.c_int32), C.byref(n)), ctx)
+    m = min(n.value, capacity)
+    return i[:m].copy(), j[:m].copy(), n.value
+
+
+def rkhsba_info(ctx):
+    k, e, n, b = C.c_int32(), C.c_int32(), C.c_int64(), C.c_int64()
+    _check(load().rkhsba_info(ctx, C.byref(k), C.byref(e), C.byref(n), C.byref(b)), ctx)
+    return dict(n_frames=k.value, n_edges=e.value, n_points=n.value, device_bytes=b.value)
+
+
+PHASES = ("grid", "bin", "pairs", "assemble", "solve")
+
+
+def rkhsba_profile(ctx, enable, read=False):
+    """Start (enable=1) / stop (0) phase timing; with read=True return
+    {phase: (ms, launches)} of what was recorded (synchronises)."""
+    ms = np.zeros(5) if read else None
+    n = np.zeros(5, np.int64) if read else None
+    _check(load().rkhsba_profile(ctx, int(enable), _ptr(ms, C.c_double), _ptr(n, C.c_int64)), ctx)
+    if read:
+        return {p: (float(ms[k]), int(n[k])) for k, p in enumerate(PHASES)}
+    return None
+
+
+def rkhsba_launch_count():
+    return int(load().rkhsba_launch_count())
+
+
+# ------------------------------------------------------------- wrapper -----
+class Problem:
+    """One RKHS-BA problem resident on the GPU (a C-ABI context)."""
+
+    def __init__(self, xyz, sem=None, rgb=None, edges=None, ell=0.1, cutoff_mult=3.0, sigma=1.0,
+                 ell_color=0.0, sem_bf16=False, max_iters=100, lambda0=1e-4, tol_step=1e-10,
+                 tol_rel_f=1e-12, stream=None):
+        self.K = len(xyz)
+        self.edges = np.asarray(edges, np.int32).reshape(-1, 2)
+        self.E = len(self.edges)
+        sem_dim = 0 if sem is None else int(np.asarray(sem[0]).reshape(len(xyz[0]), -1).shape[1]
+                                            if len(xyz[0]) else np.asarray(sem[0]).shape[-1])
+        self.params = make_params(ell, cutoff_mult, sigma, ell_color, sem_dim, sem_bf16, max_iters,
+                                  lambda0, tol_step, tol_rel_f)
+        self.ctx = rkhsba_create(xyz, sem, rgb, self.edges, self.params, stream)
+
+    @classmethod
+    def from_scene(cls, prob, **over):
+        p = dict(prob["params"])
+        p.update(over)
+        keep = {k: p[k] for k in ("ell", "cutoff_mult", "sigma", "ell_color", "sem_bf16", "max_iters",
+                                  "lambda0", "tol_step", "tol_rel_f") if k in p}
+        return cls(prob["xyz"], prob.get("sem"), prob.get("rgb"), prob["edges"], **keep)
+
+    def eval(self, poses, want_H=True, want_blocks=False):
+        return rkhsba_eval(self.ctx, poses, self.K, self.E, want_H, want_blocks)
+
+    def solve(self, poses0):
+        return rkhsba_solve(self.ctx, poses0, self.K)
+
+    def edge_pairs(self, poses, edge, capacity=1 << 24):
+        return rkhsba_edge_pairs(self.ctx, poses, self.K, edge, capacity)
+
+    def info(self):
+        return rkhsba_info(self.ctx)
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            rkhsba_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
