@@ -121,7 +121,8 @@ def rkhsba_create(xyz_list, sem_list, rgb_list, edges, params, stream=None):
                                np.zeros((0, 3)), dtype=np.float64)
     sem = None
     if sem_list is not None:
-        sem = np.ascontiguousarray(np.concatenate([np.asarray(s, np.float32).reshape(len(x), -1)
+        dim = params.sem_dim
+        sem = np.ascontiguousarray(np.concatenate([np.asarray(s, np.float32).reshape(len(x), dim)
                                                    for s, x in zip(sem_list, xyz_list)]),
                                    dtype=np.float32)
     rgb = None
@@ -258,8 +259,7 @@ class Problem:
         self.K = len(xyz)
         self.edges = np.asarray(edges, np.int32).reshape(-1, 2)
         self.E = len(self.edges)
-        sem_dim = 0 if sem is None else int(np.asarray(sem[0]).reshape(len(xyz[0]), -1).shape[1]
-                                            if len(xyz[0]) else np.asarray(sem[0]).shape[-1])
+        sem_dim = 0 if sem is None else int(np.asarray(sem[0]).shape[-1])
         self.params = make_params(ell, cutoff_mult, sigma, ell_color, sem_dim, sem_bf16, max_iters,
                                   lambda0, tol_step, tol_rel_f)
         self.ctx = rkhsba_create(xyz, sem, rgb, self.edges, self.params, stream)

@@ -43,8 +43,8 @@ def _band_pairs(prob, poses, e):
     P.update(prob["params"])
     rc = P["cutoff_mult"] * P["ell"]
     a, b = (int(v) for v in prob["edges"][e])
-    pa = O._transform(poses[a], np.asarray(prob["xyz"][a], np.float64))
-    pb = O._transform(poses[b], np.asarray(prob["xyz"][b], np.float64))
+    pa = np.asarray(prob["xyz"][a], np.float64) @ poses[a][:3, :3].T + poses[a][:3, 3]
+    pb = np.asarray(prob["xyz"][b], np.float64) @ poses[b][:3, :3].T + poses[b][:3, 3]
     i, j = O.pairs_kdtree(pa, pb, rc * (1 + 2e-6))
     d = np.linalg.norm(pa[i] - pb[j], axis=1)
     m = np.abs(d - rc) <= 1e-6 * rc
