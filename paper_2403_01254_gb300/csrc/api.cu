@@ -72,22 +72,25 @@ struct rkhsba_ctx {
     void* d_sem = nullptr;
     float4* d_col4 = nullptr;
     int* d_perm_local = nullptr;
-    long long* d_run = nullptr;       // run flags, then their exclusive scan
-    long long* d_run_excl = nullptr;
-    long long* d_occ_key = nullptr;
-    long long* d_occ_first = nullptr;  // K+1
+    long long* d_run = nullptr;       // cell run starts of the sorted points
+    const uint32_t* d_pt_cell = nullptr;  // grid cell key of every sorted point
     long long* d_total = nullptr;      // scratch totals [4]
     long long* d_scan_ws = nullptr;
 
-    long long total_bins = 0, n_items = 0, Q_total = 0, max_tasks = 0;
+    long long total_bins = 0, Q_total = 0;
+    int qbits = 0;                     // radix bits of the query keys
     EdgeXf* d_xf = nullptr;
-    int* d_bin_count = nullptr;
-    int* d_bin_cursor = nullptr;
-    long long* d_bin_val = nullptr;
-    long long* d_bin_packed = nullptr;
-    Task* d_tasks = nullptr;
-    Slot* d_slots = nullptr;
-    int* d_ntasks = nullptr;           // [2]: n_tasks, task_counter
+    uint32_t* d_qkey = nullptr;        // home-cell key per query (then sorted)
+    uint32_t* d_qkey_alt = nullptr;
+    int* d_qval = nullptr;             // query index (then sorted)
+    int* d_qval_alt = nullptr;
+    long long* d_qhist = nullptr;
+    float4* d_qrec = nullptr;          // per query: offset from home centre, point index
+    float4* d_slots = nullptr;         // the same in sorted order
+    int* d_bin_first = nullptr;        // first sorted query of each home cell
+    int* d_unit_start = nullptr;       // units of <= 32 queries of one home cell
+    int* d_ucount = nullptr;           // [2]: number of units, unit counter
+    const uint32_t* q_sorted_key = nullptr;
     long long* d_acc = nullptr;
     EdgeOut* d_eout = nullptr;
     int* d_inc_off = nullptr;
@@ -221,6 +224,7 @@ rkhsba_status normalize_params(rkhsba_ctx* ctx, const rkhsba_params* in) {
     g.h_inv = 1.0 / g.h;
     g.hf = (float)g.h;
     g.hf_inv = (float)g.h_inv;
+    g.hf_lo = (float)(g.h - (double)g.hf);
     g.rc2 = (float)(rc * rc);
     const double log2e = 1.4426950408889634;
     g.kg = (float)(-log2e / (2.0 * p.ell * p.ell));
@@ -279,8 +283,7 @@ void grid_fill(rkhsba_ctx* c, bool* keys_in_alt) {
     launch_gather(c->d_xyz, c->d_sem_in, c->d_rgb_in, c->N, c->K, c->d_pt_off, keys, perm, c->gp,
                   c->C_total, c->d_pts4, c->d_sem, c->d_col4, c->d_perm_local, c->d_cell_start,
                   c->d_run, st);
-    scan_exclusive_i64(c->d_run, c->d_run_excl, c->N, c->d_total, c->d_scan_ws, st);
-    launch_occ(keys, c->d_run_excl, c->N, c->d_occ_key, st);
+    c->d_pt_cell = keys;
     *keys_in_alt = alt;
 }
 
@@ -407,52 +410,37 @@ rkhsba_status build(rkhsba_ctx* c, const double* xyz, const float* sem, const fl
     if (c->gp.color) RK_TRY(alloc(c, &c->d_col4, N));
     RK_TRY(alloc(c, &c->d_perm_local, N));
     RK_TRY(alloc(c, &c->d_run, N));
-    RK_TRY(alloc(c, &c->d_run_excl, N));
-    RK_TRY(alloc(c, &c->d_occ_key, N));
-    RK_TRY(alloc(c, &c->d_occ_first, K + 1));
     RK_TRY(alloc(c, &c->d_total, 4));
 
-    // per-edge sizes known so far
+    // per-edge sizes: bins = cells of frame a's grid, queries = points of frame b
     c->total_bins = 0;
     c->Q_total = 0;
     for (int e = 0; e < E; ++e) {
         EdgeDev& Ed = c->edges_h[e];
         const FrameDev& Fa = c->frames_h[Ed.a];
         Ed.bin_off = c->total_bins;
+        Ed.q_off = c->Q_total;
         c->total_bins += (long long)Fa.dim[0] * Fa.dim[1] * Fa.dim[2];
         c->Q_total += c->frames_h[Ed.b].n_pts;
     }
-    long long scan_n = std::max<long long>(std::max<long long>(N, c->total_bins),
-                                           (long long)radix_hist_elems(N));
+    if (c->total_bins >= (1LL << 31) - 2) return fail(c, RKHSBA_EINVAL, "total home cells exceed 2^31");
+    if (c->Q_total >= (1LL << 31) - 64) return fail(c, RKHSBA_EINVAL, "more than 2^31 queries over all edges");
+    c->qbits = 1;
+    while ((1LL << c->qbits) <= c->total_bins) ++c->qbits;   // invalid key sorts last
+    long long scan_n = std::max<long long>((long long)radix_hist_elems(N),
+                                           (long long)radix_hist_elems(c->Q_total));
     RK_TRY(alloc(c, &c->d_scan_ws, (long long)scan_ws_elems(scan_n) + 64));
     RK_CUDA(c, cudaMemsetAsync(c->d_cell_start, 0, sizeof(int) * (c->C_total + 1), st));
     bool alt = false;
     grid_fill(c, &alt);
-    launch_frame_occ(c->d_run_excl, N, c->d_total, K, c->d_pt_off, c->d_occ_first, st);
-    std::vector<long long> occ_first(K + 1);
-    RK_CUDA(c, cudaMemcpyAsync(occ_first.data(), c->d_occ_first, sizeof(long long) * (K + 1),
-                               cudaMemcpyDeviceToHost, st));
-    RK_CUDA(c, cudaStreamSynchronize(st));
     RK_CUDA(c, cudaGetLastError());
-    for (int m = 0; m < K; ++m) {
-        c->frames_h[m].occ_off = occ_first[m];
-        c->frames_h[m].n_occ = (int)(occ_first[m + 1] - occ_first[m]);
-    }
-    RK_CUDA(c, cudaMemcpyAsync(c->d_frames, c->frames_h.data(), sizeof(FrameDev) * K,
-                               cudaMemcpyHostToDevice, st));
 
-    // edges: binning work items and fixed-point scales
+    // fixed-point scales per edge and moment class
     const double rc = c->p.cutoff_mult * c->p.ell;
-    c->n_items = 0;
-    long long nonempty_cap = 0;
     for (int e = 0; e < E; ++e) {
         EdgeDev& Ed = c->edges_h[e];
         const FrameDev& Fa = c->frames_h[Ed.a];
         const FrameDev& Fb = c->frames_h[Ed.b];
-        Ed.wi_off = c->n_items;
-        c->n_items += Fb.n_occ;
-        const long long bins = (long long)Fa.dim[0] * Fa.dim[1] * Fa.dim[2];
-        nonempty_cap += std::min<long long>(bins, Fb.n_pts);
         double smax = (double)Fa.sem_norm_max * (double)Fb.sem_norm_max * (1.0 + 1e-6) + 1e-30;
         double Wb = (double)std::max(Fa.n_pts, 1) * (double)std::max(Fb.n_pts, 1) * smax;
         double R2 = 0.0;
@@ -467,7 +455,6 @@ rkhsba_status build(rkhsba_ctx* c, const double* xyz, const float* sem, const fl
         Ed.scale[MC_CNT] = 1.0f;
         Ed.inv_scale[MC_CNT] = 1.0;
     }
-    c->max_tasks = c->Q_total / 32 + nonempty_cap + E + 1;
     RK_TRY(alloc(c, &c->d_edges, E));
     RK_CUDA(c, cudaMemcpyAsync(c->d_edges, c->edges_h.data(), sizeof(EdgeDev) * E,
                                cudaMemcpyHostToDevice, st));
@@ -487,14 +474,18 @@ rkhsba_status build(rkhsba_ctx* c, const double* xyz, const float* sem, const fl
                                cudaMemcpyHostToDevice, st));
 
     // evaluation buffers
+    const long long Q = c->Q_total;
     RK_TRY(alloc(c, &c->d_xf, E));
-    RK_TRY(alloc(c, &c->d_bin_count, c->total_bins));
-    RK_TRY(alloc(c, &c->d_bin_cursor, c->total_bins));
-    RK_TRY(alloc(c, &c->d_bin_val, c->total_bins));
-    RK_TRY(alloc(c, &c->d_bin_packed, c->total_bins));
-    RK_TRY(alloc(c, &c->d_tasks, c->max_tasks));
-    RK_TRY(alloc(c, &c->d_slots, c->Q_total));
-    RK_TRY(alloc(c, &c->d_ntasks, 4));
+    RK_TRY(alloc(c, &c->d_qkey, Q));
+    RK_TRY(alloc(c, &c->d_qkey_alt, Q));
+    RK_TRY(alloc(c, &c->d_qval, Q));
+    RK_TRY(alloc(c, &c->d_qval_alt, Q));
+    RK_TRY(alloc(c, &c->d_qhist, (long long)radix_hist_elems(Q)));
+    RK_TRY(alloc(c, &c->d_qrec, Q));
+    RK_TRY(alloc(c, &c->d_slots, Q));
+    RK_TRY(alloc(c, &c->d_bin_first, c->total_bins));
+    RK_TRY(alloc(c, &c->d_unit_start, Q));
+    RK_TRY(alloc(c, &c->d_ucount, 4));
     RK_TRY(alloc(c, &c->d_acc, (long long)E * ACC_N));
     RK_TRY(alloc(c, &c->d_eout, E));
     const long long n6 = 6LL * K;
@@ -515,29 +506,34 @@ rkhsba_status build(rkhsba_ctx* c, const double* xyz, const float* sem, const fl
     return RKHSBA_OK;
 }
 
+// Transform and bin the queries of every edge at the device poses `poses`:
+// sorted home-cell keys, sorted query records and the unit list.
+void run_binning(rkhsba_ctx* c, const double* poses, const int* done) {
+    cudaStream_t st = c->stream;
+    launch_edge_setup(poses, c->d_edges, c->E, c->d_frames, c->gp.h, c->d_xf, done, st);
+    cudaMemsetAsync(c->d_ucount, 0, sizeof(int) * 4, st);
+    launch_query_keys(c->d_edges, c->E, c->d_frames, c->d_xf, c->d_pt_cell, c->d_pts4, c->gp, c->Q_total,
+                      c->d_qkey, c->d_qval, c->d_qrec, done, st);
+    bool alt = false;
+    radix_sort_u32(c->d_qkey, c->d_qval, c->d_qkey_alt, c->d_qval_alt, c->Q_total, c->qbits, c->d_qhist,
+                   c->d_scan_ws, st, &alt);
+    c->q_sorted_key = alt ? c->d_qkey_alt : c->d_qkey;
+    const int* qv = alt ? c->d_qval_alt : c->d_qval;
+    launch_query_gather(c->q_sorted_key, qv, c->d_qrec, c->Q_total, c->d_slots, c->d_bin_first, done, st);
+    launch_units(c->q_sorted_key, c->d_bin_first, c->Q_total, c->d_unit_start, c->d_ucount, done, st);
+}
+
 // One evaluation at the device poses `poses`; results into the cand buffers.
 void run_eval(rkhsba_ctx* c, const double* poses, const int* done) {
     cudaStream_t st = c->stream;
     c->phase_begin(1);
-    launch_edge_setup(poses, c->d_edges, c->E, c->d_xf, done, st);
-    cudaMemsetAsync(c->d_bin_count, 0, sizeof(int) * c->total_bins, st);
-    cudaMemsetAsync(c->d_bin_cursor, 0, sizeof(int) * c->total_bins, st);
+    run_binning(c, poses, done);
     cudaMemsetAsync(c->d_acc, 0, sizeof(long long) * c->E * ACC_N, st);
-    cudaMemsetAsync(c->d_ntasks, 0, sizeof(int) * 4, st);
-    launch_bin(0, c->d_edges, c->E, c->d_frames, c->d_xf, c->d_occ_key, c->d_cell_start, c->d_pts4,
-               c->gp, c->d_bin_count, c->d_bin_packed, c->d_bin_cursor, c->d_slots, c->n_items, done,
-               c->num_sms, st);
-    launch_make_bins(c->d_bin_count, c->d_bin_val, c->total_bins, done, st);
-    scan_exclusive_i64(c->d_bin_val, c->d_bin_packed, c->total_bins, c->d_total + 1, c->d_scan_ws, st);
-    launch_emit_tasks(c->d_bin_count, c->d_bin_packed, c->d_edges, c->E, c->total_bins, c->d_total + 1,
-                      c->d_tasks, c->d_ntasks, done, st);
-    launch_bin(1, c->d_edges, c->E, c->d_frames, c->d_xf, c->d_occ_key, c->d_cell_start, c->d_pts4,
-               c->gp, c->d_bin_count, c->d_bin_packed, c->d_bin_cursor, c->d_slots, c->n_items, done,
-               c->num_sms, st);
     c->phase_end();
     c->phase_begin(2);
-    launch_pairs(c->d_tasks, c->d_ntasks, c->d_ntasks + 1, c->d_slots, c->d_edges, c->d_frames,
-                 c->d_cell_start, c->d_pts4, c->d_sem, c->d_col4, c->gp, c->d_acc, done, c->num_sms, st);
+    launch_pairs(c->d_unit_start, c->d_ucount, c->d_ucount + 1, c->q_sorted_key, c->d_slots, c->Q_total,
+                 c->d_edges, c->E, c->d_frames, c->d_cell_start, c->d_pts4, c->d_sem, c->d_col4, c->gp,
+                 c->d_acc, done, c->num_sms, st);
     c->phase_end();
     c->phase_begin(3);
     launch_edge_assemble(c->d_edges, c->E, c->d_xf, c->d_acc, c->p.sigma * c->p.sigma, c->d_eout, done, st);
@@ -760,7 +756,7 @@ rkhsba_status rkhsba_edge_pairs(rkhsba_ctx* c, const double* poses, int32_t edge
     RK_TRY(check_poses(c, poses));
     cudaStream_t st = c->stream;
     RK_CUDA(c, cudaMemcpyAsync(c->d_poses_cand, poses, sizeof(double) * 16 * c->K, cudaMemcpyHostToDevice, st));
-    run_eval(c, c->d_poses_cand, nullptr);
+    run_binning(c, c->d_poses_cand, nullptr);
     int* di = nullptr;
     int* dj = nullptr;
     unsigned long long* dn = nullptr;
@@ -773,10 +769,10 @@ rkhsba_status rkhsba_edge_pairs(rkhsba_ctx* c, const double* poses, int32_t edge
         return fail(c, RKHSBA_ENOMEM, "pair list buffers");
     }
     cudaMemsetAsync(dn, 0, sizeof(unsigned long long), st);
-    cudaMemsetAsync(c->d_ntasks + 1, 0, sizeof(int), st);
-    launch_emit_pairs(c->d_tasks, c->d_ntasks, c->d_ntasks + 1, c->d_slots, c->d_edges, c->d_frames,
-                      c->d_cell_start, c->d_pts4, c->gp, edge, c->d_perm_local, capacity, di, dj, dn,
-                      c->num_sms, st);
+    cudaMemsetAsync(c->d_ucount + 1, 0, sizeof(int), st);
+    launch_emit_pairs(c->d_unit_start, c->d_ucount, c->d_ucount + 1, c->q_sorted_key, c->d_slots, c->Q_total,
+                      c->d_edges, c->E, c->d_frames, c->d_cell_start, c->d_pts4, c->gp, edge, c->d_perm_local,
+                      capacity, di, dj, dn, c->num_sms, st);
     unsigned long long n = 0;
     cudaMemcpyAsync(&n, dn, sizeof(n), cudaMemcpyDeviceToHost, st);
     cudaError_t es = cudaStreamSynchronize(st);

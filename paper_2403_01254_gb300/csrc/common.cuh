@@ -10,8 +10,10 @@
 //   * cell_start[] over dense per-frame grids that carry a one-cell margin, so
 //     every cell of a 3x3x3 stencil around a cell that can hold a neighbour is
 //     addressable without a hash;
-//   * per evaluation: queries (points of frame b moved into frame a) binned by
-//     their home cell of frame a, split into warp tasks of <= 32 queries.
+//   * per evaluation: queries (points of frame b moved into frame a) sorted
+//     stably by their home cell of frame a and cut into units of <= 32
+//     queries of one home cell; a warp takes a unit and streams the
+//     candidates of the 27 surrounding cells through its lanes.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -46,27 +48,28 @@ struct FrameDev {
     int lo[3];            // absolute cell coordinates of grid cell (0,0,0)
     int dim[3];           // grid extent including a one-cell margin on each side
     long long cell_off;   // offset of this frame's cells in cell_start[]
-    long long occ_off;    // first occupied-cell id of this frame
-    int n_occ;            // occupied cells
     float sem_norm_max;   // max |l| over the frame (bounds of the fixed point)
 };
 
 struct EdgeDev {
     int a, b;             // a < b
     long long bin_off;    // first bin (bins = cells of frame a's grid)
-    long long wi_off;     // first binning work item (occupied cells of frame b)
+    long long q_off;      // first query (queries = points of frame b)
     float scale[MC_N];    // fixed-point scale per moment class (power of two)
     double inv_scale[MC_N];
 };
 
-struct EdgeXf {           // T_ab = T_a^-1 T_b for one evaluation
+// T_ab = T_a^-1 T_b for one evaluation, plus the map from frame-b grid
+// indices l (cell c = lo_b + l) to frame-a positions of cell centres,
+//   P(l) = A l + B,  A = h R_ab,  B = R_ab (lo_b + 1/2) h + t_ab,
+// as double-float pairs (hi + lo) so that queries need no FP64.
+struct EdgeXf {
     double R[9];
     double t[3];
     float Rf[9];
+    float Ahi[9], Alo[9];
+    float Bhi[3], Blo[3];
 };
-
-struct __align__(16) Task { int edge; int cell; int qstart; int qcount; };
-struct __align__(16) Slot { int s; float vx, vy, vz; };
 
 struct EdgeOut {          // FP64 per-edge results of one evaluation
     double F;             // sigma^2 sum w
@@ -79,7 +82,7 @@ struct EdgeOut {          // FP64 per-edge results of one evaluation
 
 struct GridParams {
     double h, h_inv;      // cell size h = r_c (1 + 2^-10) and its inverse
-    float hf, hf_inv;
+    float hf, hf_inv, hf_lo;  // FP32 h, 1/h and the remainder h - hf
     float rc2;            // r_c^2 in FP32
     float kg;             // -log2(e) / (2 ell^2)
     float kc;             // -log2(e) / (2 ell_c^2), 0 without colour
@@ -117,32 +120,29 @@ void launch_gather(const double* xyz, const float* sem, const float* rgb, long l
                    const long long* pt_off, const uint32_t* keys, const int* perm, GridParams gp,
                    long long C_total, float4* pts4, void* sem_sorted, float4* col4,
                    int* perm_local, int* cell_start, long long* run_flag, cudaStream_t st);
-void launch_occ(const uint32_t* keys, const long long* run_excl, long long N, long long* occ_key,
-                cudaStream_t st);
-void launch_frame_occ(const long long* run_excl, long long N, const long long* total_occ, int K,
-                      const long long* pt_off, long long* occ_first, cudaStream_t st);
 
 // pairs.cu
-void launch_edge_setup(const double* poses, const EdgeDev* edges, int E, EdgeXf* xf,
-                       const int* done, cudaStream_t st);
-void launch_bin(int pass, const EdgeDev* edges, int E, const FrameDev* frames, const EdgeXf* xf,
-                const long long* occ_key, const int* cell_start, const float4* pts4, GridParams gp,
-                int* bin_count, const long long* bin_packed, int* bin_cursor, Slot* slots,
-                long long n_items, const int* done, int num_sms, cudaStream_t st);
-void launch_make_bins(const int* bin_count, long long* bin_val, long long n_bins, const int* done,
-                      cudaStream_t st);
-void launch_emit_tasks(const int* bin_count, const long long* bin_packed, const EdgeDev* edges,
-                       int E, long long n_bins, const long long* total_packed, Task* tasks,
-                       int* n_tasks, const int* done, cudaStream_t st);
-void launch_pairs(const Task* tasks, const int* n_tasks, int* task_counter, const Slot* slots,
-                  const EdgeDev* edges, const FrameDev* frames, const int* cell_start,
-                  const float4* pts4, const void* sem_sorted, const float4* col4, GridParams gp,
-                  long long* acc, const int* done, int num_sms, cudaStream_t st);
-void launch_emit_pairs(const Task* tasks, const int* n_tasks, int* task_counter, const Slot* slots,
-                       const EdgeDev* edges, const FrameDev* frames, const int* cell_start,
-                       const float4* pts4, GridParams gp, int edge_sel, const int* perm_local,
-                       long long capacity, int* i_out, int* j_out, unsigned long long* n_out,
-                       int num_sms, cudaStream_t st);
+void launch_edge_setup(const double* poses, const EdgeDev* edges, int E, const FrameDev* frames,
+                       double h, EdgeXf* xf, const int* done, cudaStream_t st);
+void launch_query_keys(const EdgeDev* edges, int E, const FrameDev* frames, const EdgeXf* xf,
+                       const uint32_t* pt_cell, const float4* pts4, GridParams gp, long long Q,
+                       uint32_t* qkey, int* qval, float4* qrec, const int* done, cudaStream_t st);
+void launch_query_gather(const uint32_t* qkey_sorted, const int* qval_sorted, const float4* qrec,
+                         long long Q, float4* slots, int* bin_first, const int* done,
+                         cudaStream_t st);
+void launch_units(const uint32_t* qkey_sorted, const int* bin_first, long long Q, int* unit_start,
+                  int* n_units, const int* done, cudaStream_t st);
+void launch_pairs(const int* unit_start, const int* n_units, int* unit_counter,
+                  const uint32_t* qkey, const float4* slots, long long Q, const EdgeDev* edges, int E,
+                  const FrameDev* frames, const int* cell_start, const float4* pts4,
+                  const void* sem_sorted, const float4* col4, GridParams gp, long long* acc,
+                  const int* done, int num_sms, cudaStream_t st);
+void launch_emit_pairs(const int* unit_start, const int* n_units, int* unit_counter,
+                       const uint32_t* qkey, const float4* slots, long long Q, const EdgeDev* edges,
+                       int E, const FrameDev* frames, const int* cell_start, const float4* pts4,
+                       GridParams gp, int edge_sel, const int* perm_local, long long capacity,
+                       int* i_out, int* j_out, unsigned long long* n_out, int num_sms,
+                       cudaStream_t st);
 
 // solve.cu
 void launch_edge_assemble(const EdgeDev* edges, int E, const EdgeXf* xf, const long long* acc,

@@ -132,23 +132,6 @@ __global__ void k_gather(const double* __restrict__ xyz, const float* __restrict
     }
 }
 
-__global__ void k_occ(const uint32_t* __restrict__ keys, const long long* __restrict__ run_excl,
-                      long long N, long long* __restrict__ occ_key) {
-    for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < N;
-         s += (long long)gridDim.x * blockDim.x) {
-        if (s == 0 || keys[s - 1] != keys[s]) occ_key[run_excl[s]] = keys[s];
-    }
-}
-
-__global__ void k_frame_occ(const long long* __restrict__ run_excl, long long N,
-                            const long long* __restrict__ total_occ, int K,
-                            const long long* __restrict__ pt_off, long long* occ_first) {
-    int f = blockIdx.x * blockDim.x + threadIdx.x;
-    if (f > K) return;
-    long long p = pt_off[f];
-    occ_first[f] = p < N ? run_excl[p] : *total_occ;
-}
-
 inline unsigned grid_for(long long n) {
     long long b = (n + GT - 1) / GT;
     if (b < 1) b = 1;
@@ -180,19 +163,6 @@ void launch_gather(const double* xyz, const float* sem, const float* rgb, long l
     if (N <= 0) return;
     k_gather<<<grid_for(N), GT, 0, st>>>(xyz, sem, rgb, N, K, pt_off, keys, perm, gp, C_total,
                                          pts4, sem_sorted, col4, perm_local, cell_start, run_flag);
-    count_launch();
-}
-
-void launch_occ(const uint32_t* keys, const long long* run_excl, long long N, long long* occ_key,
-                cudaStream_t st) {
-    if (N <= 0) return;
-    k_occ<<<grid_for(N), GT, 0, st>>>(keys, run_excl, N, occ_key);
-    count_launch();
-}
-
-void launch_frame_occ(const long long* run_excl, long long N, const long long* total_occ, int K,
-                      const long long* pt_off, long long* occ_first, cudaStream_t st) {
-    k_frame_occ<<<(K + 1 + 127) / 128, 128, 0, st>>>(run_excl, N, total_occ, K, pt_off, occ_first);
     count_launch();
 }
 

@@ -1,37 +1,68 @@
 // Candidate search and pair kernel of the hot path.
 //
-// For every edge (a, b) of the pose graph, every point y_j of frame b is moved
-// into frame a (y' = T_ab y, T_ab = T_a^-1 T_b; the relative transform of
-// Eq. inner_product_actual_ba written in frame a, where |T_a x - T_b y| =
-// |x - T_ab y| because SE(3) acts by isometries) and binned by the frame-a
-// grid cell that contains it.  A warp then takes <= 32 queries of one home
-// cell and walks the 27 cells around it together: candidates are read once
-// per warp (broadcast loads) and each lane tests its own query.  For every
-// pair inside r_c the lane forms the weight
+// For every edge (a, b) of the pose graph the points y_j of frame b are the
+// queries: each is moved into frame a (y' = T_ab y, T_ab = T_a^-1 T_b; the
+// pair distance of Eq. inner_product_actual_ba written in frame a, since
+// |T_a x - T_b y| = |x - T_ab y|) and keyed by the frame-a grid cell holding
+// it.  A stable radix sort groups the queries by home cell (order inside a
+// cell = frame-b order, so results do not depend on thread timing), and the
+// groups are cut into units of <= 32 queries.  A warp takes one unit, stages
+// its queries in shared memory and streams the candidates of the 27
+// surrounding cells through its lanes (one candidate per lane).  Every lane
+// tests its candidate against all queries, keeps a bit mask of the pairs
+// inside r_c, and walks its own set bits to form the weight
 //     w = <l_i, l_j> * k_c(c_i, c_j) * exp(-|d|^2 / (2 ell^2))      Eq. (irls_weight)
-// and accumulates W = sum w, D = sum w d, Q = sum w d d^T with d = x - y'.
-// Per query these become the 28 edge moments (see common.cuh) in frame-a
-// coordinates, which fix the loss, the gradient of Eq. (inner_product_reformat)
-// and the Gauss-Newton blocks of Eq. (irls_final) exactly.
+// and the sums W = sum w, D = sum w d, Q = sum w d d^T (d = x - y').  With
+// y' = x - d these fold into the 28 edge moments (layout in common.cuh),
+// which fix the loss, the gradient of Eq. (inner_product_reformat) and the
+// Gauss-Newton blocks of Eq. (irls_final).  Each lane's moments are rounded to
+// 64-bit fixed point before any cross-lane sum, so edge totals are exact
+// integer sums, independent of which warp ran which unit.
 //
-// Every per-query contribution is rounded to 64-bit fixed point (power-of-two
-// scale per moment class and edge) before any cross-query sum, so the edge
-// totals are exact integer sums: independent of the order in which warps run,
-// of the binning order and of which other problems share the launch.
+// No FP64 arithmetic runs per query: the frame-a position of a frame-b cell
+// centre comes from a per-edge affine map held as double-float pairs, evaluated
+// with error-free transformations (Dekker product, Knuth sum) on the FP32 pipe.
 #include "common.cuh"
 
 namespace rk {
 
 namespace {
 constexpr unsigned FULL = 0xffffffffu;
+constexpr uint32_t NO_KEY = 0xffffffffu;
+
+// ---------------------------------------------------------- double-float --
+struct df { float hi, lo; };
+
+__device__ __forceinline__ df two_sum(float a, float b) {
+    const float s = a + b;
+    const float bb = s - a;
+    const float e = (a - (s - bb)) + (b - bb);
+    return {s, e};
+}
+__device__ __forceinline__ df fast_two_sum(float a, float b) {
+    const float s = a + b;
+    return {s, b - (s - a)};
+}
+__device__ __forceinline__ df df_add(df a, df b) {
+    const df s = two_sum(a.hi, b.hi);
+    return fast_two_sum(s.hi, s.lo + a.lo + b.lo);
+}
+// (hi + lo) * c for a float c holding a small integer or half-integer
+__device__ __forceinline__ df df_mul_f(float hi, float lo, float c) {
+    const float p = hi * c;
+    const float e = fmaf(hi, c, -p);
+    return fast_two_sum(p, fmaf(lo, c, e));
+}
 
 __global__ void k_edge_setup(const double* __restrict__ poses, const EdgeDev* __restrict__ edges,
-                             int E, EdgeXf* __restrict__ xf, const int* done) {
+                             int E, const FrameDev* __restrict__ frames, double h,
+                             EdgeXf* __restrict__ xf, const int* done) {
     if (done && *done) return;
-    int e = blockIdx.x * blockDim.x + threadIdx.x;
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= E) return;
     const double* Ta = poses + 16 * edges[e].a;
     const double* Tb = poses + 16 * edges[e].b;
+    const FrameDev& Fb = frames[edges[e].b];
     EdgeXf X;
     // R_ab = R_a^T R_b,  t_ab = R_a^T (t_b - t_a)
     for (int r = 0; r < 3; ++r)
@@ -41,16 +72,28 @@ __global__ void k_edge_setup(const double* __restrict__ poses, const EdgeDev* __
             X.R[3 * r + c] = s;
             X.Rf[3 * r + c] = (float)s;
         }
-    double dt[3] = {Tb[3] - Ta[3], Tb[7] - Ta[7], Tb[11] - Ta[11]};
+    const double dt[3] = {Tb[3] - Ta[3], Tb[7] - Ta[7], Tb[11] - Ta[11]};
     for (int r = 0; r < 3; ++r) X.t[r] = Ta[r] * dt[0] + Ta[4 + r] * dt[1] + Ta[8 + r] * dt[2];
+    // P(l) = h R l + [R (lo_b + 1/2) h + t]
+    for (int r = 0; r < 3; ++r) {
+        double B = X.t[r];
+        for (int c = 0; c < 3; ++c) {
+            const double A = h * X.R[3 * r + c];
+            X.Ahi[3 * r + c] = (float)A;
+            X.Alo[3 * r + c] = (float)(A - (double)(float)A);
+            B += X.R[3 * r + c] * ((double)Fb.lo[c] + 0.5) * h;
+        }
+        X.Bhi[r] = (float)B;
+        X.Blo[r] = (float)(B - (double)(float)B);
+    }
     xf[e] = X;
 }
 
-__device__ __forceinline__ int find_edge_wi(const EdgeDev* __restrict__ edges, int E, long long it) {
+__device__ __forceinline__ int find_edge_q(const EdgeDev* __restrict__ edges, int E, long long q) {
     int lo = 0, hi = E - 1;
     while (lo < hi) {
-        int mid = (lo + hi + 1) >> 1;
-        if (edges[mid].wi_off <= it) lo = mid; else hi = mid - 1;
+        const int mid = (lo + hi + 1) >> 1;
+        if (edges[mid].q_off <= q) lo = mid; else hi = mid - 1;
     }
     return lo;
 }
@@ -58,132 +101,100 @@ __device__ __forceinline__ int find_edge_wi(const EdgeDev* __restrict__ edges, i
 __device__ __forceinline__ int find_edge_bin(const EdgeDev* __restrict__ edges, int E, long long bin) {
     int lo = 0, hi = E - 1;
     while (lo < hi) {
-        int mid = (lo + hi + 1) >> 1;
+        const int mid = (lo + hi + 1) >> 1;
         if (edges[mid].bin_off <= bin) lo = mid; else hi = mid - 1;
     }
     return lo;
 }
 
-// One warp per (edge, occupied cell of frame b).  Lane 0 moves the cell centre
-// into frame a in FP64 and splits it into an integer cell K and an FP32
-// remainder F; each lane then moves its points in FP32 relative to K, so no
-// large coordinate ever enters FP32 arithmetic.
-template <int PASS>
-__global__ void __launch_bounds__(256) k_bin(const EdgeDev* __restrict__ edges, int E,
-                                             const FrameDev* __restrict__ frames,
-                                             const EdgeXf* __restrict__ xf,
-                                             const long long* __restrict__ occ_key,
-                                             const int* __restrict__ cell_start,
-                                             const float4* __restrict__ pts4, GridParams gp,
-                                             int* __restrict__ bin_count,
-                                             const long long* __restrict__ bin_packed,
-                                             int* __restrict__ bin_cursor, Slot* __restrict__ slots,
-                                             long long n_items, const int* done) {
+// One thread per query: frame-a home cell key and the query's FP32 offset
+// from that cell's centre.
+__global__ void k_query_keys(const EdgeDev* __restrict__ edges, int E, const FrameDev* __restrict__ frames,
+                             const EdgeXf* __restrict__ xf, const uint32_t* __restrict__ pt_cell,
+                             const float4* __restrict__ pts4, GridParams gp, long long Q,
+                             uint32_t* __restrict__ qkey, int* __restrict__ qval,
+                             float4* __restrict__ qrec, const int* done) {
     if (done && *done) return;
-    const int lane = threadIdx.x & 31;
-    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
-    for (long long it = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; it < n_items;
-         it += nwarps) {
-        const int e = find_edge_wi(edges, E, it);
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < Q;
+         q += (long long)gridDim.x * blockDim.x) {
+        const int e = find_edge_q(edges, E, q);
         const EdgeDev& Ed = edges[e];
         const FrameDev& Fa = frames[Ed.a];
         const FrameDev& Fb = frames[Ed.b];
-        const long long key = occ_key[Fb.occ_off + (it - Ed.wi_off)];
-        const int beg = cell_start[key], end = cell_start[key + 1];
-        int Kx = 0, Ky = 0, Kz = 0;
-        float Fx = 0.f, Fy = 0.f, Fz = 0.f;
-        if (lane == 0) {
-            long long loc = key - Fb.cell_off;
-            int cx = (int)(loc % Fb.dim[0]);
-            long long r = loc / Fb.dim[0];
-            int cy = (int)(r % Fb.dim[1]);
-            int cz = (int)(r / Fb.dim[1]);
-            double o[3] = {((double)(cx + Fb.lo[0]) + 0.5) * gp.h, ((double)(cy + Fb.lo[1]) + 0.5) * gp.h,
-                           ((double)(cz + Fb.lo[2]) + 0.5) * gp.h};
-            const EdgeXf& X = xf[e];
-            double P[3];
-            for (int k = 0; k < 3; ++k)
-                P[k] = fma(X.R[3 * k + 2], o[2], fma(X.R[3 * k + 1], o[1], fma(X.R[3 * k], o[0], X.t[k])));
-            double Kd[3];
-            // clamp keeps the int conversion defined for any pose; a clamped
-            // cell lies far outside every grid and is dropped below
-            for (int k = 0; k < 3; ++k) Kd[k] = fmin(fmax(floor(P[k] * gp.h_inv), -1073741824.0), 1073741824.0);
-            Kx = (int)Kd[0]; Ky = (int)Kd[1]; Kz = (int)Kd[2];
-            Fx = (float)(P[0] - (Kd[0] + 0.5) * gp.h);
-            Fy = (float)(P[1] - (Kd[1] + 0.5) * gp.h);
-            Fz = (float)(P[2] - (Kd[2] + 0.5) * gp.h);
+        const int s = (int)(Fb.pt_off + (q - Ed.q_off));
+        const int l = (int)((long long)pt_cell[s] - Fb.cell_off);
+        const float lf[3] = {(float)(l % Fb.dim[0]), (float)((l / Fb.dim[0]) % Fb.dim[1]),
+                             (float)(l / (Fb.dim[0] * Fb.dim[1]))};
+        const EdgeXf& X = xf[e];
+        float K[3], F[3];
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+            df P = {X.Bhi[r], X.Blo[r]};
+#pragma unroll
+            for (int c = 0; c < 3; ++c) P = df_add(P, df_mul_f(X.Ahi[3 * r + c], X.Alo[3 * r + c], lf[c]));
+            float k = floorf(P.hi * gp.hf_inv);
+            k = fminf(fmaxf(k, -4194304.f), 4194304.f);
+            df C = df_mul_f(gp.hf, gp.hf_lo, k + 0.5f);
+            df Rm = df_add(P, {-C.hi, -C.lo});
+            float f = Rm.hi + Rm.lo;
+            if (f < -0.5f * gp.hf) { k -= 1.f; C = df_mul_f(gp.hf, gp.hf_lo, k + 0.5f);
+                                     Rm = df_add(P, {-C.hi, -C.lo}); f = Rm.hi + Rm.lo; }
+            else if (f >= 0.5f * gp.hf) { k += 1.f; C = df_mul_f(gp.hf, gp.hf_lo, k + 0.5f);
+                                          Rm = df_add(P, {-C.hi, -C.lo}); f = Rm.hi + Rm.lo; }
+            K[r] = k;
+            F[r] = f;
         }
-        Kx = __shfl_sync(FULL, Kx, 0); Ky = __shfl_sync(FULL, Ky, 0); Kz = __shfl_sync(FULL, Kz, 0);
-        Fx = __shfl_sync(FULL, Fx, 0); Fy = __shfl_sync(FULL, Fy, 0); Fz = __shfl_sync(FULL, Fz, 0);
-        const float* R = xf[e].Rf;
-        const float r0 = R[0], r1 = R[1], r2 = R[2], r3 = R[3], r4 = R[4], r5 = R[5], r6 = R[6],
-                    r7 = R[7], r8 = R[8];
-        for (int s = beg + lane; s < end; s += 32) {
-            const float4 p = pts4[s];
-            const float vx = fmaf(r2, p.z, fmaf(r1, p.y, fmaf(r0, p.x, Fx)));
-            const float vy = fmaf(r5, p.z, fmaf(r4, p.y, fmaf(r3, p.x, Fy)));
-            const float vz = fmaf(r8, p.z, fmaf(r7, p.y, fmaf(r6, p.x, Fz)));
-            const float mx = floorf(fmaf(vx, gp.hf_inv, 0.5f));
-            const float my = floorf(fmaf(vy, gp.hf_inv, 0.5f));
-            const float mz = floorf(fmaf(vz, gp.hf_inv, 0.5f));
-            const int hx = Kx + (int)mx - Fa.lo[0];
-            const int hy = Ky + (int)my - Fa.lo[1];
-            const int hz = Kz + (int)mz - Fa.lo[2];
-            if (hx < 0 || hy < 0 || hz < 0 || hx >= Fa.dim[0] || hy >= Fa.dim[1] || hz >= Fa.dim[2])
-                continue;   // no frame-a point within one cell: no neighbour possible
-            const long long bin = Ed.bin_off + ((long long)hz * Fa.dim[1] + hy) * Fa.dim[0] + hx;
-            if (PASS == 0) {
-                atomicAdd(&bin_count[bin], 1);
-            } else {
-                const int qstart = (int)(bin_packed[bin] & 0xffffffffLL);
-                const int r = atomicAdd(&bin_cursor[bin], 1);
-                if (r >= bin_count[bin]) continue;   // never past the counted range
-                const int pos = qstart + r;
-                Slot q;
-                q.s = s;
-                q.vx = fmaf(-mx, gp.hf, vx);
-                q.vy = fmaf(-my, gp.hf, vy);
-                q.vz = fmaf(-mz, gp.hf, vz);
-                slots[pos] = q;
-            }
-        }
+        const float4 p = pts4[s];
+        const float* R = X.Rf;
+        const float vx = fmaf(R[2], p.z, fmaf(R[1], p.y, fmaf(R[0], p.x, F[0])));
+        const float vy = fmaf(R[5], p.z, fmaf(R[4], p.y, fmaf(R[3], p.x, F[1])));
+        const float vz = fmaf(R[8], p.z, fmaf(R[7], p.y, fmaf(R[6], p.x, F[2])));
+        const float mx = floorf(fmaf(vx, gp.hf_inv, 0.5f));
+        const float my = floorf(fmaf(vy, gp.hf_inv, 0.5f));
+        const float mz = floorf(fmaf(vz, gp.hf_inv, 0.5f));
+        const int hx = (int)(K[0] + mx) - Fa.lo[0];
+        const int hy = (int)(K[1] + my) - Fa.lo[1];
+        const int hz = (int)(K[2] + mz) - Fa.lo[2];
+        uint32_t key = NO_KEY;
+        if (hx >= 0 && hy >= 0 && hz >= 0 && hx < Fa.dim[0] && hy < Fa.dim[1] && hz < Fa.dim[2])
+            key = (uint32_t)(Ed.bin_off + ((long long)hz * Fa.dim[1] + hy) * Fa.dim[0] + hx);
+        qkey[q] = key;
+        qval[q] = (int)q;
+        qrec[q] = make_float4(fmaf(-mx, gp.hf, vx), fmaf(-my, gp.hf, vy), fmaf(-mz, gp.hf, vz),
+                              __int_as_float(s));
     }
 }
 
-// count -> packed (count | warp tasks << 32) for one scan of both prefix sums
-__global__ void k_make_bins(const int* __restrict__ cnt, long long* __restrict__ val, long long n,
-                            const int* done) {
+__global__ void k_query_gather(const uint32_t* __restrict__ key, const int* __restrict__ val,
+                               const float4* __restrict__ qrec, long long Q, float4* __restrict__ slots,
+                               int* __restrict__ bin_first, const int* done) {
     if (done && *done) return;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-         i += (long long)gridDim.x * blockDim.x) {
-        long long c = cnt[i];
-        val[i] = c | (((c + 31) >> 5) << 32);
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < Q;
+         k += (long long)gridDim.x * blockDim.x) {
+        slots[k] = qrec[val[k]];
+        const uint32_t kk = key[k];
+        if (kk != NO_KEY && (k == 0 || key[k - 1] != kk)) bin_first[kk] = (int)k;
     }
 }
 
-__global__ void k_emit_tasks(const int* __restrict__ cnt, const long long* __restrict__ packed,
-                             const EdgeDev* __restrict__ edges, int E, long long n_bins,
-                             const long long* __restrict__ total, Task* __restrict__ tasks,
-                             int* __restrict__ n_tasks, const int* done) {
+// a unit starts at the first query of a home cell and every 32 queries after
+__global__ void k_units(const uint32_t* __restrict__ key, const int* __restrict__ bin_first, long long Q,
+                        int* __restrict__ unit_start, int* __restrict__ n_units, const int* done) {
     if (done && *done) return;
-    if (blockIdx.x == 0 && threadIdx.x == 0) *n_tasks = (int)(*total >> 32);
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n_bins;
-         i += (long long)gridDim.x * blockDim.x) {
-        const int c = cnt[i];
-        if (c == 0) continue;
-        const long long p = packed[i];
-        const int qs = (int)(p & 0xffffffffLL);
-        const int ts = (int)(p >> 32);
-        const int e = find_edge_bin(edges, E, i);
-        const int cell = (int)(i - edges[e].bin_off);
-        for (int k = 0; 32 * k < c; ++k) {
-            Task t;
-            t.edge = e;
-            t.cell = cell;
-            t.qstart = qs + 32 * k;
-            t.qcount = min(32, c - 32 * k);
-            tasks[ts + k] = t;
+    const int lane = threadIdx.x & 31;
+    for (long long base = (blockIdx.x * (long long)blockDim.x + threadIdx.x) & ~31LL; base < Q;
+         base += (long long)gridDim.x * blockDim.x) {
+        const long long k = base + lane;
+        bool st = false;
+        if (k < Q) {
+            const uint32_t kk = key[k];
+            st = kk != NO_KEY && ((k - bin_first[kk]) & 31) == 0;
         }
+        const unsigned m = __ballot_sync(FULL, st);
+        int off = 0;
+        if (lane == 0 && m) off = atomicAdd(n_units, __popc(m));
+        off = __shfl_sync(FULL, off, 0);
+        if (st) unit_start[off + __popc(m & ((1u << lane) - 1u))] = (int)k;
     }
 }
 
@@ -257,164 +268,337 @@ struct Sem<DP, true> {    // BF16 rows of DP values (DP % 8 == 0), FP32 products
     }
 };
 
+// Label rows staged in shared memory (FP32 or BF16 rows) and their dot
+// product with a row held in registers.
+template <int DP, bool BF16>
+struct SemRow;
+template <int DP>
+struct SemRow<DP, false> {
+    static constexpr int WORDS = DP;          // 32-bit words per row
+    __device__ __forceinline__ static void stage(float* dst, const void* base, int i) {
+        const float4* src = reinterpret_cast<const float4*>(base) + (size_t)i * (DP / 4);
+        float4* d = reinterpret_cast<float4*>(dst);
+#pragma unroll
+        for (int k = 0; k < DP / 4; ++k) d[k] = __ldg(src + k);
+    }
+    __device__ __forceinline__ static float dot(const Sem<DP, false>& q, const float* row) {
+        const float4* r = reinterpret_cast<const float4*>(row);
+        float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+        for (int k = 0; k < DP / 4; ++k) {
+            const float4 v = r[k];
+            s0 = fmaf(q.q[4 * k], v.x, s0);
+            s1 = fmaf(q.q[4 * k + 1], v.y, s1);
+            s0 = fmaf(q.q[4 * k + 2], v.z, s0);
+            s1 = fmaf(q.q[4 * k + 3], v.w, s1);
+        }
+        return s0 + s1;
+    }
+};
+template <int DP>
+struct SemRow<DP, true> {
+    static constexpr int WORDS = DP / 2;
+    __device__ __forceinline__ static void stage(float* dst, const void* base, int i) {
+        const uint4* src = reinterpret_cast<const uint4*>(base) + (size_t)i * (DP / 8);
+        uint4* d = reinterpret_cast<uint4*>(dst);
+#pragma unroll
+        for (int k = 0; k < DP / 8; ++k) d[k] = __ldg(src + k);
+    }
+    __device__ __forceinline__ static float dot(const Sem<DP, true>& q, const float* row) {
+        const uint4* r = reinterpret_cast<const uint4*>(row);
+        float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+        for (int k = 0; k < DP / 8; ++k) {
+            const uint4 v = r[k];
+            s0 = fmaf(q.q[8 * k + 0], bf_lo(v.x), s0); s1 = fmaf(q.q[8 * k + 1], bf_hi(v.x), s1);
+            s0 = fmaf(q.q[8 * k + 2], bf_lo(v.y), s0); s1 = fmaf(q.q[8 * k + 3], bf_hi(v.y), s1);
+            s0 = fmaf(q.q[8 * k + 4], bf_lo(v.z), s0); s1 = fmaf(q.q[8 * k + 5], bf_hi(v.z), s1);
+            s0 = fmaf(q.q[8 * k + 6], bf_lo(v.w), s0); s1 = fmaf(q.q[8 * k + 7], bf_hi(v.w), s1);
+        }
+        return s0 + s1;
+    }
+};
+template <>
+struct SemRow<0, false> {
+    static constexpr int WORDS = 0;
+    __device__ __forceinline__ static void stage(float*, const void*, int) {}
+    __device__ __forceinline__ static float dot(const Sem<0, false>&, const float*) { return 1.f; }
+};
+
+
 constexpr int PAIR_T = 256;
 
+// Per-warp shared memory: the unit's queries and the 9 stencil rows.
 template <int DP, bool BF16, bool COLOR>
-__global__ void __launch_bounds__(PAIR_T, 2)
-k_pairs(const Task* __restrict__ tasks, const int* __restrict__ n_tasks, int* task_counter,
-        const Slot* __restrict__ slots, const EdgeDev* __restrict__ edges,
-        const FrameDev* __restrict__ frames, const int* __restrict__ cell_start,
-        const float4* __restrict__ pts4, const void* __restrict__ sem_sorted,
-        const float4* __restrict__ col4, GridParams gp, long long* __restrict__ acc, const int* done) {
-    if (done && *done) return;
-    const int lane = threadIdx.x & 31;
-    const int ntask = *n_tasks;
-    for (;;) {
-        int t = 0;
-        if (lane == 0) t = atomicAdd(task_counter, 1);
-        t = __shfl_sync(FULL, t, 0);
-        if (t >= ntask) break;
-        const Task T = tasks[t];
-        const EdgeDev& Ed = edges[T.edge];
-        const FrameDev& Fa = frames[Ed.a];
-        const int dx0 = Fa.dim[0], dy0 = Fa.dim[1], dz0 = Fa.dim[2];
-        const long long coff = Fa.cell_off;
-        const bool valid = lane < T.qcount;
-        Slot q;
-        if (valid) q = slots[T.qstart + lane];
-        else { q.s = 0; q.vx = q.vy = q.vz = 0.f; }
-        Sem<DP, BF16> qs;
-        if (DP > 0) qs.load(sem_sorted, q.s, valid);
-        float4 qc = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (COLOR && valid) qc = col4[q.s];
-        const int hx = T.cell % dx0;
-        const int hy = (T.cell / dx0) % dy0;
-        const int hz = T.cell / (dx0 * dy0);
+__host__ __device__ constexpr int warp_smem_words() {
+    return 32 * 4 + (COLOR ? 32 * 4 : 0) + 32 * SemRow<DP, BF16>::WORDS + 4 * 10;
+}
 
-        float W = 0.f, Dx = 0.f, Dy = 0.f, Dz = 0.f;
-        float Qxx = 0.f, Qxy = 0.f, Qxz = 0.f, Qyy = 0.f, Qyz = 0.f, Qzz = 0.f;
+struct Rows {
+    int* rb;    // [9] first point of the row (three x-adjacent cells)
+    int* b1;    // [9] first point of the home-x cell
+    int* b2;    // [9] first point of the x+1 cell
+    int* pre;   // [10] prefix of row lengths
+};
+
+// Rows of the 3x3x3 stencil around home cell (hx, hy, hz): lanes 0..8 fill one
+// row each; returns the total candidate count.
+__device__ __forceinline__ int build_rows(const Rows& R, const int* __restrict__ cell_start, long long coff,
+                                          int dx0, int dy0, int dz0, int hx, int hy, int hz, int lane) {
+    int len = 0, rb = 0, b1 = 0, b2 = 0;
+    if (lane < 9) {
+        const int ny = hy + (lane % 3) - 1, nz = hz + (lane / 3) - 1;
+        if (ny >= 0 && ny < dy0 && nz >= 0 && nz < dz0) {
+            const long long g0 = coff + ((long long)nz * dy0 + ny) * dx0;
+            const int xlo = max(hx - 1, 0), xhi = min(hx + 1, dx0 - 1);
+            rb = cell_start[g0 + xlo];
+            len = cell_start[g0 + xhi + 1] - rb;
+            b1 = cell_start[g0 + hx];
+            b2 = cell_start[g0 + hx + 1];
+        }
+    }
+    int inc = len;
+#pragma unroll
+    for (int o = 1; o < 16; o <<= 1) {
+        const int u = __shfl_up_sync(FULL, inc, o);
+        if (lane >= o) inc += u;
+    }
+    if (lane < 9) {
+        R.rb[lane] = rb;
+        R.b1[lane] = b1;
+        R.b2[lane] = b2;
+        R.pre[lane] = inc - len;
+    }
+    const int total = __shfl_sync(FULL, inc, 8);
+    if (lane == 9) R.pre[9] = total;
+    __syncwarp();
+    return total;
+}
+
+// Candidate v of the unit's stream: point index and offset (dx, dy, dz) of
+// its cell from the home cell.
+__device__ __forceinline__ int stream_point(const Rows& R, int v, int& dx, int& dy, int& dz) {
+    int r = 0;
+#pragma unroll
+    for (int k = 1; k < 9; ++k) r += (R.pre[k] <= v) ? 1 : 0;
+    const int i = R.rb[r] + (v - R.pre[r]);
+    dx = (i >= R.b1[r]) + (i >= R.b2[r]) - 1;
+    dy = (r % 3) - 1;
+    dz = (r / 3) - 1;
+    return i;
+}
+
+template <int DP, bool BF16, bool COLOR>
+__global__ void __launch_bounds__(PAIR_T, 3)
+k_pairs(const int* __restrict__ unit_start, const int* __restrict__ n_units, int* unit_counter,
+        const uint32_t* __restrict__ qkey, const float4* __restrict__ slots, long long Q,
+        const EdgeDev* __restrict__ edges, int E, const FrameDev* __restrict__ frames,
+        const int* __restrict__ cell_start, const float4* __restrict__ pts4,
+        const void* __restrict__ sem_sorted, const float4* __restrict__ col4, GridParams gp,
+        long long* __restrict__ acc, const int* done) {
+    if (done && *done) return;
+    extern __shared__ float4 smem4[];
+    constexpr int SW = SemRow<DP, BF16>::WORDS;
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    float* wb = reinterpret_cast<float*>(smem4) + warp * warp_smem_words<DP, BF16, COLOR>();
+    float4* sq = reinterpret_cast<float4*>(wb);                       // [32] query offsets
+    float4* scq = reinterpret_cast<float4*>(wb + 128);                // [32] query colours
+    float* ssq = wb + (COLOR ? 256 : 128);                            // [32][SW] query labels
+    int* ri = reinterpret_cast<int*>(ssq + 32 * SW);
+    const Rows R{ri, ri + 9, ri + 18, ri + 27};
+    const int nu = *n_units;
+    for (;;) {
+        int u = 0;
+        if (lane == 0) u = atomicAdd(unit_counter, 1);
+        u = __shfl_sync(FULL, u, 0);
+        if (u >= nu) break;
+        const int k0 = unit_start[u];
+        const uint32_t key0 = qkey[k0];
+        const long long kk = (long long)k0 + lane;
+        const bool mine = kk < Q && qkey[kk] == key0;
+        const int qcount = __popc(__ballot_sync(FULL, mine));
+        const int e = find_edge_bin(edges, E, key0);
+        const FrameDev& Fa = frames[edges[e].a];
+        const int dx0 = Fa.dim[0], dy0 = Fa.dim[1], dz0 = Fa.dim[2];
+        const int cell = (int)(key0 - edges[e].bin_off);
+        const int hx = cell % dx0, hy = (cell / dx0) % dy0, hz = cell / (dx0 * dy0);
+        __syncwarp();
+        if (lane < qcount) {
+            const float4 r = slots[kk];
+            const int s = __float_as_int(r.w);
+            sq[lane] = make_float4(r.x, r.y, r.z, 0.f);
+            if (COLOR) scq[lane] = __ldg(col4 + s);
+            SemRow<DP, BF16>::stage(ssq + lane * SW, sem_sorted, s);
+        }
+        const int C = build_rows(R, cell_start, Fa.cell_off, dx0, dy0, dz0, hx, hy, hz, lane);
+
+        float W = 0.f, Dv[3] = {0.f, 0.f, 0.f}, Sy[3] = {0.f, 0.f, 0.f};
+        float Myy[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, Mdy[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        float Qm[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         int cnt = 0;
-        for (int dz = -1; dz <= 1; ++dz) {
-            const int nz = hz + dz;
-            if (nz < 0 || nz >= dz0) continue;
-            for (int dy = -1; dy <= 1; ++dy) {
-                const int ny = hy + dy;
-                if (ny < 0 || ny >= dy0) continue;
-                for (int dx = -1; dx <= 1; ++dx) {
-                    const int nx = hx + dx;
-                    if (nx < 0 || nx >= dx0) continue;
-                    const long long g = coff + ((long long)nz * dy0 + ny) * dx0 + nx;
-                    const int beg = cell_start[g], end = cell_start[g + 1];
-                    // query relative to the centre of the neighbour cell
-                    const float qx = fmaf(-(float)dx, gp.hf, q.vx);
-                    const float qy = fmaf(-(float)dy, gp.hf, q.vy);
-                    const float qz = fmaf(-(float)dz, gp.hf, q.vz);
-                    for (int i = beg; i < end; ++i) {
-                        const float4 p = __ldg(pts4 + i);
-                        const float ex = p.x - qx, ey = p.y - qy, ez = p.z - qz;
-                        const float d2 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
-                        if (valid && d2 < gp.rc2) {
-                            float arg = d2 * gp.kg;
-                            if (COLOR) {
-                                const float4 c = __ldg(col4 + i);
-                                const float cr = c.x - qc.x, cg = c.y - qc.y, cb = c.z - qc.z;
-                                arg = fmaf(fmaf(cr, cr, fmaf(cg, cg, cb * cb)), gp.kc, arg);
-                            }
-                            const float k = exp2f(arg);
-                            const float s = (DP > 0) ? qs.dot(sem_sorted, i) : 1.f;
-                            const float w = s * k;
-                            const float wx = w * ex, wy = w * ey, wz = w * ez;
-                            W += w;
-                            Dx += wx; Dy += wy; Dz += wz;
-                            Qxx = fmaf(wx, ex, Qxx); Qxy = fmaf(wx, ey, Qxy); Qxz = fmaf(wx, ez, Qxz);
-                            Qyy = fmaf(wy, ey, Qyy); Qyz = fmaf(wy, ez, Qyz); Qzz = fmaf(wz, ez, Qzz);
-                            ++cnt;
-                        }
+        for (int c0 = 0; c0 < C; c0 += 32) {
+            const int v = c0 + lane;
+            const bool has = v < C;
+            int dx = 0, dy = 0, dz = 0, i = 0;
+            if (has) i = stream_point(R, v, dx, dy, dz);
+            float4 p = has ? __ldg(pts4 + i) : make_float4(0.f, 0.f, 0.f, 0.f);
+            // candidate relative to the home cell centre
+            const float x0 = fmaf((float)dx, gp.hf, p.x);
+            const float x1 = fmaf((float)dy, gp.hf, p.y);
+            const float x2 = fmaf((float)dz, gp.hf, p.z);
+            Sem<DP, BF16> cs;
+            if (DP > 0) cs.load(sem_sorted, i, has);
+            float4 cc = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (COLOR && has) cc = __ldg(col4 + i);
+            unsigned mask = 0u;
+            for (int j = 0; j < qcount; ++j) {
+                const float4 y = sq[j];
+                const float ex = x0 - y.x, ey = x1 - y.y, ez = x2 - y.z;
+                const float d2 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
+                mask |= (d2 < gp.rc2) ? (1u << j) : 0u;
+            }
+            if (!has) mask = 0u;
+            float w0 = 0.f, d0 = 0.f, d1 = 0.f, d2s = 0.f;
+            float q00 = 0.f, q01 = 0.f, q02 = 0.f, q11 = 0.f, q12 = 0.f, q22 = 0.f;
+            while (__any_sync(FULL, mask != 0u)) {
+                if (mask) {
+                    const int j = __ffs(mask) - 1;
+                    mask &= mask - 1u;
+                    const float4 y = sq[j];
+                    const float ex = x0 - y.x, ey = x1 - y.y, ez = x2 - y.z;
+                    const float dd = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
+                    float arg = dd * gp.kg;
+                    if (COLOR) {
+                        const float4 qc = scq[j];
+                        const float cr = cc.x - qc.x, cg = cc.y - qc.y, cb = cc.z - qc.z;
+                        arg = fmaf(fmaf(cr, cr, fmaf(cg, cg, cb * cb)), gp.kc, arg);
                     }
+                    const float s = SemRow<DP, BF16>::dot(cs, ssq + j * SW);
+                    const float w = s * exp2f(arg);
+                    const float wx = w * ex, wy = w * ey, wz = w * ez;
+                    w0 += w;
+                    d0 += wx; d1 += wy; d2s += wz;
+                    q00 = fmaf(wx, ex, q00); q01 = fmaf(wx, ey, q01); q02 = fmaf(wx, ez, q02);
+                    q11 = fmaf(wy, ey, q11); q12 = fmaf(wy, ez, q12); q22 = fmaf(wz, ez, q22);
+                    ++cnt;
                 }
             }
+            // fold the candidate's sums: y' = x - d
+            const float x[3] = {x0, x1, x2};
+            const float dc[3] = {d0, d1, d2s};
+            const float qc6[6] = {q00, q01, q02, q11, q12, q22};
+            W += w0;
+#pragma unroll
+            for (int m = 0; m < 3; ++m) {
+                Dv[m] += dc[m];
+                Sy[m] = fmaf(w0, x[m], Sy[m]) - dc[m];
+            }
+            int t6 = 0;
+#pragma unroll
+            for (int m = 0; m < 3; ++m)
+#pragma unroll
+                for (int l = m; l < 3; ++l, ++t6) {
+                    // sum w y'y'^T = W x x^T - x D^T - D x^T + Q
+                    Myy[t6] += fmaf(w0 * x[m], x[l], -(x[m] * dc[l] + dc[m] * x[l])) + qc6[t6];
+                    Qm[t6] += qc6[t6];
+                }
+#pragma unroll
+            for (int m = 0; m < 3; ++m)
+#pragma unroll
+                for (int l = 0; l < 3; ++l) {
+                    // sum w d y'^T = D x^T - Q
+                    const int qi = (m <= l) ? (m == 0 ? l : (m == 1 ? 2 + l : 5)) : (l == 0 ? m : (l == 1 ? 2 + m : 5));
+                    Mdy[3 * m + l] += fmaf(dc[m], x[l], -qc6[qi]);
+                }
         }
-        // query position y' in frame-a coordinates
-        const float yx = fmaf((float)(hx + Fa.lo[0]) + 0.5f, gp.hf, q.vx);
-        const float yy = fmaf((float)(hy + Fa.lo[1]) + 0.5f, gp.hf, q.vy);
-        const float yz = fmaf((float)(hz + Fa.lo[2]) + 0.5f, gp.hf, q.vz);
-        const float Wx = W * yx, Wy = W * yy, Wz = W * yz;
-        const float* sc = Ed.scale;
-        long long v[N_MOM];
-        v[0] = to_fixed(W, sc[MC_W]);
-        v[1] = to_fixed(Dx, sc[MC_D]); v[2] = to_fixed(Dy, sc[MC_D]); v[3] = to_fixed(Dz, sc[MC_D]);
-        v[4] = to_fixed(Wx, sc[MC_SY]); v[5] = to_fixed(Wy, sc[MC_SY]); v[6] = to_fixed(Wz, sc[MC_SY]);
-        v[7] = to_fixed(Wx * yx, sc[MC_MYY]); v[8] = to_fixed(Wx * yy, sc[MC_MYY]);
-        v[9] = to_fixed(Wx * yz, sc[MC_MYY]); v[10] = to_fixed(Wy * yy, sc[MC_MYY]);
-        v[11] = to_fixed(Wy * yz, sc[MC_MYY]); v[12] = to_fixed(Wz * yz, sc[MC_MYY]);
-        v[13] = to_fixed(Dx * yx, sc[MC_MDY]); v[14] = to_fixed(Dx * yy, sc[MC_MDY]);
-        v[15] = to_fixed(Dx * yz, sc[MC_MDY]); v[16] = to_fixed(Dy * yx, sc[MC_MDY]);
-        v[17] = to_fixed(Dy * yy, sc[MC_MDY]); v[18] = to_fixed(Dy * yz, sc[MC_MDY]);
-        v[19] = to_fixed(Dz * yx, sc[MC_MDY]); v[20] = to_fixed(Dz * yy, sc[MC_MDY]);
-        v[21] = to_fixed(Dz * yz, sc[MC_MDY]);
-        v[22] = to_fixed(Qxx, sc[MC_Q]); v[23] = to_fixed(Qxy, sc[MC_Q]); v[24] = to_fixed(Qxz, sc[MC_Q]);
-        v[25] = to_fixed(Qyy, sc[MC_Q]); v[26] = to_fixed(Qyz, sc[MC_Q]); v[27] = to_fixed(Qzz, sc[MC_Q]);
-        v[28] = cnt;
-        long long* dst = acc + (long long)T.edge * ACC_N;
+        // home-centre coordinates -> frame-a coordinates: y' += o
+        const float o[3] = {((float)(hx + Fa.lo[0]) + 0.5f) * gp.hf, ((float)(hy + Fa.lo[1]) + 0.5f) * gp.hf,
+                            ((float)(hz + Fa.lo[2]) + 0.5f) * gp.hf};
+        {
+            int t6 = 0;
+#pragma unroll
+            for (int m = 0; m < 3; ++m)
+#pragma unroll
+                for (int l = m; l < 3; ++l, ++t6)
+                    Myy[t6] += Sy[m] * o[l] + o[m] * Sy[l] + W * o[m] * o[l];
+#pragma unroll
+            for (int m = 0; m < 3; ++m)
+#pragma unroll
+                for (int l = 0; l < 3; ++l) Mdy[3 * m + l] = fmaf(Dv[m], o[l], Mdy[3 * m + l]);
+#pragma unroll
+            for (int m = 0; m < 3; ++m) Sy[m] = fmaf(W, o[m], Sy[m]);
+        }
+        const float* scl = edges[e].scale;
+        long long* dst = acc + (long long)e * ACC_N;
 #pragma unroll
         for (int k = 0; k < N_MOM; ++k) {
-            const long long tot = warp_sum_ll(v[k]);
-            if (lane == k && tot != 0) atomicAdd(reinterpret_cast<unsigned long long*>(dst + k),
-                                                 (unsigned long long)tot);
+            float val;
+            if (k == 0) val = W;
+            else if (k < 4) val = Dv[k - 1];
+            else if (k < 7) val = Sy[k - 4];
+            else if (k < 13) val = Myy[k - 7];
+            else if (k < 22) val = Mdy[k - 13];
+            else val = Qm[(k - 22) % 6];
+            const long long vv = (k == N_MOM - 1) ? (long long)cnt : to_fixed(val, __ldg(scl + moment_class(k)));
+            const long long tot = warp_sum_ll(vv);
+            if (lane == k && tot != 0)
+                atomicAdd(reinterpret_cast<unsigned long long*>(dst + k), (unsigned long long)tot);
         }
     }
 }
 
 // Same search, geometry only: writes the pair list of one edge (verification).
 __global__ void __launch_bounds__(PAIR_T)
-k_emit_pairs(const Task* __restrict__ tasks, const int* __restrict__ n_tasks, int* task_counter,
-             const Slot* __restrict__ slots, const EdgeDev* __restrict__ edges,
-             const FrameDev* __restrict__ frames, const int* __restrict__ cell_start,
-             const float4* __restrict__ pts4, GridParams gp, int edge_sel,
-             const int* __restrict__ perm_local, long long capacity, int* __restrict__ i_out,
-             int* __restrict__ j_out, unsigned long long* n_out) {
+k_emit_pairs(const int* __restrict__ unit_start, const int* __restrict__ n_units, int* unit_counter,
+             const uint32_t* __restrict__ qkey, const float4* __restrict__ slots, long long Q,
+             const EdgeDev* __restrict__ edges, int E, const FrameDev* __restrict__ frames,
+             const int* __restrict__ cell_start, const float4* __restrict__ pts4, GridParams gp,
+             int edge_sel, const int* __restrict__ perm_local, long long capacity,
+             int* __restrict__ i_out, int* __restrict__ j_out, unsigned long long* n_out) {
+    __shared__ float4 s_q[PAIR_T / 32][32];
+    __shared__ int s_rows[PAIR_T / 32][40];
     const int lane = threadIdx.x & 31;
-    const int ntask = *n_tasks;
+    const int warp = threadIdx.x >> 5;
+    float4* sq = s_q[warp];
+    const Rows R{s_rows[warp], s_rows[warp] + 9, s_rows[warp] + 18, s_rows[warp] + 27};
+    const int nu = *n_units;
     for (;;) {
-        int t = 0;
-        if (lane == 0) t = atomicAdd(task_counter, 1);
-        t = __shfl_sync(FULL, t, 0);
-        if (t >= ntask) break;
-        const Task T = tasks[t];
-        if (T.edge != edge_sel) continue;
-        const FrameDev& Fa = frames[edges[T.edge].a];
+        int u = 0;
+        if (lane == 0) u = atomicAdd(unit_counter, 1);
+        u = __shfl_sync(FULL, u, 0);
+        if (u >= nu) break;
+        const int k0 = unit_start[u];
+        const uint32_t key0 = qkey[k0];
+        const int e = find_edge_bin(edges, E, key0);
+        if (e != edge_sel) continue;
+        const long long kk = (long long)k0 + lane;
+        const bool mine = kk < Q && qkey[kk] == key0;
+        const int qcount = __popc(__ballot_sync(FULL, mine));
+        const FrameDev& Fa = frames[edges[e].a];
         const int dx0 = Fa.dim[0], dy0 = Fa.dim[1], dz0 = Fa.dim[2];
-        const bool valid = lane < T.qcount;
-        Slot q;
-        if (valid) q = slots[T.qstart + lane];
-        else { q.s = 0; q.vx = q.vy = q.vz = 0.f; }
-        const int hx = T.cell % dx0, hy = (T.cell / dx0) % dy0, hz = T.cell / (dx0 * dy0);
-        const int jq = valid ? perm_local[q.s] : 0;
-        for (int dz = -1; dz <= 1; ++dz) {
-            const int nz = hz + dz;
-            if (nz < 0 || nz >= dz0) continue;
-            for (int dy = -1; dy <= 1; ++dy) {
-                const int ny = hy + dy;
-                if (ny < 0 || ny >= dy0) continue;
-                for (int dx = -1; dx <= 1; ++dx) {
-                    const int nx = hx + dx;
-                    if (nx < 0 || nx >= dx0) continue;
-                    const long long g = Fa.cell_off + ((long long)nz * dy0 + ny) * dx0 + nx;
-                    const int beg = cell_start[g], end = cell_start[g + 1];
-                    const float qx = fmaf(-(float)dx, gp.hf, q.vx);
-                    const float qy = fmaf(-(float)dy, gp.hf, q.vy);
-                    const float qz = fmaf(-(float)dz, gp.hf, q.vz);
-                    for (int i = beg; i < end; ++i) {
-                        const float4 p = __ldg(pts4 + i);
-                        const float ex = p.x - qx, ey = p.y - qy, ez = p.z - qz;
-                        const float d2 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
-                        if (valid && d2 < gp.rc2) {
-                            unsigned long long k = atomicAdd(n_out, 1ULL);
-                            if ((long long)k < capacity) {
-                                i_out[k] = perm_local[i];
-                                j_out[k] = jq;
-                            }
-                        }
+        const int cell = (int)(key0 - edges[e].bin_off);
+        const int hx = cell % dx0, hy = (cell / dx0) % dy0, hz = cell / (dx0 * dy0);
+        __syncwarp();
+        if (lane < qcount) sq[lane] = slots[kk];
+        const int C = build_rows(R, cell_start, Fa.cell_off, dx0, dy0, dz0, hx, hy, hz, lane);
+        for (int c0 = 0; c0 < C; c0 += 32) {
+            const int v = c0 + lane;
+            if (v >= C) continue;
+            int dx, dy, dz;
+            const int i = stream_point(R, v, dx, dy, dz);
+            const float4 p = __ldg(pts4 + i);
+            const float x0 = fmaf((float)dx, gp.hf, p.x), x1 = fmaf((float)dy, gp.hf, p.y),
+                        x2 = fmaf((float)dz, gp.hf, p.z);
+            for (int j = 0; j < qcount; ++j) {
+                const float4 y = sq[j];
+                const float ex = x0 - y.x, ey = x1 - y.y, ez = x2 - y.z;
+                const float d2 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
+                if (d2 < gp.rc2) {
+                    const unsigned long long t = atomicAdd(n_out, 1ULL);
+                    if ((long long)t < capacity) {
+                        i_out[t] = perm_local[i];
+                        j_out[t] = perm_local[__float_as_int(y.w)];
                     }
                 }
             }
@@ -430,24 +614,27 @@ inline unsigned blocks_for(long long n, int t) {
 }
 
 template <int DP, bool BF16, bool COLOR>
-void run_pairs(unsigned grid, cudaStream_t st, const Task* tasks, const int* n_tasks,
-               int* task_counter, const Slot* slots, const EdgeDev* edges, const FrameDev* frames,
-               const int* cell_start, const float4* pts4, const void* sem, const float4* col4,
-               GridParams gp, long long* acc, const int* done) {
-    k_pairs<DP, BF16, COLOR><<<grid, PAIR_T, 0, st>>>(tasks, n_tasks, task_counter, slots, edges,
-                                                      frames, cell_start, pts4, sem, col4, gp, acc,
-                                                      done);
+void run_pairs(unsigned grid, cudaStream_t st, const int* unit_start, const int* n_units,
+               int* unit_counter, const uint32_t* qkey, const float4* slots, long long Q,
+               const EdgeDev* edges, int E, const FrameDev* frames, const int* cell_start,
+               const float4* pts4, const void* sem, const float4* col4, GridParams gp,
+               long long* acc, const int* done) {
+    const size_t smem = sizeof(float) * (PAIR_T / 32) * warp_smem_words<DP, BF16, COLOR>();
+    k_pairs<DP, BF16, COLOR><<<grid, PAIR_T, smem, st>>>(unit_start, n_units, unit_counter, qkey, slots,
+                                                         Q, edges, E, frames, cell_start, pts4, sem,
+                                                         col4, gp, acc, done);
 }
 
 template <bool COLOR>
-bool dispatch_pairs(unsigned grid, cudaStream_t st, const Task* tasks, const int* n_tasks,
-                    int* task_counter, const Slot* slots, const EdgeDev* edges,
-                    const FrameDev* frames, const int* cell_start, const float4* pts4,
-                    const void* sem, const float4* col4, GridParams gp, long long* acc,
-                    const int* done) {
-#define RK_P(DPV, BFV) \
-    run_pairs<DPV, BFV, COLOR>(grid, st, tasks, n_tasks, task_counter, slots, edges, frames, \
-                               cell_start, pts4, sem, col4, gp, acc, done); return true
+bool dispatch_pairs(unsigned grid, cudaStream_t st, const int* unit_start, const int* n_units,
+                    int* unit_counter, const uint32_t* qkey, const float4* slots, long long Q,
+                    const EdgeDev* edges, int E, const FrameDev* frames, const int* cell_start,
+                    const float4* pts4, const void* sem, const float4* col4, GridParams gp,
+                    long long* acc, const int* done) {
+#define RK_P(DPV, BFV)                                                                            \
+    run_pairs<DPV, BFV, COLOR>(grid, st, unit_start, n_units, unit_counter, qkey, slots, Q, edges, \
+                               E, frames, cell_start, pts4, sem, col4, gp, acc, done);            \
+    return true
     if (gp.sem_pad == 0) { RK_P(0, false); }
     if (gp.sem_bf16) {
         switch (gp.sem_pad) {
@@ -472,64 +659,62 @@ bool dispatch_pairs(unsigned grid, cudaStream_t st, const Task* tasks, const int
 }
 }  // namespace
 
-void launch_edge_setup(const double* poses, const EdgeDev* edges, int E, EdgeXf* xf,
-                       const int* done, cudaStream_t st) {
-    k_edge_setup<<<(E + 127) / 128, 128, 0, st>>>(poses, edges, E, xf, done);
+void launch_edge_setup(const double* poses, const EdgeDev* edges, int E, const FrameDev* frames,
+                       double h, EdgeXf* xf, const int* done, cudaStream_t st) {
+    k_edge_setup<<<(E + 127) / 128, 128, 0, st>>>(poses, edges, E, frames, h, xf, done);
     count_launch();
 }
 
-void launch_bin(int pass, const EdgeDev* edges, int E, const FrameDev* frames, const EdgeXf* xf,
-                const long long* occ_key, const int* cell_start, const float4* pts4, GridParams gp,
-                int* bin_count, const long long* bin_packed, int* bin_cursor, Slot* slots,
-                long long n_items, const int* done, int num_sms, cudaStream_t st) {
-    if (n_items <= 0) return;
-    long long want = (n_items + 7) / 8;   // 8 warps per block
-    long long cap = (long long)num_sms * 8;
-    unsigned grid = (unsigned)(want < cap ? want : cap);
-    if (pass == 0)
-        k_bin<0><<<grid, 256, 0, st>>>(edges, E, frames, xf, occ_key, cell_start, pts4, gp, bin_count,
-                                       bin_packed, bin_cursor, slots, n_items, done);
-    else
-        k_bin<1><<<grid, 256, 0, st>>>(edges, E, frames, xf, occ_key, cell_start, pts4, gp, bin_count,
-                                       bin_packed, bin_cursor, slots, n_items, done);
+void launch_query_keys(const EdgeDev* edges, int E, const FrameDev* frames, const EdgeXf* xf,
+                       const uint32_t* pt_cell, const float4* pts4, GridParams gp, long long Q,
+                       uint32_t* qkey, int* qval, float4* qrec, const int* done, cudaStream_t st) {
+    if (Q <= 0) return;
+    k_query_keys<<<blocks_for(Q, 256), 256, 0, st>>>(edges, E, frames, xf, pt_cell, pts4, gp, Q, qkey, qval,
+                                                    qrec, done);
     count_launch();
 }
 
-void launch_make_bins(const int* bin_count, long long* bin_val, long long n_bins, const int* done,
-                      cudaStream_t st) {
-    if (n_bins <= 0) return;
-    k_make_bins<<<blocks_for(n_bins, 256), 256, 0, st>>>(bin_count, bin_val, n_bins, done);
+void launch_query_gather(const uint32_t* qkey_sorted, const int* qval_sorted, const float4* qrec,
+                         long long Q, float4* slots, int* bin_first, const int* done,
+                         cudaStream_t st) {
+    if (Q <= 0) return;
+    k_query_gather<<<blocks_for(Q, 256), 256, 0, st>>>(qkey_sorted, qval_sorted, qrec, Q, slots, bin_first,
+                                                      done);
     count_launch();
 }
 
-void launch_emit_tasks(const int* bin_count, const long long* bin_packed, const EdgeDev* edges,
-                       int E, long long n_bins, const long long* total_packed, Task* tasks,
-                       int* n_tasks, const int* done, cudaStream_t st) {
-    k_emit_tasks<<<blocks_for(n_bins, 256), 256, 0, st>>>(bin_count, bin_packed, edges, E, n_bins,
-                                                          total_packed, tasks, n_tasks, done);
+void launch_units(const uint32_t* qkey_sorted, const int* bin_first, long long Q, int* unit_start,
+                  int* n_units, const int* done, cudaStream_t st) {
+    if (Q <= 0) return;
+    k_units<<<blocks_for(Q, 256), 256, 0, st>>>(qkey_sorted, bin_first, Q, unit_start, n_units, done);
     count_launch();
 }
 
-void launch_pairs(const Task* tasks, const int* n_tasks, int* task_counter, const Slot* slots,
-                  const EdgeDev* edges, const FrameDev* frames, const int* cell_start,
-                  const float4* pts4, const void* sem_sorted, const float4* col4, GridParams gp,
-                  long long* acc, const int* done, int num_sms, cudaStream_t st) {
-    unsigned grid = (unsigned)(num_sms * 2);
-    bool ok = gp.color ? dispatch_pairs<true>(grid, st, tasks, n_tasks, task_counter, slots, edges,
-                                              frames, cell_start, pts4, sem_sorted, col4, gp, acc, done)
-                       : dispatch_pairs<false>(grid, st, tasks, n_tasks, task_counter, slots, edges,
-                                               frames, cell_start, pts4, sem_sorted, col4, gp, acc, done);
+void launch_pairs(const int* unit_start, const int* n_units, int* unit_counter,
+                  const uint32_t* qkey, const float4* slots, long long Q, const EdgeDev* edges, int E,
+                  const FrameDev* frames, const int* cell_start, const float4* pts4,
+                  const void* sem_sorted, const float4* col4, GridParams gp, long long* acc,
+                  const int* done, int num_sms, cudaStream_t st) {
+    if (Q <= 0) return;
+    const unsigned grid = (unsigned)(num_sms * 3);
+    const bool ok = gp.color
+        ? dispatch_pairs<true>(grid, st, unit_start, n_units, unit_counter, qkey, slots, Q, edges, E, frames,
+                               cell_start, pts4, sem_sorted, col4, gp, acc, done)
+        : dispatch_pairs<false>(grid, st, unit_start, n_units, unit_counter, qkey, slots, Q, edges, E, frames,
+                                cell_start, pts4, sem_sorted, col4, gp, acc, done);
     if (ok) count_launch();
 }
 
-void launch_emit_pairs(const Task* tasks, const int* n_tasks, int* task_counter, const Slot* slots,
-                       const EdgeDev* edges, const FrameDev* frames, const int* cell_start,
-                       const float4* pts4, GridParams gp, int edge_sel, const int* perm_local,
-                       long long capacity, int* i_out, int* j_out, unsigned long long* n_out,
-                       int num_sms, cudaStream_t st) {
-    k_emit_pairs<<<num_sms * 2, PAIR_T, 0, st>>>(tasks, n_tasks, task_counter, slots, edges, frames,
-                                                 cell_start, pts4, gp, edge_sel, perm_local,
-                                                 capacity, i_out, j_out, n_out);
+void launch_emit_pairs(const int* unit_start, const int* n_units, int* unit_counter,
+                       const uint32_t* qkey, const float4* slots, long long Q, const EdgeDev* edges,
+                       int E, const FrameDev* frames, const int* cell_start, const float4* pts4,
+                       GridParams gp, int edge_sel, const int* perm_local, long long capacity,
+                       int* i_out, int* j_out, unsigned long long* n_out, int num_sms,
+                       cudaStream_t st) {
+    if (Q <= 0) return;
+    k_emit_pairs<<<num_sms * 2, PAIR_T, 0, st>>>(unit_start, n_units, unit_counter, qkey, slots, Q, edges, E,
+                                                 frames, cell_start, pts4, gp, edge_sel, perm_local, capacity,
+                                                 i_out, j_out, n_out);
     count_launch();
 }
 
