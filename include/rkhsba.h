@@ -191,6 +191,40 @@ rkhsba_status rkhsba_edge_pairs(rkhsba_ctx* ctx, const double* poses, int32_t ed
  */
 rkhsba_status rkhsba_profile(rkhsba_ctx* ctx, int32_t enable, double* ms, int64_t* launches);
 
+/*
+ * rkhsba_eval_static -- the evaluation of rkhsba_eval for a small problem,
+ * without allocating any device memory.  The paper has no counterpart; this
+ * entry point exists for callers that cannot call cudaMalloc: code living
+ * inside another runtime that owns the device memory through its own pool,
+ * real-time loops that must not take allocator locks or face an allocation
+ * failure mid-run, and code that may run while a stream is being captured.
+ *
+ * Every temporary buffer comes from one fixed 32 MiB device array inside the
+ * library (each GPU that loads the library holds it until the process
+ * exits).  Limits: n_frames <= 16, n_edges <= 64, total points <= 32768,
+ * queries (sum over edges of the points of the larger-index frame) <= 131072,
+ * grid cells <= 2^20 over all frames and over all edges' home cells;
+ * larger problems return RKHSBA_EINVAL with a message and touch no memory
+ * beyond the array.  The first call on a device looks up the array's device
+ * address; make that first call before any stream capture on that device.
+ * All calls share the array and reuse its contents (what must start at zero
+ * is cleared in every call); calls whose GPU work overlaps (other streams or
+ * other host threads) race on it, so the caller serialises them.
+ *
+ *   n_frames, n_points, edges, params  as for rkhsba_create
+ *   d_xyz, d_sem, d_rgb   DEVICE inputs laid out as for rkhsba_create
+ *                         (d_sem/d_rgb may be NULL)
+ *   poses      [K*16] HOST float64 poses
+ *   loss, grad, H_full    HOST outputs as for rkhsba_eval (each may be NULL)
+ *   cuda_stream  stream to run on (NULL: the default stream)
+ * Synchronous: returns after the outputs are written.
+ */
+rkhsba_status rkhsba_eval_static(int32_t n_frames, const int64_t* n_points, const double* d_xyz,
+                                 const float* d_sem, const float* d_rgb, int32_t n_edges,
+                                 const int32_t* edges, const rkhsba_params* params,
+                                 const double* poses, double* loss, double* grad, double* H_full,
+                                 void* cuda_stream);
+
 /* Problem shape and device memory of a context. */
 rkhsba_status rkhsba_info(const rkhsba_ctx* ctx, int32_t* n_frames, int32_t* n_edges,
                           int64_t* n_points_total, int64_t* device_bytes);

@@ -834,3 +834,9 @@ const char* rkhsba_last_error(const rkhsba_ctx* c) {
 int64_t rkhsba_launch_count(void) { return g_launches.load(); }
 
 }  // extern "C"
+
+namespace rk {
+// Message of the last context-free failure on this thread (read back through
+// rkhsba_last_error(NULL)); used by entry points defined in other files.
+void set_thread_error(const char* msg) { t_err = msg ? msg : ""; }
+}  // namespace rk

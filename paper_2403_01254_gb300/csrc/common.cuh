@@ -159,3 +159,8 @@ void launch_copy_if_accepted(const LMState* st_dev, double* dst, const double* s
                              long long n, cudaStream_t st);
 
 }  // namespace rk
+
+namespace rk {
+// api.cu: sets the message returned by rkhsba_last_error(NULL) on this thread
+void set_thread_error(const char* msg);
+}  // namespace rk

@@ -294,3 +294,30 @@ class Problem:
             self.close()
         except Exception:
             pass
+
+
+def rkhsba_eval_static(n_points, d_xyz, d_sem, d_rgb, edges, params, poses, stream=None):
+    """Evaluation without device allocation (rkhsba_eval_static in the C ABI).
+
+    For callers that cannot allocate device memory: the library runs the
+    evaluation in a fixed scratch array of its own.  d_xyz / d_sem / d_rgb are
+    device pointers (ints, or None); results come back as host arrays.
+    """
+    lib = load()
+    f = lib.rkhsba_eval_static
+    if f.argtypes is None:
+        f.argtypes = [C.c_int32, P(C.c_int64), C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32,
+                      P(C.c_int32), P(Params), P(C.c_double), P(C.c_double), P(C.c_double),
+                      P(C.c_double), C.c_void_p]
+        f.restype = C.c_int
+    n = np.ascontiguousarray(n_points, dtype=np.int64)
+    K = len(n)
+    e = np.ascontiguousarray(np.asarray(edges, np.int32).reshape(-1))
+    T = np.ascontiguousarray(poses, dtype=np.float64).reshape(K * 16)
+    loss = np.zeros(1)
+    grad = np.zeros(6 * K)
+    H = np.zeros((6 * K, 6 * K))
+    _check(f(K, _ptr(n, C.c_int64), d_xyz, d_sem, d_rgb, len(e) // 2, _ptr(e, C.c_int32),
+             C.byref(params), _ptr(T, C.c_double), _ptr(loss, C.c_double), _ptr(grad, C.c_double),
+             _ptr(H, C.c_double), stream))
+    return dict(loss=float(loss[0]), grad=grad, H=H)
