@@ -50,6 +50,8 @@ def build(force=False, verbose=False, ptxas_v=False):
     nvcc = _nvcc()
     os.makedirs(BUILD, exist_ok=True)
     extra = ["-Xptxas", "-v"] if ptxas_v else []
+    # extra -D flags for build-time kernel variants (e.g. RKHSBA_NVCC_DEFINES="RK_PAIR_MINB=2")
+    extra += ["-D" + d for d in os.environ.get("RKHSBA_NVCC_DEFINES", "").split()]
 
     def one(src):
         obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")

@@ -28,6 +28,10 @@ inline void count_launch(long long n = 1) { g_launches.fetch_add(n, std::memory_
 constexpr int MAX_SEM = 32;     // label floats per point
 constexpr int ACC_N = 32;       // int64 accumulator slots per edge
 constexpr int N_MOM = 29;       // used slots (see MomentIndex)
+#ifndef RK_UNIT_Q
+#define RK_UNIT_Q 32
+#endif
+constexpr int UNIT_Q = RK_UNIT_Q;   // queries of one home cell per warp unit (32 or 64)
 
 // Fixed-point accumulator layout per edge.  All sums are over the pairs of the
 // edge, in frame-a coordinates: d = x - y', y' = T_ab y.

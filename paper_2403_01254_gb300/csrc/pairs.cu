@@ -177,7 +177,7 @@ __global__ void k_query_gather(const uint32_t* __restrict__ key, const int* __re
     }
 }
 
-// a unit starts at the first query of a home cell and every 32 queries after
+// a unit starts at the first query of a home cell and every UNIT_Q queries after
 __global__ void k_units(const uint32_t* __restrict__ key, const int* __restrict__ bin_first, long long Q,
                         int* __restrict__ unit_start, int* __restrict__ n_units, const int* done) {
     if (done && *done) return;
@@ -188,7 +188,7 @@ __global__ void k_units(const uint32_t* __restrict__ key, const int* __restrict_
         bool st = false;
         if (k < Q) {
             const uint32_t kk = key[k];
-            st = kk != NO_KEY && ((k - bin_first[kk]) & 31) == 0;
+            st = kk != NO_KEY && ((k - bin_first[kk]) % UNIT_Q) == 0;
         }
         const unsigned m = __ballot_sync(FULL, st);
         int off = 0;
@@ -327,11 +327,24 @@ struct SemRow<0, false> {
 
 
 constexpr int PAIR_T = 256;
+#ifndef RK_PAIR_MINB
+#define RK_PAIR_MINB 2              // resident CTAs per SM the register budget targets
+#endif
+constexpr int UQ = UNIT_Q;          // queries per unit (one or two 32-bit mask words)
+static_assert(UQ == 32 || UQ == 64, "units hold 32 or 64 queries");
 
-// Per-warp shared memory: the unit's queries and the 9 stencil rows.
+__device__ __forceinline__ float ex2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// Per-warp shared memory: the unit's queries and the 9 stencil rows.  A query
+// is kept as m = (-2 y, |y|^2) so that the cutoff test of a candidate x is
+// |y|^2 - 2 x.y < r_c^2 - |x|^2 (three FMA); d = x - y = x + m/2.
 template <int DP, bool BF16, bool COLOR>
 __host__ __device__ constexpr int warp_smem_words() {
-    return 32 * 4 + (COLOR ? 32 * 4 : 0) + 32 * SemRow<DP, BF16>::WORDS + 4 * 10;
+    return UQ * 4 + (COLOR ? UQ * 4 : 0) + UQ * SemRow<DP, BF16>::WORDS + 4 * 10;
 }
 
 struct Rows {
@@ -388,8 +401,43 @@ __device__ __forceinline__ int stream_point(const Rows& R, int v, int& dx, int& 
     return i;
 }
 
+// Unit header shared by the pair and the pair-list kernels: home cell of the
+// unit starting at sorted query k0, and the number of its queries (<= UQ).
+__device__ __forceinline__ int unit_queries(const uint32_t* __restrict__ qkey, long long Q, int k0,
+                                            uint32_t key0, int lane) {
+    // units start every UQ queries of a home cell, so a unit holds at most UQ
+    // of them even when the cell continues past k0 + UQ
+    const long long k1 = (long long)k0 + lane, k2 = k1 + 32;
+    const bool m1 = k1 < Q && qkey[k1] == key0;
+    const bool m2 = UQ > 32 && k2 < Q && qkey[k2] == key0;
+    const int n = __popc(__ballot_sync(FULL, m1)) + __popc(__ballot_sync(FULL, m2));
+    return n < UQ ? n : UQ;
+}
+
+// cutoff test of the staged candidate (x, thr = r_c^2 - |x|^2) against the
+// unit's queries j in [j0, j0 + 32), bit j - j0 set when inside
+__device__ __forceinline__ unsigned test_word(const float4* __restrict__ sm, int j0, int n, float x0, float x1,
+                                              float x2, float thr) {
+    unsigned mask = 0u;
+    if (n >= 32) {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+            const float4 m = sm[j0 + j];
+            const float t = fmaf(x0, m.x, fmaf(x1, m.y, fmaf(x2, m.z, m.w)));
+            mask |= (t < thr) ? (1u << j) : 0u;
+        }
+    } else {
+        for (int j = 0; j < n; ++j) {
+            const float4 m = sm[j0 + j];
+            const float t = fmaf(x0, m.x, fmaf(x1, m.y, fmaf(x2, m.z, m.w)));
+            mask |= (t < thr) ? (1u << j) : 0u;
+        }
+    }
+    return mask;
+}
+
 template <int DP, bool BF16, bool COLOR>
-__global__ void __launch_bounds__(PAIR_T, 3)
+__global__ void __launch_bounds__(PAIR_T, RK_PAIR_MINB)
 k_pairs(const int* __restrict__ unit_start, const int* __restrict__ n_units, int* unit_counter,
         const uint32_t* __restrict__ qkey, const float4* __restrict__ slots, long long Q,
         const EdgeDev* __restrict__ edges, int E, const FrameDev* __restrict__ frames,
@@ -402,10 +450,10 @@ k_pairs(const int* __restrict__ unit_start, const int* __restrict__ n_units, int
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     float* wb = reinterpret_cast<float*>(smem4) + warp * warp_smem_words<DP, BF16, COLOR>();
-    float4* sq = reinterpret_cast<float4*>(wb);                       // [32] query offsets
-    float4* scq = reinterpret_cast<float4*>(wb + 128);                // [32] query colours
-    float* ssq = wb + (COLOR ? 256 : 128);                            // [32][SW] query labels
-    int* ri = reinterpret_cast<int*>(ssq + 32 * SW);
+    float4* sm = reinterpret_cast<float4*>(wb);                       // [UQ] (-2y, |y|^2)
+    float4* scq = reinterpret_cast<float4*>(wb + 4 * UQ);             // [UQ] query colours
+    float* ssq = wb + (COLOR ? 8 : 4) * UQ;                           // [UQ][SW] query labels
+    int* ri = reinterpret_cast<int*>(ssq + UQ * SW);
     const Rows R{ri, ri + 9, ri + 18, ri + 27};
     const int nu = *n_units;
     for (;;) {
@@ -415,21 +463,24 @@ k_pairs(const int* __restrict__ unit_start, const int* __restrict__ n_units, int
         if (u >= nu) break;
         const int k0 = unit_start[u];
         const uint32_t key0 = qkey[k0];
-        const long long kk = (long long)k0 + lane;
-        const bool mine = kk < Q && qkey[kk] == key0;
-        const int qcount = __popc(__ballot_sync(FULL, mine));
+        const int qcount = unit_queries(qkey, Q, k0, key0, lane);
         const int e = find_edge_bin(edges, E, key0);
         const FrameDev& Fa = frames[edges[e].a];
         const int dx0 = Fa.dim[0], dy0 = Fa.dim[1], dz0 = Fa.dim[2];
         const int cell = (int)(key0 - edges[e].bin_off);
         const int hx = cell % dx0, hy = (cell / dx0) % dy0, hz = cell / (dx0 * dy0);
         __syncwarp();
-        if (lane < qcount) {
-            const float4 r = slots[kk];
-            const int s = __float_as_int(r.w);
-            sq[lane] = make_float4(r.x, r.y, r.z, 0.f);
-            if (COLOR) scq[lane] = __ldg(col4 + s);
-            SemRow<DP, BF16>::stage(ssq + lane * SW, sem_sorted, s);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int q = lane + 32 * h;
+            if (q < qcount) {
+                const float4 r = slots[(long long)k0 + q];
+                const int s = __float_as_int(r.w);
+                sm[q] = make_float4(-2.f * r.x, -2.f * r.y, -2.f * r.z,
+                                    fmaf(r.x, r.x, fmaf(r.y, r.y, r.z * r.z)));
+                if (COLOR) scq[q] = __ldg(col4 + s);
+                SemRow<DP, BF16>::stage(ssq + q * SW, sem_sorted, s);
+            }
         }
         const int C = build_rows(R, cell_start, Fa.cell_off, dx0, dy0, dz0, hx, hy, hz, lane);
 
@@ -442,31 +493,29 @@ k_pairs(const int* __restrict__ unit_start, const int* __restrict__ n_units, int
             const bool has = v < C;
             int dx = 0, dy = 0, dz = 0, i = 0;
             if (has) i = stream_point(R, v, dx, dy, dz);
-            float4 p = has ? __ldg(pts4 + i) : make_float4(0.f, 0.f, 0.f, 0.f);
+            const float4 p = has ? __ldg(pts4 + i) : make_float4(0.f, 0.f, 0.f, 0.f);
             // candidate relative to the home cell centre
             const float x0 = fmaf((float)dx, gp.hf, p.x);
             const float x1 = fmaf((float)dy, gp.hf, p.y);
             const float x2 = fmaf((float)dz, gp.hf, p.z);
+            const float xx = fmaf(x0, x0, fmaf(x1, x1, x2 * x2));
+            const float thr = gp.rc2 - xx;
             Sem<DP, BF16> cs;
             if (DP > 0) cs.load(sem_sorted, i, has);
             float4 cc = make_float4(0.f, 0.f, 0.f, 0.f);
             if (COLOR && has) cc = __ldg(col4 + i);
-            unsigned mask = 0u;
-            for (int j = 0; j < qcount; ++j) {
-                const float4 y = sq[j];
-                const float ex = x0 - y.x, ey = x1 - y.y, ez = x2 - y.z;
-                const float d2 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
-                mask |= (d2 < gp.rc2) ? (1u << j) : 0u;
-            }
-            if (!has) mask = 0u;
+            unsigned mk0 = test_word(sm, 0, qcount, x0, x1, x2, thr);
+            unsigned mk1 = (qcount > 32) ? test_word(sm, 32, qcount - 32, x0, x1, x2, thr) : 0u;
+            if (!has) mk0 = mk1 = 0u;
             float w0 = 0.f, d0 = 0.f, d1 = 0.f, d2s = 0.f;
             float q00 = 0.f, q01 = 0.f, q02 = 0.f, q11 = 0.f, q12 = 0.f, q22 = 0.f;
-            while (__any_sync(FULL, mask != 0u)) {
-                if (mask) {
-                    const int j = __ffs(mask) - 1;
-                    mask &= mask - 1u;
-                    const float4 y = sq[j];
-                    const float ex = x0 - y.x, ey = x1 - y.y, ez = x2 - y.z;
+            while (__any_sync(FULL, (mk0 | mk1) != 0u)) {
+                if (mk0 | mk1) {
+                    int j;
+                    if (mk0) { j = __ffs(mk0) - 1; mk0 &= mk0 - 1u; }
+                    else { j = 31 + __ffs(mk1); mk1 &= mk1 - 1u; }
+                    const float4 m = sm[j];
+                    const float ex = fmaf(0.5f, m.x, x0), ey = fmaf(0.5f, m.y, x1), ez = fmaf(0.5f, m.z, x2);
                     const float dd = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
                     float arg = dd * gp.kg;
                     if (COLOR) {
@@ -475,7 +524,7 @@ k_pairs(const int* __restrict__ unit_start, const int* __restrict__ n_units, int
                         arg = fmaf(fmaf(cr, cr, fmaf(cg, cg, cb * cb)), gp.kc, arg);
                     }
                     const float s = SemRow<DP, BF16>::dot(cs, ssq + j * SW);
-                    const float w = s * exp2f(arg);
+                    const float w = s * ex2_approx(arg);
                     const float wx = w * ex, wy = w * ey, wz = w * ez;
                     w0 += w;
                     d0 += wx; d1 += wy; d2s += wz;
@@ -490,26 +539,27 @@ k_pairs(const int* __restrict__ unit_start, const int* __restrict__ n_units, int
             const float qc6[6] = {q00, q01, q02, q11, q12, q22};
             W += w0;
 #pragma unroll
-            for (int m = 0; m < 3; ++m) {
-                Dv[m] += dc[m];
-                Sy[m] = fmaf(w0, x[m], Sy[m]) - dc[m];
+            for (int mm = 0; mm < 3; ++mm) {
+                Dv[mm] += dc[mm];
+                Sy[mm] = fmaf(w0, x[mm], Sy[mm]) - dc[mm];
             }
             int t6 = 0;
 #pragma unroll
-            for (int m = 0; m < 3; ++m)
+            for (int mm = 0; mm < 3; ++mm)
 #pragma unroll
-                for (int l = m; l < 3; ++l, ++t6) {
+                for (int l = mm; l < 3; ++l, ++t6) {
                     // sum w y'y'^T = W x x^T - x D^T - D x^T + Q
-                    Myy[t6] += fmaf(w0 * x[m], x[l], -(x[m] * dc[l] + dc[m] * x[l])) + qc6[t6];
+                    Myy[t6] += fmaf(w0 * x[mm], x[l], -(x[mm] * dc[l] + dc[mm] * x[l])) + qc6[t6];
                     Qm[t6] += qc6[t6];
                 }
 #pragma unroll
-            for (int m = 0; m < 3; ++m)
+            for (int mm = 0; mm < 3; ++mm)
 #pragma unroll
                 for (int l = 0; l < 3; ++l) {
                     // sum w d y'^T = D x^T - Q
-                    const int qi = (m <= l) ? (m == 0 ? l : (m == 1 ? 2 + l : 5)) : (l == 0 ? m : (l == 1 ? 2 + m : 5));
-                    Mdy[3 * m + l] += fmaf(dc[m], x[l], -qc6[qi]);
+                    const int qi = (mm <= l) ? (mm == 0 ? l : (mm == 1 ? 2 + l : 5))
+                                             : (l == 0 ? mm : (l == 1 ? 2 + mm : 5));
+                    Mdy[3 * mm + l] += fmaf(dc[mm], x[l], -qc6[qi]);
                 }
         }
         // home-centre coordinates -> frame-a coordinates: y' += o
@@ -518,16 +568,16 @@ k_pairs(const int* __restrict__ unit_start, const int* __restrict__ n_units, int
         {
             int t6 = 0;
 #pragma unroll
-            for (int m = 0; m < 3; ++m)
+            for (int mm = 0; mm < 3; ++mm)
 #pragma unroll
-                for (int l = m; l < 3; ++l, ++t6)
-                    Myy[t6] += Sy[m] * o[l] + o[m] * Sy[l] + W * o[m] * o[l];
+                for (int l = mm; l < 3; ++l, ++t6)
+                    Myy[t6] += Sy[mm] * o[l] + o[mm] * Sy[l] + W * o[mm] * o[l];
 #pragma unroll
-            for (int m = 0; m < 3; ++m)
+            for (int mm = 0; mm < 3; ++mm)
 #pragma unroll
-                for (int l = 0; l < 3; ++l) Mdy[3 * m + l] = fmaf(Dv[m], o[l], Mdy[3 * m + l]);
+                for (int l = 0; l < 3; ++l) Mdy[3 * mm + l] = fmaf(Dv[mm], o[l], Mdy[3 * mm + l]);
 #pragma unroll
-            for (int m = 0; m < 3; ++m) Sy[m] = fmaf(W, o[m], Sy[m]);
+            for (int mm = 0; mm < 3; ++mm) Sy[mm] = fmaf(W, o[mm], Sy[mm]);
         }
         const float* scl = edges[e].scale;
         long long* dst = acc + (long long)e * ACC_N;
@@ -548,7 +598,8 @@ k_pairs(const int* __restrict__ unit_start, const int* __restrict__ n_units, int
     }
 }
 
-// Same search, geometry only: writes the pair list of one edge (verification).
+// Same search and the same cutoff test, geometry only: writes the pair list
+// of one edge (verification).
 __global__ void __launch_bounds__(PAIR_T)
 k_emit_pairs(const int* __restrict__ unit_start, const int* __restrict__ n_units, int* unit_counter,
              const uint32_t* __restrict__ qkey, const float4* __restrict__ slots, long long Q,
@@ -556,11 +607,12 @@ k_emit_pairs(const int* __restrict__ unit_start, const int* __restrict__ n_units
              const int* __restrict__ cell_start, const float4* __restrict__ pts4, GridParams gp,
              int edge_sel, const int* __restrict__ perm_local, long long capacity,
              int* __restrict__ i_out, int* __restrict__ j_out, unsigned long long* n_out) {
-    __shared__ float4 s_q[PAIR_T / 32][32];
+    __shared__ float4 s_m[PAIR_T / 32][UQ];
+    __shared__ int s_j[PAIR_T / 32][UQ];
     __shared__ int s_rows[PAIR_T / 32][40];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
-    float4* sq = s_q[warp];
+    float4* sm = s_m[warp];
     const Rows R{s_rows[warp], s_rows[warp] + 9, s_rows[warp] + 18, s_rows[warp] + 27};
     const int nu = *n_units;
     for (;;) {
@@ -572,15 +624,20 @@ k_emit_pairs(const int* __restrict__ unit_start, const int* __restrict__ n_units
         const uint32_t key0 = qkey[k0];
         const int e = find_edge_bin(edges, E, key0);
         if (e != edge_sel) continue;
-        const long long kk = (long long)k0 + lane;
-        const bool mine = kk < Q && qkey[kk] == key0;
-        const int qcount = __popc(__ballot_sync(FULL, mine));
+        const int qcount = unit_queries(qkey, Q, k0, key0, lane);
         const FrameDev& Fa = frames[edges[e].a];
         const int dx0 = Fa.dim[0], dy0 = Fa.dim[1], dz0 = Fa.dim[2];
         const int cell = (int)(key0 - edges[e].bin_off);
         const int hx = cell % dx0, hy = (cell / dx0) % dy0, hz = cell / (dx0 * dy0);
         __syncwarp();
-        if (lane < qcount) sq[lane] = slots[kk];
+        for (int h = 0; h < 2; ++h) {
+            const int q = lane + 32 * h;
+            if (q < qcount) {
+                const float4 r = slots[(long long)k0 + q];
+                sm[q] = make_float4(-2.f * r.x, -2.f * r.y, -2.f * r.z, fmaf(r.x, r.x, fmaf(r.y, r.y, r.z * r.z)));
+                s_j[warp][q] = perm_local[__float_as_int(r.w)];
+            }
+        }
         const int C = build_rows(R, cell_start, Fa.cell_off, dx0, dy0, dz0, hx, hy, hz, lane);
         for (int c0 = 0; c0 < C; c0 += 32) {
             const int v = c0 + lane;
@@ -590,15 +647,15 @@ k_emit_pairs(const int* __restrict__ unit_start, const int* __restrict__ n_units
             const float4 p = __ldg(pts4 + i);
             const float x0 = fmaf((float)dx, gp.hf, p.x), x1 = fmaf((float)dy, gp.hf, p.y),
                         x2 = fmaf((float)dz, gp.hf, p.z);
+            const float thr = gp.rc2 - fmaf(x0, x0, fmaf(x1, x1, x2 * x2));
             for (int j = 0; j < qcount; ++j) {
-                const float4 y = sq[j];
-                const float ex = x0 - y.x, ey = x1 - y.y, ez = x2 - y.z;
-                const float d2 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
-                if (d2 < gp.rc2) {
-                    const unsigned long long t = atomicAdd(n_out, 1ULL);
-                    if ((long long)t < capacity) {
-                        i_out[t] = perm_local[i];
-                        j_out[t] = perm_local[__float_as_int(y.w)];
+                const float4 m = sm[j];
+                const float t = fmaf(x0, m.x, fmaf(x1, m.y, fmaf(x2, m.z, m.w)));
+                if (t < thr) {
+                    const unsigned long long k = atomicAdd(n_out, 1ULL);
+                    if ((long long)k < capacity) {
+                        i_out[k] = perm_local[i];
+                        j_out[k] = s_j[warp][j];
                     }
                 }
             }
@@ -620,6 +677,13 @@ void run_pairs(unsigned grid, cudaStream_t st, const int* unit_start, const int*
                const float4* pts4, const void* sem, const float4* col4, GridParams gp,
                long long* acc, const int* done) {
     const size_t smem = sizeof(float) * (PAIR_T / 32) * warp_smem_words<DP, BF16, COLOR>();
+    static int blocks_per_sm = 0;   // opt in to > 48 KB and size the persistent grid, once
+    if (!blocks_per_sm) {
+        cudaFuncSetAttribute(k_pairs<DP, BF16, COLOR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_pairs<DP, BF16, COLOR>, PAIR_T, smem);
+        if (blocks_per_sm < 1) blocks_per_sm = 1;
+    }
+    grid *= (unsigned)blocks_per_sm;
     k_pairs<DP, BF16, COLOR><<<grid, PAIR_T, smem, st>>>(unit_start, n_units, unit_counter, qkey, slots,
                                                          Q, edges, E, frames, cell_start, pts4, sem,
                                                          col4, gp, acc, done);
@@ -696,7 +760,7 @@ void launch_pairs(const int* unit_start, const int* n_units, int* unit_counter,
                   const void* sem_sorted, const float4* col4, GridParams gp, long long* acc,
                   const int* done, int num_sms, cudaStream_t st) {
     if (Q <= 0) return;
-    const unsigned grid = (unsigned)(num_sms * 3);
+    const unsigned grid = (unsigned)num_sms;   // times the resident blocks per SM
     const bool ok = gp.color
         ? dispatch_pairs<true>(grid, st, unit_start, n_units, unit_counter, qkey, slots, Q, edges, E, frames,
                                cell_start, pts4, sem_sorted, col4, gp, acc, done)
