@@ -499,7 +499,7 @@ rkhsba_status build(rkhsba_ctx* c, const double* xyz, const float* sem, const fl
     RK_TRY(alloc(c, &c->d_poses_cand, 16LL * K));
     RK_TRY(alloc(c, &c->d_state, 1));
     const long long nf = 6LL * (K - 1);
-    RK_TRY(alloc(c, &c->d_lm_ws, nf * nf + nf + 16));
+    RK_TRY(alloc(c, &c->d_lm_ws, nf * nf + 2 * nf + 16));
     RK_CUDA(c, cudaMemsetAsync(c->d_state, 0, sizeof(LMState), st));
     RK_CUDA(c, cudaStreamSynchronize(st));
     RK_CUDA(c, cudaGetLastError());

@@ -177,24 +177,33 @@ __global__ void k_query_gather(const uint32_t* __restrict__ key, const int* __re
     }
 }
 
-// a unit starts at the first query of a home cell and every UNIT_Q queries after
-__global__ void k_units(const uint32_t* __restrict__ key, const int* __restrict__ bin_first, long long Q,
-                        int* __restrict__ unit_start, int* __restrict__ n_units, const int* done) {
+// a unit starts at the first query of a home cell and every UNIT_Q queries
+// after; one atomic per block reserves the block's slots in the unit list
+__global__ void __launch_bounds__(256) k_units(const uint32_t* __restrict__ key, const int* __restrict__ bin_first,
+                                               long long Q, int* __restrict__ unit_start,
+                                               int* __restrict__ n_units, const int* done) {
     if (done && *done) return;
-    const int lane = threadIdx.x & 31;
-    for (long long base = (blockIdx.x * (long long)blockDim.x + threadIdx.x) & ~31LL; base < Q;
-         base += (long long)gridDim.x * blockDim.x) {
-        const long long k = base + lane;
+    __shared__ int s_cnt[8];
+    __shared__ int s_base;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (long long base = (long long)blockIdx.x * blockDim.x; base < Q; base += (long long)gridDim.x * blockDim.x) {
+        const long long k = base + threadIdx.x;
         bool st = false;
         if (k < Q) {
             const uint32_t kk = key[k];
             st = kk != NO_KEY && ((k - bin_first[kk]) % UNIT_Q) == 0;
         }
         const unsigned m = __ballot_sync(FULL, st);
-        int off = 0;
-        if (lane == 0 && m) off = atomicAdd(n_units, __popc(m));
-        off = __shfl_sync(FULL, off, 0);
-        if (st) unit_start[off + __popc(m & ((1u << lane) - 1u))] = (int)k;
+        if (lane == 0) s_cnt[warp] = __popc(m);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int tot = 0;
+            for (int w = 0; w < 8; ++w) { const int c = s_cnt[w]; s_cnt[w] = tot; tot += c; }
+            s_base = tot ? atomicAdd(n_units, tot) : 0;
+        }
+        __syncthreads();
+        if (st) unit_start[s_base + s_cnt[warp] + __popc(m & ((1u << lane) - 1u))] = (int)k;
+        __syncthreads();
     }
 }
 

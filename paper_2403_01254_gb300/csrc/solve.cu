@@ -235,6 +235,20 @@ __device__ __forceinline__ double block_max(double v, double* red) {
     return r;
 }
 
+// 1/sqrt(d) for d > 0: FP32 estimate refined by two Newton-Raphson steps
+// r <- r (3 - d r^2) / 2 in FP64 (each step doubles the correct bits:
+// ~2^-22 -> 2^-44 -> FP64 rounding).  Outside the FP32 range the estimate
+// falls back to the FP64 square root.
+__device__ __forceinline__ double rsqrt_nr(double d) {
+    const float f = (float)d;
+    double r;
+    if (f > 1e-37f && f < 1e37f) r = (double)rsqrtf(f);
+    else r = 1.0 / sqrt(d);
+    r = r * fma(-0.5 * d * r, r, 1.5);
+    r = r * fma(-0.5 * d * r, r, 1.5);
+    return r;
+}
+
 constexpr int LM_T = 512;
 constexpr int LM_SMEM_N = 160;   // n <= 160 keeps the factor in shared memory
 
@@ -268,40 +282,53 @@ __global__ void __launch_bounds__(LM_T) k_lm_solve(int K, const double* __restri
         A[(long long)i * n + i] = hii + lam * fmax(hii, floor_d);
     }
     __syncthreads();
-    // right-looking Cholesky, lower triangle in place
+    // right-looking Cholesky, lower triangle in place; the pivot's reciprocal
+    // square root is kept in rinv[] so that no FP64 division or square root
+    // sits on the sequential path
+    double* rinv = y + n;
+    const int warp = tid >> 5, lane = tid & 31;
+    constexpr int NW = LM_T / 32;
     for (int k = 0; k < n; ++k) {
         if (tid == 0) {
             const double d = A[(long long)k * n + k];
-            if (!(d > 0.0)) fail = 1;
-            else A[(long long)k * n + k] = sqrt(d);
+            const double r = rsqrt_nr(d);
+            if (!(d > 0.0) || !(r > 0.0) || !isfinite(r)) fail = 1;
+            else {
+                A[(long long)k * n + k] = d * r;   // sqrt(d)
+                rinv[k] = r;
+            }
         }
         __syncthreads();
         if (fail) break;
-        const double L = A[(long long)k * n + k];
-        for (int i = k + 1 + tid; i < n; i += LM_T) A[(long long)i * n + k] /= L;
+        const double r = rinv[k];
+        for (int i = k + 1 + tid; i < n; i += LM_T) A[(long long)i * n + k] *= r;
         __syncthreads();
-        const int m = n - k - 1;
-        for (long long idx = tid; idx < (long long)m * m; idx += LM_T) {
-            const int i = k + 1 + (int)(idx / m), j = k + 1 + (int)(idx % m);
-            if (j <= i) A[(long long)i * n + j] -= A[(long long)i * n + k] * A[(long long)j * n + k];
+        // rows over warps, columns j <= i over lanes
+        for (int i = k + 1 + warp; i < n; i += NW) {
+            const double lik = A[(long long)i * n + k];
+            for (int j = k + 1 + lane; j <= i; j += 32)
+                A[(long long)i * n + j] = fma(-lik, A[(long long)j * n + k], A[(long long)i * n + j]);
         }
         __syncthreads();
     }
     if (!fail) {
-        for (int k = 0; k < n; ++k) {           // L z = -b
-            if (tid == 0) y[k] /= A[(long long)k * n + k];
-            __syncthreads();
-            const double yk = y[k];
-            for (int i = k + 1 + tid; i < n; i += LM_T) y[i] -= A[(long long)i * n + k] * yk;
-            __syncthreads();
+        if (warp == 0) {                          // substitutions in one warp
+            for (int k = 0; k < n; ++k) {         // L z = -b
+                const double yk = y[k] * rinv[k];
+                __syncwarp();
+                if (lane == 0) y[k] = yk;
+                for (int i = k + 1 + lane; i < n; i += 32) y[i] = fma(-A[(long long)i * n + k], yk, y[i]);
+                __syncwarp();
+            }
+            for (int k = n - 1; k >= 0; --k) {    // L^T delta = z
+                const double yk = y[k] * rinv[k];
+                __syncwarp();
+                if (lane == 0) y[k] = yk;
+                for (int i = lane; i < k; i += 32) y[i] = fma(-A[(long long)k * n + i], yk, y[i]);
+                __syncwarp();
+            }
         }
-        for (int k = n - 1; k >= 0; --k) {      // L^T delta = z
-            if (tid == 0) y[k] /= A[(long long)k * n + k];
-            __syncthreads();
-            const double yk = y[k];
-            for (int i = tid; i < k; i += LM_T) y[i] -= A[(long long)k * n + i] * yk;
-            __syncthreads();
-        }
+        __syncthreads();
     } else {
         for (int i = tid; i < n; i += LM_T) y[i] = 0.0;
         __syncthreads();
@@ -404,7 +431,8 @@ void launch_frame_assemble(const EdgeDev* edges, int E, int K, const int* inc_of
 void launch_lm_solve(int K, const double* H_cur, const double* b_cur, const double* poses_cur,
                      double* poses_cand, LMState* st_dev, double* ws, cudaStream_t st) {
     const int n = 6 * (K - 1);
-    size_t smem = (n <= LM_SMEM_N) ? (size_t)(n * n + n) * sizeof(double) : 0;
+    // factor A (n x n), right-hand side y (n) and pivot reciprocals rinv (n)
+    size_t smem = (n <= LM_SMEM_N) ? (size_t)(n * n + 2 * n) * sizeof(double) : 0;
     if (smem > 48 * 1024)
         cudaFuncSetAttribute(k_lm_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k_lm_solve<<<1, LM_T, smem, st>>>(K, H_cur, b_cur, poses_cur, poses_cand, st_dev, ws);
