@@ -225,6 +225,72 @@ rkhsba_status rkhsba_eval_static(int32_t n_frames, const int64_t* n_points, cons
                                  const double* poses, double* loss, double* grad, double* H_full,
                                  void* cuda_stream);
 
+/* ------------------------------------------------------------------------
+ * Request server: continuous batching of BA solves on one GPU.
+ *
+ * Requests (each a problem as for rkhsba_create plus initial poses) are
+ * queued by rkhsba_submit and admitted while an in-flight slot is free and
+ * the device-memory budget allows (the problem's buffers are estimated from
+ * its sizes before admission and charged at their real size after).  Every
+ * admitted problem keeps its points and grids resident and runs the
+ * rkhsba_solve loop (Sec. V-A, V-C) on its own stream, a few LM iterations
+ * per issue, so the GPU work of different requests overlaps; a finished
+ * request frees its slot and memory and the next one is admitted at once.
+ * Results do not depend on what else is running: a request solved alone and
+ * in a mix gives the same poses bit for bit.
+ *
+ * Threads: rkhsba_submit / rkhsba_poll / rkhsba_cancel / rkhsba_server_stats
+ * may be called from any host threads; the server's own threads make all
+ * CUDA calls for its requests.  Failures of one request (invalid input,
+ * allocation failure, watchdog timeout) end that request only.
+ * ------------------------------------------------------------------------ */
+typedef struct rkhsba_server rkhsba_server;
+
+typedef struct {
+    int32_t max_inflight;      /* concurrently admitted requests (default 8) */
+    int32_t iters_per_issue;   /* LM iterations issued per round (default 4) */
+    int64_t memory_budget;     /* bytes of device memory for admitted requests
+                                  (0: half of the free memory at creation) */
+    double request_timeout_ms; /* watchdog per request from admission (0: none) */
+} rkhsba_server_config;
+
+typedef struct {
+    int32_t state;             /* 0 queued, 1 running, 2 finished, 3 failed, 4 cancelled */
+    int32_t status;            /* RKHSBA_OK / ENOTCONV when finished, error code otherwise */
+    rkhsba_solve_info solve;   /* as for rkhsba_solve */
+    double queue_ms;           /* submit -> admission */
+    double latency_ms;         /* submit -> result ready */
+    int64_t device_bytes;      /* device memory the request held */
+} rkhsba_request_info;
+
+rkhsba_status rkhsba_server_create(rkhsba_server** out, const rkhsba_server_config* cfg);
+
+/* Stop the server: running and queued requests are cancelled; returns once
+ * all GPU work of the server has finished and its memory is freed. */
+void rkhsba_server_destroy(rkhsba_server* srv);
+
+/* Queue one problem (arguments as for rkhsba_create, HOST memory, copied
+ * before the call returns) with initial poses [K*16]; *ticket names it. */
+rkhsba_status rkhsba_submit(rkhsba_server* srv, int32_t n_frames, const int64_t* n_points,
+                            const double* xyz, const float* sem, const float* rgb,
+                            int32_t n_edges, const int32_t* edges, const rkhsba_params* params,
+                            const double* poses0, int64_t* ticket);
+
+/* Wait up to timeout_ms (0: do not wait, < 0: wait forever) for a request.
+ * Returns RKHSBA_OK once it has ended (finished, failed or cancelled; see
+ * info->state / info->status) and writes poses [K*16] when finished; the
+ * ticket is then released.  Returns RKHSBA_EBUSY while it is still queued or
+ * running, RKHSBA_EINVAL for an unknown ticket. */
+rkhsba_status rkhsba_poll(rkhsba_server* srv, int64_t ticket, int32_t timeout_ms, double* poses,
+                          rkhsba_request_info* info);
+
+/* Ask a queued or running request to stop; its poll then reports state 4. */
+rkhsba_status rkhsba_cancel(rkhsba_server* srv, int64_t ticket);
+
+/* Counters: requests queued, running, finished so far; device bytes held. */
+rkhsba_status rkhsba_server_stats(rkhsba_server* srv, int64_t* queued, int64_t* running,
+                                  int64_t* finished, int64_t* device_bytes);
+
 /* Problem shape and device memory of a context. */
 rkhsba_status rkhsba_info(const rkhsba_ctx* ctx, int32_t* n_frames, int32_t* n_edges,
                           int64_t* n_points_total, int64_t* device_bytes);

@@ -5,10 +5,10 @@ The CUDA library ``librkhsba.so`` (C ABI in include/rkhsba.h) does all the
 work; ``rkhsba`` is its ctypes binding.  Importing this package does not
 touch the GPU; loading the library fails loudly when it cannot be built.
 """
-from .rkhsba import (Problem, RkhsbaError, load, make_params, rkhsba_create,  # noqa: F401
+from .rkhsba import (Problem, RkhsbaError, Server, load, make_params, rkhsba_create,  # noqa: F401
                      rkhsba_create_device, rkhsba_destroy, rkhsba_edge_pairs, rkhsba_eval,
                      rkhsba_get_state, rkhsba_info, rkhsba_iterate, rkhsba_launch_count,
                      rkhsba_rebuild, rkhsba_set_poses_device, rkhsba_solve, rkhsba_profile,
                      EXPORTS)
 
-__all__ = ["Problem", "RkhsbaError", "load", "make_params", "EXPORTS"]
+__all__ = ["Problem", "Server", "RkhsbaError", "load", "make_params", "EXPORTS"]

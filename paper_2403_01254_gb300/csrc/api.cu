@@ -621,6 +621,29 @@ rkhsba_status create_impl(rkhsba_ctx** out, int32_t n_frames, const int64_t* n_p
 }
 }  // namespace
 
+// Internal stepping interface for the request server (server.cu): the same
+// device-resident LM loop as rkhsba_solve, issued asynchronously.
+namespace rk {
+rkhsba_status ctx_begin_solve(rkhsba_ctx* c, const double* host_poses) {
+    RK_TRY(check_poses(c, host_poses));
+    RK_CUDA(c, cudaMemcpyAsync(c->d_poses_cand, host_poses, sizeof(double) * 16 * c->K, cudaMemcpyHostToDevice,
+                               c->stream));
+    reset_state(c);
+    lm_initial(c);
+    RK_CUDA(c, cudaGetLastError());
+    return RKHSBA_OK;
+}
+void ctx_iterate(rkhsba_ctx* c, int n) {
+    for (int i = 0; i < n; ++i) lm_iteration(c);
+}
+cudaStream_t ctx_stream(const rkhsba_ctx* c) { return c->stream; }
+const void* ctx_state_dev(const rkhsba_ctx* c) { return c->d_state; }
+const double* ctx_poses_dev(const rkhsba_ctx* c) { return c->d_poses_cur; }
+size_t ctx_bytes(const rkhsba_ctx* c) { return c->bytes; }
+int ctx_max_iters(const rkhsba_ctx* c) { return c->p.max_iters; }
+int ctx_state_bytes() { return (int)sizeof(LMState); }
+}  // namespace rk
+
 extern "C" {
 
 rkhsba_status rkhsba_create(rkhsba_ctx** out, int32_t n_frames, const int64_t* n_points,

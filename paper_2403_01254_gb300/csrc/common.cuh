@@ -164,7 +164,19 @@ void launch_copy_if_accepted(const LMState* st_dev, double* dst, const double* s
 
 }  // namespace rk
 
+#include "rkhsba.h"
+
 namespace rk {
 // api.cu: sets the message returned by rkhsba_last_error(NULL) on this thread
 void set_thread_error(const char* msg);
+
+// api.cu: asynchronous LM stepping of a context (used by the request server)
+rkhsba_status ctx_begin_solve(rkhsba_ctx* c, const double* host_poses);
+void ctx_iterate(rkhsba_ctx* c, int n);
+cudaStream_t ctx_stream(const rkhsba_ctx* c);
+const void* ctx_state_dev(const rkhsba_ctx* c);
+const double* ctx_poses_dev(const rkhsba_ctx* c);
+size_t ctx_bytes(const rkhsba_ctx* c);
+int ctx_max_iters(const rkhsba_ctx* c);
+int ctx_state_bytes();
 }  // namespace rk

@@ -1,0 +1,470 @@
+// Request server: continuous batching of RKHS-BA solves on one GPU.
+//
+// Two host threads drive the device.  The admission thread takes queued
+// requests while an in-flight slot is free and the device-memory budget has
+// room, builds each problem (upload + grid step) on the slot's stream and
+// hands it to the stepping thread.  The stepping thread advances every
+// admitted problem by a few LM iterations at a time (the loop of
+// rkhsba_solve: solve, evaluate, accept; Sec. V-A, V-C), checks completion
+// with an event per issue, and finishes requests whose LM state says done:
+// poses copied out, context destroyed, slot and memory released, waiting
+// pollers and the admission thread woken.  Problems on different streams run
+// concurrently on the GPU.  Because every evaluation is exact in its
+// reductions (fixed point) and stable in its sorts, a request's result does
+// not depend on which other requests share the GPU.
+#include "common.cuh"
+#include "rkhsba.h"
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cmath>
+#include <condition_variable>
+#include <deque>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+namespace {
+using namespace rk;
+using Clock = std::chrono::steady_clock;
+
+enum ReqState { RQ_QUEUED = 0, RQ_RUNNING = 1, RQ_DONE = 2, RQ_FAILED = 3, RQ_CANCELLED = 4 };
+
+struct Req {
+    int64_t ticket = 0;
+    int K = 0, E = 0;
+    std::vector<int64_t> n;
+    std::vector<double> xyz;
+    std::vector<float> sem, rgb;
+    std::vector<int32_t> edges;
+    rkhsba_params p{};
+    std::vector<double> poses0;
+    size_t est = 0, bytes = 0;
+    int state = RQ_QUEUED;
+    int status = RKHSBA_OK;
+    std::atomic<bool> cancel{false};
+    rkhsba_ctx* ctx = nullptr;
+    int slot = -1;
+    cudaEvent_t ev = nullptr;
+    bool started = false;
+    int issued = 0;
+    Clock::time_point t_submit, t_admit, t_done;
+    rkhsba_solve_info info{};
+    std::vector<double> result;
+};
+
+double ms_between(Clock::time_point a, Clock::time_point b) {
+    return std::chrono::duration<double, std::milli>(b - a).count();
+}
+
+// Device bytes a problem will hold, from its sizes (mirrors the buffers of
+// rkhsba_create): points, labels, sort buffers, grids over the frames'
+// bounding boxes, per-edge queries and home cells, and the 6K system.
+size_t estimate_bytes(const Req& r) {
+    const double rc = (r.p.cutoff_mult > 0 ? r.p.cutoff_mult : 3.0) * r.p.ell;
+    const double h = rc * (1.0 + 1.0 / 1024.0);
+    std::vector<double> cells(r.K, 1.0);
+    long long off = 0;
+    for (int m = 0; m < r.K; ++m) {
+        if (r.n[m] > 0) {
+            double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+            for (long long i = off; i < off + r.n[m]; ++i)
+                for (int k = 0; k < 3; ++k) {
+                    lo[k] = std::min(lo[k], r.xyz[3 * i + k]);
+                    hi[k] = std::max(hi[k], r.xyz[3 * i + k]);
+                }
+            double c = 1.0;
+            for (int k = 0; k < 3; ++k) c *= std::floor((hi[k] - lo[k]) / h) + 4.0;
+            cells[m] = c;
+        }
+        off += r.n[m];
+    }
+    double N = (double)off, Q = 0, bins = 0, C = 0;
+    for (int m = 0; m < r.K; ++m) C += cells[m];
+    for (int e = 0; e < r.E; ++e) {
+        int a = std::min(r.edges[2 * e], r.edges[2 * e + 1]), b = std::max(r.edges[2 * e], r.edges[2 * e + 1]);
+        Q += (double)r.n[b];
+        bins += cells[a];
+    }
+    const double D = r.p.sem_dim;
+    const double bytes = N * (24 + 8 * D + 16 + 16 + 40 + 12) + Q * 68 + bins * 4 + C * 4 +
+                         (double)r.K * r.K * 36 * 8 * 2 + (double)r.E * 1600 + (4 << 20);
+    return (size_t)(bytes * 1.25);
+}
+}  // namespace
+
+struct rkhsba_server {
+    rkhsba_server_config cfg{};
+    std::vector<cudaStream_t> streams;
+    std::vector<int> free_slots;
+    std::mutex mu;
+    std::condition_variable cv_admit;   // admission thread: queue or resources changed
+    std::condition_variable cv_done;    // pollers: a request ended
+    std::condition_variable cv_step;    // stepping thread: new running request
+    std::deque<Req*> queue;
+    std::vector<Req*> running;
+    std::unordered_map<int64_t, Req*> all;
+    size_t mem_in_use = 0;
+    int64_t next_ticket = 1;
+    int64_t finished = 0;
+    bool stop = false;
+    std::thread admit_thr, step_thr;
+    int device = 0;
+
+    void admit_loop();
+    void step_loop();
+    void finish(Req* r, int state, int status);   // called without mu held
+};
+
+void rkhsba_server::finish(Req* r, int state, int status) {
+    if (r->ctx) {
+        if (state == RQ_DONE) {
+            LMState s{};
+            cudaStream_t st = ctx_stream(r->ctx);
+            cudaError_t e1 = cudaMemcpyAsync(&s, ctx_state_dev(r->ctx), sizeof(LMState), cudaMemcpyDeviceToHost, st);
+            r->result.assign((size_t)16 * r->K, 0.0);
+            cudaError_t e2 = cudaMemcpyAsync(r->result.data(), ctx_poses_dev(r->ctx), sizeof(double) * 16 * r->K,
+                                             cudaMemcpyDeviceToHost, st);
+            cudaError_t e3 = cudaStreamSynchronize(st);
+            if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess) {
+                state = RQ_FAILED;
+                status = RKHSBA_ECUDA;
+            } else {
+                r->info.iters = s.iters;
+                r->info.status = s.done ? s.status : RKHSBA_ENOTCONV;
+                r->info.final_loss = -s.F_cur;
+                r->info.lambda = s.lambda;
+                r->info.pair_terms = s.pair_terms;
+                status = r->info.status;
+            }
+        }
+        rkhsba_destroy(r->ctx);
+        r->ctx = nullptr;
+    }
+    if (r->ev) {
+        cudaEventDestroy(r->ev);
+        r->ev = nullptr;
+    }
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        if (r->slot >= 0) free_slots.push_back(r->slot);
+        r->slot = -1;
+        mem_in_use -= std::min(mem_in_use, r->bytes);
+        r->state = state;
+        r->status = status;
+        r->t_done = Clock::now();
+        running.erase(std::remove(running.begin(), running.end(), r), running.end());
+        r->xyz.clear(); r->xyz.shrink_to_fit();
+        r->sem.clear(); r->sem.shrink_to_fit();
+        r->rgb.clear(); r->rgb.shrink_to_fit();
+        ++finished;
+    }
+    cv_done.notify_all();
+    cv_admit.notify_all();
+}
+
+void rkhsba_server::admit_loop() {
+    cudaSetDevice(device);
+    for (;;) {
+        Req* r = nullptr;
+        int slot = -1;
+        {
+            std::unique_lock<std::mutex> lk(mu);
+            for (;;) {
+                if (stop) return;
+                // drop cancelled requests at the head of the queue
+                while (!queue.empty() && queue.front()->cancel) {
+                    Req* c = queue.front();
+                    queue.pop_front();
+                    c->state = RQ_CANCELLED;
+                    c->status = RKHSBA_OK;
+                    c->t_done = Clock::now();
+                    ++finished;
+                    cv_done.notify_all();
+                }
+                if (!queue.empty() && !free_slots.empty()) {
+                    Req* q = queue.front();
+                    // admit by memory; a request larger than the whole budget
+                    // runs alone once nothing else holds memory
+                    if (mem_in_use + q->est <= (size_t)cfg.memory_budget || mem_in_use == 0) break;
+                }
+                cv_admit.wait(lk);
+            }
+            r = queue.front();
+            queue.pop_front();
+            slot = free_slots.back();
+            free_slots.pop_back();
+            r->slot = slot;
+            mem_in_use += r->est;
+            r->state = RQ_RUNNING;
+            r->t_admit = Clock::now();
+        }
+        rkhsba_ctx* ctx = nullptr;
+        rkhsba_status s = rkhsba_create(&ctx, r->K, r->n.data(), r->xyz.data(), r->sem.empty() ? nullptr : r->sem.data(),
+                                        r->rgb.empty() ? nullptr : r->rgb.data(), r->E, r->edges.data(), &r->p,
+                                        (void*)streams[slot]);
+        if (s == RKHSBA_OK) s = ctx_begin_solve(ctx, r->poses0.data());
+        cudaEvent_t ev = nullptr;
+        if (s == RKHSBA_OK && cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) s = RKHSBA_ECUDA;
+        if (s != RKHSBA_OK) {
+            r->ctx = ctx;
+            {
+                std::lock_guard<std::mutex> lk(mu);
+                mem_in_use -= std::min(mem_in_use, r->est);
+                r->est = 0;
+            }
+            finish(r, RQ_FAILED, s);
+            continue;
+        }
+        {
+            std::lock_guard<std::mutex> lk(mu);
+            r->ctx = ctx;
+            r->ev = ev;
+            const size_t real = ctx_bytes(ctx);
+            mem_in_use = mem_in_use - std::min(mem_in_use, r->est) + real;
+            r->bytes = real;
+            running.push_back(r);
+        }
+        cv_step.notify_all();
+    }
+}
+
+void rkhsba_server::step_loop() {
+    cudaSetDevice(device);
+    const int chunk = std::max(1, cfg.iters_per_issue);
+    std::vector<Req*> snap;
+    for (;;) {
+        {
+            std::unique_lock<std::mutex> lk(mu);
+            if (stop) return;
+            if (running.empty()) cv_step.wait_for(lk, std::chrono::milliseconds(5));
+            if (stop) return;
+            snap = running;
+        }
+        bool issued = false;
+        for (Req* r : snap) {
+            if (r->cancel) {
+                if (r->started) cudaEventSynchronize(r->ev);
+                finish(r, RQ_CANCELLED, RKHSBA_OK);
+                continue;
+            }
+            if (cfg.request_timeout_ms > 0 && ms_between(r->t_admit, Clock::now()) > cfg.request_timeout_ms) {
+                if (r->started) cudaEventSynchronize(r->ev);
+                finish(r, RQ_FAILED, RKHSBA_ETIMEOUT);
+                continue;
+            }
+            if (!r->started) {
+                r->started = true;
+                ctx_iterate(r->ctx, chunk);
+                r->issued = chunk;
+                cudaEventRecord(r->ev, ctx_stream(r->ctx));
+                issued = true;
+                continue;
+            }
+            const cudaError_t q = cudaEventQuery(r->ev);
+            if (q == cudaErrorNotReady) continue;
+            if (q != cudaSuccess) {
+                finish(r, RQ_FAILED, RKHSBA_ECUDA);
+                continue;
+            }
+            LMState s{};
+            cudaStream_t rs = ctx_stream(r->ctx);
+            if (cudaMemcpyAsync(&s, ctx_state_dev(r->ctx), sizeof(LMState), cudaMemcpyDeviceToHost, rs) != cudaSuccess ||
+                cudaStreamSynchronize(rs) != cudaSuccess) {
+                finish(r, RQ_FAILED, RKHSBA_ECUDA);
+                continue;
+            }
+            if (s.done || r->issued >= ctx_max_iters(r->ctx)) {
+                finish(r, RQ_DONE, RKHSBA_OK);
+                continue;
+            }
+            ctx_iterate(r->ctx, std::min(chunk, ctx_max_iters(r->ctx) - r->issued));
+            r->issued += chunk;
+            cudaEventRecord(r->ev, ctx_stream(r->ctx));
+            issued = true;
+        }
+        if (!issued) std::this_thread::sleep_for(std::chrono::microseconds(20));
+    }
+}
+
+extern "C" {
+
+rkhsba_status rkhsba_server_create(rkhsba_server** out, const rkhsba_server_config* cfg) {
+    if (!out) return RKHSBA_EINVAL;
+    *out = nullptr;
+    rkhsba_server* s = new rkhsba_server();
+    if (cfg) s->cfg = *cfg;
+    if (s->cfg.max_inflight <= 0) s->cfg.max_inflight = 8;
+    if (s->cfg.iters_per_issue <= 0) s->cfg.iters_per_issue = 4;
+    if (cudaGetDevice(&s->device) != cudaSuccess) {
+        delete s;
+        set_thread_error("no CUDA device");
+        return RKHSBA_ECUDA;
+    }
+    if (s->cfg.memory_budget <= 0) {
+        size_t fr = 0, tot = 0;
+        if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
+            delete s;
+            set_thread_error("cudaMemGetInfo failed");
+            return RKHSBA_ECUDA;
+        }
+        s->cfg.memory_budget = (int64_t)(fr / 2);
+    }
+    for (int i = 0; i < s->cfg.max_inflight; ++i) {
+        cudaStream_t st;
+        if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+            for (auto x : s->streams) cudaStreamDestroy(x);
+            delete s;
+            set_thread_error("stream creation failed");
+            return RKHSBA_ECUDA;
+        }
+        s->streams.push_back(st);
+        s->free_slots.push_back(s->cfg.max_inflight - 1 - i);
+    }
+    s->admit_thr = std::thread([s] { s->admit_loop(); });
+    s->step_thr = std::thread([s] { s->step_loop(); });
+    *out = s;
+    return RKHSBA_OK;
+}
+
+void rkhsba_server_destroy(rkhsba_server* s) {
+    if (!s) return;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->stop = true;
+    }
+    s->cv_admit.notify_all();
+    s->cv_step.notify_all();
+    s->admit_thr.join();
+    s->step_thr.join();
+    // cancel what is left: the threads are gone, so no lock contention
+    std::vector<Req*> left = s->running;
+    for (Req* r : left) {
+        if (r->ev && r->started) cudaEventSynchronize(r->ev);
+        s->finish(r, RQ_CANCELLED, RKHSBA_OK);
+    }
+    for (auto st : s->streams) {
+        cudaStreamSynchronize(st);
+        cudaStreamDestroy(st);
+    }
+    for (auto& kv : s->all) delete kv.second;
+    delete s;
+}
+
+rkhsba_status rkhsba_submit(rkhsba_server* s, int32_t n_frames, const int64_t* n_points, const double* xyz,
+                            const float* sem, const float* rgb, int32_t n_edges, const int32_t* edges,
+                            const rkhsba_params* params, const double* poses0, int64_t* ticket) {
+    if (!s || !n_points || !edges || !params || !poses0 || !ticket || n_frames < 1 || n_edges < 1) {
+        set_thread_error("rkhsba_submit: bad arguments");
+        return RKHSBA_EINVAL;
+    }
+    Req* r = new Req();
+    r->K = n_frames;
+    r->E = n_edges;
+    r->n.assign(n_points, n_points + n_frames);
+    long long N = 0;
+    for (int m = 0; m < n_frames; ++m) {
+        if (n_points[m] < 0) {
+            delete r;
+            set_thread_error("rkhsba_submit: negative point count");
+            return RKHSBA_EINVAL;
+        }
+        N += n_points[m];
+    }
+    if (N > 0 && !xyz) {
+        delete r;
+        set_thread_error("rkhsba_submit: xyz is NULL");
+        return RKHSBA_EINVAL;
+    }
+    r->xyz.assign(xyz, xyz + 3 * N);
+    if (sem && params->sem_dim > 0) r->sem.assign(sem, sem + (size_t)N * params->sem_dim);
+    if (rgb) r->rgb.assign(rgb, rgb + 3 * N);
+    r->edges.assign(edges, edges + 2 * n_edges);
+    r->p = *params;
+    r->poses0.assign(poses0, poses0 + 16 * n_frames);
+    if (!(r->p.ell > 0.0)) {
+        delete r;
+        set_thread_error("rkhsba_submit: params.ell must be > 0");
+        return RKHSBA_EINVAL;
+    }
+    for (int e = 0; e < n_edges; ++e)
+        if (edges[2 * e] < 0 || edges[2 * e] >= n_frames || edges[2 * e + 1] < 0 || edges[2 * e + 1] >= n_frames) {
+            delete r;
+            set_thread_error("rkhsba_submit: edge names a missing frame");
+            return RKHSBA_EINVAL;
+        }
+    r->est = estimate_bytes(*r);
+    r->t_submit = Clock::now();
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        if (s->stop) {
+            delete r;
+            return RKHSBA_EBUSY;
+        }
+        r->ticket = s->next_ticket++;
+        s->all[r->ticket] = r;
+        s->queue.push_back(r);
+        *ticket = r->ticket;
+    }
+    s->cv_admit.notify_all();
+    return RKHSBA_OK;
+}
+
+rkhsba_status rkhsba_poll(rkhsba_server* s, int64_t ticket, int32_t timeout_ms, double* poses,
+                          rkhsba_request_info* info) {
+    if (!s) return RKHSBA_EINVAL;
+    std::unique_lock<std::mutex> lk(s->mu);
+    auto it = s->all.find(ticket);
+    if (it == s->all.end()) {
+        set_thread_error("rkhsba_poll: unknown ticket");
+        return RKHSBA_EINVAL;
+    }
+    Req* r = it->second;
+    auto ended = [r] { return r->state >= RQ_DONE; };
+    if (!ended()) {
+        if (timeout_ms < 0) s->cv_done.wait(lk, ended);
+        else if (timeout_ms > 0) s->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), ended);
+    }
+    if (info) {
+        info->state = r->state;
+        info->status = r->status;
+        info->solve = r->info;
+        info->queue_ms = r->state == RQ_QUEUED ? ms_between(r->t_submit, Clock::now())
+                                               : ms_between(r->t_submit, r->t_admit);
+        info->latency_ms = ended() ? ms_between(r->t_submit, r->t_done) : ms_between(r->t_submit, Clock::now());
+        info->device_bytes = (int64_t)r->bytes;
+    }
+    if (!ended()) return RKHSBA_EBUSY;
+    if (poses && r->state == RQ_DONE) std::copy(r->result.begin(), r->result.end(), poses);
+    s->all.erase(it);
+    delete r;
+    return RKHSBA_OK;
+}
+
+rkhsba_status rkhsba_cancel(rkhsba_server* s, int64_t ticket) {
+    if (!s) return RKHSBA_EINVAL;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        auto it = s->all.find(ticket);
+        if (it == s->all.end()) return RKHSBA_EINVAL;
+        it->second->cancel = true;
+    }
+    s->cv_admit.notify_all();
+    return RKHSBA_OK;
+}
+
+rkhsba_status rkhsba_server_stats(rkhsba_server* s, int64_t* queued, int64_t* running, int64_t* finished,
+                                  int64_t* device_bytes) {
+    if (!s) return RKHSBA_EINVAL;
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (queued) *queued = (int64_t)s->queue.size();
+    if (running) *running = (int64_t)s->running.size();
+    if (finished) *finished = s->finished;
+    if (device_bytes) *device_bytes = (int64_t)s->mem_in_use;
+    return RKHSBA_OK;
+}
+
+}  // extern "C"

@@ -21,7 +21,8 @@ EXPORTS = [
     "rkhsba_create", "rkhsba_create_device", "rkhsba_destroy", "rkhsba_eval", "rkhsba_solve",
     "rkhsba_set_poses_device", "rkhsba_rebuild", "rkhsba_iterate", "rkhsba_get_state",
     "rkhsba_edge_pairs", "rkhsba_info", "rkhsba_last_error", "rkhsba_launch_count",
-    "rkhsba_profile",
+    "rkhsba_profile", "rkhsba_server_create", "rkhsba_server_destroy", "rkhsba_submit",
+    "rkhsba_poll", "rkhsba_cancel", "rkhsba_server_stats",
 ]
 
 
@@ -41,6 +42,19 @@ class Params(C.Structure):
 class SolveInfo(C.Structure):
     _fields_ = [("iters", C.c_int32), ("status", C.c_int32), ("final_loss", C.c_double),
                 ("lam", C.c_double), ("pair_terms", C.c_int64)]
+
+
+class ServerConfig(C.Structure):
+    _fields_ = [("max_inflight", C.c_int32), ("iters_per_issue", C.c_int32),
+                ("memory_budget", C.c_int64), ("request_timeout_ms", C.c_double)]
+
+
+class RequestInfo(C.Structure):
+    _fields_ = [("state", C.c_int32), ("status", C.c_int32), ("solve", SolveInfo),
+                ("queue_ms", C.c_double), ("latency_ms", C.c_double), ("device_bytes", C.c_int64)]
+
+
+REQUEST_STATES = {0: "queued", 1: "running", 2: "finished", 3: "failed", 4: "cancelled"}
 
 
 _lib = None
@@ -81,12 +95,20 @@ def load(build_if_missing=True):
         "rkhsba_last_error": [vp],
         "rkhsba_launch_count": [],
         "rkhsba_profile": [vp, C.c_int32, P(C.c_double), P(C.c_int64)],
+        "rkhsba_server_create": [P(vp), P(ServerConfig)],
+        "rkhsba_server_destroy": [vp],
+        "rkhsba_submit": [vp, C.c_int32, P(C.c_int64), P(C.c_double), P(C.c_float), P(C.c_float),
+                          C.c_int32, P(C.c_int32), P(Params), P(C.c_double), P(C.c_int64)],
+        "rkhsba_poll": [vp, C.c_int64, C.c_int32, P(C.c_double), P(RequestInfo)],
+        "rkhsba_cancel": [vp, C.c_int64],
+        "rkhsba_server_stats": [vp, P(C.c_int64), P(C.c_int64), P(C.c_int64), P(C.c_int64)],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
         f.argtypes = args
         f.restype = C.c_int
     lib.rkhsba_destroy.restype = None
+    lib.rkhsba_server_destroy.restype = None
     lib.rkhsba_last_error.restype = C.c_char_p
     lib.rkhsba_launch_count.restype = C.c_int64
     _lib = lib
@@ -321,3 +343,112 @@ def rkhsba_eval_static(n_points, d_xyz, d_sem, d_rgb, edges, params, poses, stre
              C.byref(params), _ptr(T, C.c_double), _ptr(loss, C.c_double), _ptr(grad, C.c_double),
              _ptr(H, C.c_double), stream))
     return dict(loss=float(loss[0]), grad=grad, H=H)
+
+
+# ------------------------------------------------------------- server ------
+class Server:
+    """Continuous-batching request server (rkhsba_server_* in the C ABI)."""
+
+    def __init__(self, max_inflight=8, iters_per_issue=4, memory_budget=0, request_timeout_ms=0.0):
+        lib = load()
+        cfg = ServerConfig(int(max_inflight), int(iters_per_issue), int(memory_budget),
+                           float(request_timeout_ms))
+        h = C.c_void_p()
+        _check(lib.rkhsba_server_create(C.byref(h), C.byref(cfg)))
+        self.h = h.value
+        self.K = {}
+
+    def submit(self, prob, poses0=None, **over):
+        """Queue a problem dict (as produced by ``scenes``); returns a ticket."""
+        lib = load()
+        p = dict(prob["params"])
+        p.update(over)
+        K = len(prob["xyz"])
+        sem = prob.get("sem")
+        sem_dim = 0 if sem is None else int(np.asarray(sem[0]).shape[-1])
+        params = make_params(p["ell"], p.get("cutoff_mult", 3.0), p.get("sigma", 1.0),
+                             p.get("ell_color", 0.0), sem_dim, p.get("sem_bf16", 0),
+                             p.get("max_iters", 100), p.get("lambda0", 1e-4),
+                             p.get("tol_step", 1e-10), p.get("tol_rel_f", 1e-12))
+        n = np.array([len(x) for x in prob["xyz"]], np.int64)
+        xyz = np.ascontiguousarray(np.concatenate([np.asarray(x, np.float64).reshape(-1, 3)
+                                                   for x in prob["xyz"]]))
+        semf = None
+        if sem is not None:
+            semf = np.ascontiguousarray(np.concatenate([np.asarray(s_, np.float32).reshape(len(x), sem_dim)
+                                                        for s_, x in zip(sem, prob["xyz"])]))
+        rgb = prob.get("rgb")
+        rgbf = None
+        if rgb is not None and p.get("ell_color", 0.0) > 0:
+            rgbf = np.ascontiguousarray(np.concatenate([np.asarray(c, np.float32).reshape(-1, 3)
+                                                        for c in rgb]))
+        e = np.ascontiguousarray(np.asarray(prob["edges"], np.int32).reshape(-1))
+        T0 = np.ascontiguousarray(prob["poses0"] if poses0 is None else poses0,
+                                  dtype=np.float64).reshape(K * 16)
+        t = C.c_int64()
+        _check(lib.rkhsba_submit(self.h, K, _ptr(n, C.c_int64), _ptr(xyz, C.c_double),
+                                 _ptr(semf, C.c_float), _ptr(rgbf, C.c_float), len(e) // 2,
+                                 _ptr(e, C.c_int32), C.byref(params), _ptr(T0, C.c_double),
+                                 C.byref(t)))
+        self.K[t.value] = K
+        return t.value
+
+    def poll(self, ticket, timeout_ms=-1):
+        """(poses or None, info) once the request ended, None while it runs."""
+        K = self.K[ticket]
+        T = np.zeros(K * 16)
+        info = RequestInfo()
+        st = load().rkhsba_poll(self.h, int(ticket), int(timeout_ms), _ptr(T, C.c_double),
+                                C.byref(info))
+        if st == EBUSY:
+            return None
+        _check(st)
+        del self.K[ticket]
+        d = dict(state=REQUEST_STATES[info.state], status=STATUS_NAMES.get(info.status, info.status),
+                 iters=info.solve.iters, final_loss=info.solve.final_loss,
+                 pair_terms=int(info.solve.pair_terms), queue_ms=info.queue_ms,
+                 latency_ms=info.latency_ms, device_bytes=int(info.device_bytes))
+        return (T.reshape(K, 4, 4) if info.state == 2 else None), d
+
+    def cancel(self, ticket):
+        _check(load().rkhsba_cancel(self.h, int(ticket)))
+
+    def stats(self):
+        q, r, f, b = C.c_int64(), C.c_int64(), C.c_int64(), C.c_int64()
+        _check(load().rkhsba_server_stats(self.h, C.byref(q), C.byref(r), C.byref(f), C.byref(b)))
+        return dict(queued=q.value, running=r.value, finished=f.value, device_bytes=b.value)
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().rkhsba_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def rkhsba_server_create(max_inflight=8, iters_per_issue=4, memory_budget=0, request_timeout_ms=0.0):
+    return Server(max_inflight, iters_per_issue, memory_budget, request_timeout_ms)
+
+
+def rkhsba_server_destroy(server):
+    server.close()
+
+
+def rkhsba_submit(server, prob, poses0=None, **over):
+    return server.submit(prob, poses0, **over)
+
+
+def rkhsba_poll(server, ticket, timeout_ms=-1):
+    return server.poll(ticket, timeout_ms)
+
+
+def rkhsba_cancel(server, ticket):
+    server.cancel(ticket)
+
+
+def rkhsba_server_stats(server):
+    return server.stats()

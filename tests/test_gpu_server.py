@@ -1,0 +1,136 @@
+"""Request server (continuous batching) on the GPU.
+
+A request's result must not depend on what else is running: solved alone, in
+a mix with others, and through rkhsba_solve, the poses are the same bit for
+bit (every reduction of the evaluation is exact in fixed point and every sort
+is stable).  Failures of one request (bad input, watchdog, cancellation) end
+that request only; shutting the server down with work in flight returns.
+"""
+import time
+
+import numpy as np
+import pytest
+
+import scenes
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pk():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2403_01254_gb300 as pk
+    pk.load()
+    return pk
+
+
+def _problems():
+    out = []
+    for k, (K, n) in enumerate([(3, 2500), (2, 4000), (4, 1500), (3, 3000), (2, 1200), (5, 1000)]):
+        p = scenes.lidar_street_problem(seed=900 + k, n_frames=K, n_points=n, max_deg=3.0, max_trans=0.1)
+        p["params"] = dict(p["params"], max_iters=25)
+        out.append(p)
+    out.append(scenes.tiny_problem(seed=77, n_frames=3, n=300, extent=1.0, ell=0.15, color=True))
+    out[-1]["params"] = dict(out[-1]["params"], max_iters=25)
+    return out
+
+
+def test_results_same_alone_in_mix_and_direct(pk):
+    probs = _problems()
+    direct = []
+    for p in probs:
+        g = pk.Problem.from_scene(p)
+        try:
+            direct.append(g.solve(p["poses0"]))
+        finally:
+            g.close()
+    srv = pk.Server(max_inflight=4)
+    try:
+        alone = []
+        for p in probs:
+            t = srv.submit(p)
+            alone.append(srv.poll(t, timeout_ms=-1))
+        tickets = [srv.submit(p) for p in probs]
+        mix = [srv.poll(t, timeout_ms=-1) for t in tickets]
+    finally:
+        srv.close()
+    for (Td, infd), (Ta, ia), (Tm, im) in zip(direct, alone, mix):
+        assert ia["state"] == "finished" and im["state"] == "finished"
+        assert np.array_equal(Ta, Tm), "mix changed the result"
+        assert np.array_equal(Ta, Td), "server differs from rkhsba_solve"
+        assert ia["iters"] == im["iters"] == infd["iters"]
+        assert ia["pair_terms"] == im["pair_terms"] == infd["pair_terms"]
+
+
+def test_admission_by_memory_runs_one_at_a_time(pk):
+    probs = _problems()[:4]
+    srv = pk.Server(max_inflight=4, memory_budget=1)   # every request exceeds the budget
+    try:
+        tickets = [srv.submit(p) for p in probs]
+        seen = 0
+        while True:
+            s = srv.stats()
+            seen = max(seen, s["running"])
+            if s["finished"] >= len(probs):
+                break
+            time.sleep(0.002)
+        res = [srv.poll(t, timeout_ms=-1) for t in tickets]
+    finally:
+        srv.close()
+    assert seen <= 1
+    assert all(r[1]["state"] == "finished" for r in res)
+
+
+def test_bad_request_fails_alone(pk):
+    probs = _problems()[:3]
+    bad = dict(probs[1], xyz=[x.copy() for x in probs[1]["xyz"]])
+    bad["xyz"][0][5, 2] = np.nan
+    srv = pk.Server(max_inflight=2)
+    try:
+        t0 = srv.submit(probs[0])
+        tb = srv.submit(bad)
+        t2 = srv.submit(probs[2])
+        r0, rb, r2 = (srv.poll(t, timeout_ms=-1) for t in (t0, tb, t2))
+        with pytest.raises(pk.RkhsbaError) as ei:
+            srv.submit(dict(probs[0], edges=np.array([[0, 9]], np.int32)))
+        assert ei.value.status == 1
+    finally:
+        srv.close()
+    assert r0[1]["state"] == "finished" and r2[1]["state"] == "finished"
+    assert rb[1]["state"] == "failed" and rb[1]["status"] == "EINVAL" and rb[0] is None
+
+
+def test_cancel_and_watchdog(pk):
+    big = scenes.lidar_street_problem(seed=5, n_frames=6, n_points=20000)
+    big["params"] = dict(big["params"], max_iters=100)
+    srv = pk.Server(max_inflight=1)
+    try:
+        t1 = srv.submit(big)
+        t2 = srv.submit(big)          # queued behind t1
+        srv.cancel(t2)
+        srv.cancel(t1)
+        r1 = srv.poll(t1, timeout_ms=-1)
+        r2 = srv.poll(t2, timeout_ms=-1)
+    finally:
+        srv.close()
+    assert r1[1]["state"] in ("cancelled", "finished")
+    assert r2[1]["state"] == "cancelled"
+    srv = pk.Server(max_inflight=1, request_timeout_ms=0.001)
+    try:
+        t = srv.submit(big)
+        r = srv.poll(t, timeout_ms=-1)
+    finally:
+        srv.close()
+    assert r[1]["state"] == "failed" and r[1]["status"] == "ETIMEOUT"
+
+
+def test_shutdown_with_requests_in_flight(pk):
+    probs = _problems()
+    srv = pk.Server(max_inflight=3)
+    for p in probs:
+        srv.submit(p)
+    t0 = time.time()
+    srv.close()
+    assert time.time() - t0 < 60
