@@ -42,9 +42,19 @@ def flops_per_pair(sem_dim, color):
     return 29 + 2 * sem_dim + (9 if color else 0)
 
 
-def workload():
+WORKLOADS = {
+    # name: (generator, kwargs); the default is the headline workload
+    "lidar_street_8x20000": ("lidar_street_problem", dict(seed=1434)),
+    "plane_sphere_2x2000": ("plane_sphere_problem", dict(seed=1334)),
+    "window_10x50000": ("window_problem", dict(seed=1534, window=10)),
+    "mapping_64x100000": ("mapping_problem", dict(seed=1734)),
+}
+
+
+def workload(name=None):
     import scenes
-    return scenes.config_problem(2)
+    gen, kw = WORKLOADS[name or WORKLOAD]
+    return getattr(scenes, gen)(**kw)
 
 
 # ------------------------------------------------------------------ oracle --
@@ -180,7 +190,7 @@ def ours(args, rank, world, local_rank):
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     pk.load()
-    prob = workload()
+    prob = workload(args.workload)
     K = len(prob["xyz"])
     sem_dim = prob["sem"][0].shape[1]
     n_points = np.array([len(x) for x in prob["xyz"]], np.int64)
@@ -189,15 +199,18 @@ def ours(args, rank, world, local_rank):
     poses0 = np.ascontiguousarray(prob["poses0"].reshape(K * 16))
     edges = np.asarray(prob["edges"], np.int32)
     P = prob["params"]
-    params = pk.make_params(P["ell"], P["cutoff_mult"], P["sigma"], 0.0, sem_dim, 0,
-                            max_iters=1000)
+    color = prob.get("rgb") is not None and P.get("ell_color", 0.0) > 0
+    rgb_h = np.ascontiguousarray(np.concatenate(prob["rgb"]).astype(np.float32)) if color else None
+    params = pk.make_params(P["ell"], P["cutoff_mult"], P["sigma"], P.get("ell_color", 0.0), sem_dim,
+                            P.get("sem_bf16", 0), max_iters=1000)
     stream = torch.cuda.Stream(device=dev)
     xyz_d = torch.from_numpy(xyz_h).to(dev)
     sem_d = torch.from_numpy(sem_h).to(dev)
+    rgb_d = torch.from_numpy(rgb_h).to(dev) if color else None
     poses_d = torch.from_numpy(poses0).to(dev)
     torch.cuda.synchronize()
-    ctx = pk.rkhsba_create_device(n_points, xyz_d.data_ptr(), sem_d.data_ptr(), None, edges, params,
-                                  stream.cuda_stream)
+    ctx = pk.rkhsba_create_device(n_points, xyz_d.data_ptr(), sem_d.data_ptr(),
+                                  rgb_d.data_ptr() if color else None, edges, params, stream.cuda_stream)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
 
     def step():
@@ -246,7 +259,7 @@ def ours(args, rank, world, local_rank):
 
     # roofline of the dominant kernel (the pair kernel): FP32 arithmetic
     pair_ms, pair_n = prof["pairs"]
-    fl = flops_per_pair(sem_dim, False)
+    fl = flops_per_pair(sem_dim, color)
     achieved = pairs_per_step * args.steps * fl / (pair_ms / 1e3) / 1e12 if pair_ms > 0 else None
     props = torch.cuda.get_device_properties(dev)
     sm_max = (clk or {}).get("sm_max_mhz") or 2070.0
@@ -268,15 +281,19 @@ def ours(args, rank, world, local_rank):
         pos_p = torch.empty(poses0.shape, dtype=torch.float64, pin_memory=True).numpy()
         xyz_p[:] = xyz_h
         sem_p[:] = sem_h
-        params1 = pk.make_params(P["ell"], P["cutoff_mult"], P["sigma"], 0.0, sem_dim, 0,
-                                 max_iters=1)
+        params1 = pk.make_params(P["ell"], P["cutoff_mult"], P["sigma"], P.get("ell_color", 0.0),
+                                 sem_dim, P.get("sem_bf16", 0), max_iters=1)
+        rgb_p = None
+        if color:
+            rgb_p = torch.empty(rgb_h.shape, dtype=torch.float32, pin_memory=True).numpy()
+            rgb_p[:] = rgb_h
         n_e2e = max(3, min(args.steps, 20))
         e2e_pairs, e2e_s = 0, 0.0
         for k in range(n_e2e + 2):
             pos_p[:] = poses0
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            c2 = rb.rkhsba_create_flat(n_points, xyz_p, sem_p, None, edges, params1,
+            c2 = rb.rkhsba_create_flat(n_points, xyz_p, sem_p, rgb_p, edges, params1,
                                        stream.cuda_stream)
             T, info = rb.rkhsba_solve(c2, pos_p, K)
             rb.rkhsba_destroy(c2)
@@ -284,24 +301,143 @@ def ours(args, rank, world, local_rank):
             if k >= 2:
                 e2e_pairs += info["pair_terms"]
                 e2e_s += dt
-        h2d = xyz_h.nbytes + sem_h.nbytes + poses0.nbytes + edges.nbytes + n_points.nbytes
+        h2d = (xyz_h.nbytes + sem_h.nbytes + (rgb_h.nbytes if color else 0) + poses0.nbytes +
+               edges.nbytes + n_points.nbytes)
         e2e = dict(value=e2e_pairs / e2e_s, unit=UNIT, h2d_bytes_per_step=int(h2d),
                    d2h_bytes_per_step=int(poses0.nbytes + 64), steps=n_e2e,
                    step="create (H2D + grids) + solve with max_iters 1 + destroy")
+
+    serve = None
+    if rank == 0 and world == 1 and not args.no_serving and args.workload == WORKLOAD:
+        serve = serving(pk)
 
     if rank == 0:
         line = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps,
                     warmup=args.warmup, ms_per_step=ms_max / args.steps, higher_is_better=True,
                     scaling="weak", vs_baseline=None, dtype="f32", data="synthetic",
-                    config=dict(workload=WORKLOAD, frames=K, points=int(n_points.sum()),
+                    config=dict(workload=args.workload, frames=K, points=int(n_points.sum()),
                                 edges=len(edges), sem_dim=sem_dim, ell=P["ell"],
                                 pair_terms_per_step=int(pairs_per_step),
                                 l2="256 MiB buffer written between steps, outside the timed events",
                                 step="grid build + evaluation + one LM iteration (2 evaluations)",
                                 parallelism="replicas" if world > 1 else "single GPU"),
                     roofline=roofline, cpu_baseline=cpu_base, e2e=e2e, gpu_launches=int(n_launch),
-                    clocks=clk)
+                    clocks=clk, serving=serve)
         print(json.dumps(line), flush=True)
+
+
+def serving(pk, seed=1634, n_requests=200, pool_size=8, max_iters=30, load_factor=0.8):
+    """Served BA solves: a Poisson stream of requests (2-10 frames x 5k-100k
+    LiDAR points, log-uniform, 19-class labels) at load_factor x the measured
+    single-stream capacity.  Served form: the request server (continuous
+    batching, BF16 labels on the device).  Plain form: one request at a time
+    through rkhsba_create + rkhsba_solve with FP32 labels.  Requests are drawn
+    from a pool of pool_size generated problems (generation of 200 distinct
+    LiDAR problems would dominate the run)."""
+    import threading
+
+    import scenes
+    specs = scenes.request_stream(seed=seed, n_requests=n_requests)
+    pool = []
+    for sp in specs[:pool_size]:
+        p = scenes.lidar_street_problem(seed=sp["seed"], n_frames=sp["n_frames"],
+                                        n_points=sp["n_points"], sem_bf16=1)
+        p["params"] = dict(p["params"], max_iters=max_iters)
+        pool.append(p)
+    rng = np.random.default_rng(seed)
+    order = [i % pool_size for i in range(n_requests)]
+
+    def plain_solve(p):
+        g = pk.Problem.from_scene(p, sem_bf16=0)
+        try:
+            return g.solve(p["poses0"])
+        finally:
+            g.close()
+
+    # single-stream capacity from the plain form on every pool problem
+    plain_solve(pool[0])
+    svc = []
+    for p in pool:
+        t0 = time.perf_counter()
+        plain_solve(p)
+        svc.append(time.perf_counter() - t0)
+    mean_svc = sum(svc[order[i]] for i in range(n_requests)) / n_requests
+    rate = load_factor / mean_svc
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, size=n_requests))
+
+    def pct(x, q):
+        return float(np.percentile(np.asarray(x), q))
+
+    # served form
+    srv = pk.Server(max_inflight=8)
+    lat, done_t = [None] * n_requests, [None] * n_requests
+    tickets = [None] * n_requests
+    ready = threading.Event()
+    fail = []
+
+    def poller():
+        ready.wait()
+        for i in range(n_requests):
+            while tickets[i] is None:
+                time.sleep(0.0002)
+            r = srv.poll(tickets[i], timeout_ms=-1)
+            done_t[i] = time.perf_counter()
+            lat[i] = r[1]["latency_ms"]
+            if r[1]["state"] != "finished":
+                fail.append(r[1])
+
+    th = threading.Thread(target=poller)
+    th.start()
+    t0 = time.perf_counter()
+    ready.set()
+    for i in range(n_requests):
+        dt = t0 + arrivals[i] - time.perf_counter()
+        if dt > 0:
+            time.sleep(dt)
+        tickets[i] = srv.submit(pool[order[i]])
+    th.join()
+    srv.close()
+    served_wall = max(done_t) - t0
+    served = dict(solves_per_s=n_requests / served_wall, p50_ms=pct(lat, 50), p99_ms=pct(lat, 99),
+                  failed=len(fail))
+
+    # plain form: FIFO, one request at a time
+    lat2 = []
+    t0 = time.perf_counter()
+    free_at = t0
+    for i in range(n_requests):
+        arr = t0 + arrivals[i]
+        now = time.perf_counter()
+        if now < arr:
+            time.sleep(arr - now)
+        plain_solve(pool[order[i]])
+        fin = time.perf_counter()
+        lat2.append(1e3 * (fin - arr))
+        free_at = fin
+    plain_wall = free_at - t0
+    plain = dict(solves_per_s=n_requests / plain_wall, p50_ms=pct(lat2, 50), p99_ms=pct(lat2, 99))
+
+    # capacity: every request queued at once (served) / back to back (plain)
+    srv = pk.Server(max_inflight=8)
+    t0 = time.perf_counter()
+    tk = [srv.submit(pool[order[i]]) for i in range(n_requests)]
+    for t in tk:
+        srv.poll(t, timeout_ms=-1)
+    cap_served = n_requests / (time.perf_counter() - t0)
+    srv.close()
+    t0 = time.perf_counter()
+    for i in range(n_requests):
+        plain_solve(pool[order[i]])
+    cap_plain = n_requests / (time.perf_counter() - t0)
+    served["capacity_solves_per_s"] = cap_served
+    plain["capacity_solves_per_s"] = cap_plain
+    return dict(metric="served BA solves/s, p50/p99 latency", requests=n_requests, pool=pool_size,
+                arrival_rate_per_s=rate, load_factor=load_factor, max_iters=max_iters,
+                mean_single_stream_service_ms=1e3 * mean_svc,
+                pool_sizes=[[len(p["xyz"]), int(sum(len(x) for x in p["xyz"]))] for p in pool],
+                served=served, plain_fp32_single=plain,
+                note="solves_per_s and latencies under Poisson arrivals at load_factor x the plain "
+                     "single-stream capacity; capacity_solves_per_s with every request queued at once")
 
 
 def main():
@@ -312,6 +448,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--workload", default=WORKLOAD, choices=sorted(WORKLOADS),
+                    help="other workloads of the paper's shapes (the driver uses the default)")
     ap.add_argument("--oracle-sample", default=None)
     args = ap.parse_args()
     if args.oracle_sample:

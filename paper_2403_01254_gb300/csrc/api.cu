@@ -10,6 +10,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <mutex>
 #include <cstdio>
 #include <cstring>
 #include <set>
@@ -140,9 +141,11 @@ struct rkhsba_ctx {
     }
 
     ~rkhsba_ctx() {
+        // stream-ordered frees: no device-wide synchronisation, so contexts
+        // ending while others run (the request server) do not stall them
+        for (auto& b : bufs) cudaFreeAsync(b.p, stream);
         if (stream) cudaStreamSynchronize(stream);
         for (auto e : ev_pool) cudaEventDestroy(e);
-        for (auto& b : bufs) cudaFree(b.p);
         if (own_stream && stream) cudaStreamDestroy(stream);
     }
 };
@@ -173,7 +176,7 @@ rkhsba_status alloc(rkhsba_ctx* ctx, T** out, long long count) {
     size_t bytes = (size_t)std::max<long long>(count, 1) * sizeof(T);
     bytes = (bytes + 255) & ~(size_t)255;
     void* p = nullptr;
-    cudaError_t e = cudaMalloc(&p, bytes);
+    cudaError_t e = cudaMallocAsync(&p, bytes, ctx->stream);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return fail(ctx, RKHSBA_ENOMEM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed: " +
@@ -295,6 +298,20 @@ double bound_exp_scale(double bound, float* scale) {
     return std::ldexp(1.0, -e);
 }
 
+// Freed context memory stays in the device's default pool for the next
+// context instead of going back to the driver (set once per device).
+void keep_pool_warm(int dev) {
+    static std::once_flag flags[64];
+    if (dev < 0 || dev >= 64) return;
+    std::call_once(flags[dev], [dev] {
+        cudaMemPool_t pool;
+        if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+            unsigned long long thr = ~0ULL;
+            cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+        }
+    });
+}
+
 rkhsba_status build(rkhsba_ctx* c, const double* xyz, const float* sem, const float* rgb, bool on_device,
                     void* stream) {
     const long long N = c->N;
@@ -302,6 +319,7 @@ rkhsba_status build(rkhsba_ctx* c, const double* xyz, const float* sem, const fl
     int dev = 0;
     RK_CUDA(c, cudaGetDevice(&dev));
     RK_CUDA(c, cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, dev));
+    keep_pool_warm(dev);
     if (stream) {
         c->stream = (cudaStream_t)stream;
     } else {
