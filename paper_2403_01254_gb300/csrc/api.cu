@@ -10,6 +10,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <mutex>
 #include <cstdio>
 #include <cstring>
@@ -20,6 +21,7 @@
 
 namespace rk {
 std::atomic<long long> g_launches{0};
+thread_local long long t_launches = 0;
 }
 
 using namespace rk;
@@ -108,6 +110,9 @@ struct rkhsba_ctx {
     LMState* d_state = nullptr;
     double* d_lm_ws = nullptr;
     bool need_initial = true;
+    cudaGraphExec_t iter_graph = nullptr;   // one LM iteration, replayed
+    bool use_graph = true;
+    long long iter_launches = 0;            // kernels in one iteration
 
     // phase profiler (CUDA events on the context stream)
     static constexpr int NPH = 5;
@@ -146,6 +151,7 @@ struct rkhsba_ctx {
         for (auto& b : bufs) cudaFreeAsync(b.p, stream);
         if (stream) cudaStreamSynchronize(stream);
         for (auto e : ev_pool) cudaEventDestroy(e);
+        if (iter_graph) cudaGraphExecDestroy(iter_graph);
         if (own_stream && stream) cudaStreamDestroy(stream);
     }
 };
@@ -320,6 +326,7 @@ rkhsba_status build(rkhsba_ctx* c, const double* xyz, const float* sem, const fl
     RK_CUDA(c, cudaGetDevice(&dev));
     RK_CUDA(c, cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, dev));
     keep_pool_warm(dev);
+    if (const char* ng = std::getenv("RKHSBA_NO_GRAPHS")) c->use_graph = ng[0] == '0';
     if (stream) {
         c->stream = (cudaStream_t)stream;
     } else {
@@ -617,6 +624,45 @@ void lm_iteration(rkhsba_ctx* c) {
     c->phase_end();
 }
 
+// n LM iterations.  After the first evaluation has run (kernel attributes and
+// occupancy are then settled), one iteration is captured into a CUDA graph
+// and replayed, which removes the per-kernel launch cost of the ~30 small
+// launches of an iteration.  With the phase profiler on, or when capture is
+// not possible, the iterations are launched one kernel at a time.
+void lm_iterate(rkhsba_ctx* c, int n) {
+    if (n <= 0) return;
+    if (c->prof || !c->use_graph) {
+        for (int i = 0; i < n; ++i) lm_iteration(c);
+        return;
+    }
+    if (!c->iter_graph) {
+        cudaGraph_t g = nullptr;
+        const long long before = t_launches;
+        bool ok = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+        if (ok) {
+            lm_iteration(c);
+            ok = cudaStreamEndCapture(c->stream, &g) == cudaSuccess && g != nullptr;
+        }
+        if (ok) ok = cudaGraphInstantiate(&c->iter_graph, g, 0) == cudaSuccess;
+        if (g) cudaGraphDestroy(g);
+        const long long kernels = t_launches - before;   // captured, not run
+        g_launches.fetch_sub(kernels);
+        t_launches = before;
+        if (!ok) {
+            cudaGetLastError();
+            c->iter_graph = nullptr;
+            c->use_graph = false;
+            for (int i = 0; i < n; ++i) lm_iteration(c);
+            return;
+        }
+        c->iter_launches = kernels;
+    }
+    for (int i = 0; i < n; ++i) {
+        cudaGraphLaunch(c->iter_graph, c->stream);
+        count_launch(c->iter_launches);
+    }
+}
+
 rkhsba_status create_impl(rkhsba_ctx** out, int32_t n_frames, const int64_t* n_points,
                           const double* xyz, const float* sem, const float* rgb, int32_t n_edges,
                           const int32_t* edges, const rkhsba_params* params, void* stream,
@@ -651,9 +697,7 @@ rkhsba_status ctx_begin_solve(rkhsba_ctx* c, const double* host_poses) {
     RK_CUDA(c, cudaGetLastError());
     return RKHSBA_OK;
 }
-void ctx_iterate(rkhsba_ctx* c, int n) {
-    for (int i = 0; i < n; ++i) lm_iteration(c);
-}
+void ctx_iterate(rkhsba_ctx* c, int n) { lm_iterate(c, n); }
 cudaStream_t ctx_stream(const rkhsba_ctx* c) { return c->stream; }
 const void* ctx_state_dev(const rkhsba_ctx* c) { return c->d_state; }
 const double* ctx_poses_dev(const rkhsba_ctx* c) { return c->d_poses_cur; }
@@ -738,7 +782,7 @@ rkhsba_status rkhsba_rebuild(rkhsba_ctx* c) {
 rkhsba_status rkhsba_iterate(rkhsba_ctx* c, int32_t n_iters) {
     if (!c) return fail(nullptr, RKHSBA_EINVAL, "ctx is NULL");
     if (c->need_initial) lm_initial(c);
-    for (int i = 0; i < n_iters; ++i) lm_iteration(c);
+    lm_iterate(c, n_iters);
     RK_CUDA(c, cudaGetLastError());
     return RKHSBA_OK;
 }
@@ -775,7 +819,7 @@ rkhsba_status rkhsba_solve(rkhsba_ctx* c, double* poses, rkhsba_solve_info* info
     int issued = 0;
     while (issued < c->p.max_iters) {
         const int chunk = std::min(4, c->p.max_iters - issued);
-        for (int i = 0; i < chunk; ++i) lm_iteration(c);
+        lm_iterate(c, chunk);
         issued += chunk;
         RK_CUDA(c, cudaMemcpyAsync(&s, c->d_state, sizeof(LMState), cudaMemcpyDeviceToHost, c->stream));
         RK_CUDA(c, cudaStreamSynchronize(c->stream));

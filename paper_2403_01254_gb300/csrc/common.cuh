@@ -22,8 +22,12 @@
 
 namespace rk {
 
-extern std::atomic<long long> g_launches;
-inline void count_launch(long long n = 1) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+extern std::atomic<long long> g_launches;      // kernels launched by the library (process)
+extern thread_local long long t_launches;      // the same, counted per host thread
+inline void count_launch(long long n = 1) {
+    g_launches.fetch_add(n, std::memory_order_relaxed);
+    t_launches += n;
+}
 
 constexpr int MAX_SEM = 32;     // label floats per point
 constexpr int ACC_N = 32;       // int64 accumulator slots per edge

@@ -433,8 +433,15 @@ void launch_lm_solve(int K, const double* H_cur, const double* b_cur, const doub
     const int n = 6 * (K - 1);
     // factor A (n x n), right-hand side y (n) and pivot reciprocals rinv (n)
     size_t smem = (n <= LM_SMEM_N) ? (size_t)(n * n + 2 * n) * sizeof(double) : 0;
-    if (smem > 48 * 1024)
-        cudaFuncSetAttribute(k_lm_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    // opt in once to the largest factor kept in shared memory (not a stream
+    // operation, so it must not happen while an iteration is being captured;
+    // the first call of any context runs before capture)
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaFuncSetAttribute(k_lm_solve, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)((size_t)(LM_SMEM_N * LM_SMEM_N + 2 * LM_SMEM_N) * sizeof(double)));
+        attr_set = true;
+    }
     k_lm_solve<<<1, LM_T, smem, st>>>(K, H_cur, b_cur, poses_cur, poses_cand, st_dev, ws);
     count_launch();
 }
