@@ -28,6 +28,13 @@ Readings of points the paper leaves open (each also listed in the design doc):
     b = sum w J^T d;  H = sum w J^T J (Gauss-Newton matrix of the IRLS cost),
     with d = T_a x_i - T_b y_j in world coordinates, J_a = R_a [I | -[x_i]x],
     J_b = -R_b [I | -[y_j]x]  (rho first, then phi, per the wedge).
+  * RKHS distance |f_a - f_b|^2 = <f_a,f_a> + <f_b,f_b> - 2 <f_a,f_b> with the
+    same sparse sums (Eq. dist_rkhs); cosine <f_a,f_b> / (|f_a| |f_b|).
+  * Lengthscale decay (Sec. V-C): ell <- ell (1 + decay sign(dD/dell)) after
+    each inner solve; stop when an inner solve accepts no step.
+  * Rotation search (Sec. IV-A): candidate k places frame b at
+    T_a [R_k | mu_a - R_k mu_b] (frame centroids aligned; the paper leaves the
+    translation of a candidate open) and scores it by the cosine.
   * LM step (H_ff + lambda * Dm) delta = -b_f over every frame but frame 0,
     Dm = diag(max(H_ii, 1e-9 * max_k H_kk)); accept when F increases
     (lambda /= 10), otherwise lambda *= 10.  Stop when an accepted step has
@@ -45,7 +52,8 @@ from scipy.spatial import cKDTree
 __all__ = [
     "DEFAULTS", "hat", "wedge", "se3_exp", "se3_log", "pose_error",
     "label_weights", "pairs_bruteforce", "pairs_kdtree", "edge_terms",
-    "evaluate", "lm_solve", "irls_frozen_solve", "edge_pairs",
+    "evaluate", "lm_solve", "irls_frozen_solve", "edge_pairs", "inner_product", "self_inner",
+    "distance_and_cosine", "ell_decay_solve", "icosahedral_rotations", "rotation_search",
 ]
 
 DEFAULTS = dict(ell=0.1, cutoff_mult=3.0, sigma=1.0, ell_color=0.0, sem_bf16=0,
@@ -402,3 +410,149 @@ def irls_frozen_solve(xa, xb, i, j, w, Ta, Tb, iters=50, lam=0.0):
             break
     del Ra
     return Tb
+
+
+# ---------------------------------------------------------------------------
+# inner products, RKHS distance and cosine (Sec. III-A, Eq. dist_rkhs)
+# ---------------------------------------------------------------------------
+def inner_product(xa, xb, Ta, Tb, sem_a=None, sem_b=None, rgb_a=None, rgb_b=None, params=None):
+    """<f_{T_a X_a}, f_{T_b X_b}> over the pairs inside the cutoff (Eq. double_sum)."""
+    return edge_terms(xa, xb, Ta, Tb, sem_a, sem_b, rgb_a, rgb_b, params)["F"]
+
+
+def self_inner(x, sem=None, rgb=None, params=None):
+    """<f_X, f_X>: the double sum of a frame with itself (pose invariant)."""
+    I = np.eye(4)
+    return inner_product(x, x, I, I, sem, sem, rgb, rgb, params)
+
+
+def distance_and_cosine(problem, poses, params=None):
+    """Per edge: RKHS distance |f_a - f_b|^2 = <f_a,f_a> + <f_b,f_b> - 2<f_a,f_b>
+    (Eq. dist_rkhs) and the cosine <f_a,f_b> / (|f_a| |f_b|); the self terms;
+    and d(sum of the edge distances)/d ell.  Each inner product is
+    sigma^2 sum c k with k = exp(-|d|^2 / 2 ell^2), so its derivative in ell
+    is sigma^2 / ell^3 sum c k |d|^2 (the moving cutoff is not differentiated)."""
+    P = _params(problem["params"])
+    if params:
+        P.update(params)
+    K = len(problem["xyz"])
+    I = np.eye(4)
+    s_terms = []
+    for m in range(K):
+        x, s, c = _frame_inputs(problem, m)
+        s_terms.append(edge_terms(x, x, I, I, s, s, c, c, P))
+    selfs = np.array([t["F"] for t in s_terms])
+    self_E = np.array([t["E"] for t in s_terms])
+    dist, cos, cross, cross_E = [], [], [], []
+    for a, b in np.asarray(problem["edges"]).reshape(-1, 2):
+        a, b = int(a), int(b)
+        xa, sa, ca = _frame_inputs(problem, a)
+        xb, sb, cb = _frame_inputs(problem, b)
+        t = edge_terms(xa, xb, poses[a], poses[b], sa, sb, ca, cb, P)
+        cross.append(t["F"])
+        cross_E.append(t["E"])
+        dist.append(selfs[a] + selfs[b] - 2.0 * t["F"])
+        cos.append(t["F"] / math.sqrt(selfs[a] * selfs[b]) if selfs[a] > 0 and selfs[b] > 0 else 0.0)
+    sig2, ell = P["sigma"] ** 2, P["ell"]
+    dE = sum(self_E[int(a)] + self_E[int(b)] for a, b in np.asarray(problem["edges"]).reshape(-1, 2))
+    dD_dell = sig2 / ell ** 3 * (dE - 2.0 * float(np.sum(cross_E)))
+    return dict(self=selfs, cross=np.array(cross), dist=np.array(dist), cos=np.array(cos),
+                self_E=self_E, cross_E=np.array(cross_E), dD_dell=dD_dell)
+
+
+def ell_decay_solve(problem, poses0=None, params=None, decay=0.1, ell_min=0.0, max_outer=10):
+    """Inner-outer loop of Sec. V-C.  Inner: the LM pose solve at fixed ell.
+    Outer: ell <- ell (1 + decay * sign(dD/dell)), D the summed edge distance
+    of Eq. dist_rkhs at the solved poses, floored at ell_min.  The loop ends
+    when an inner solve accepts no step (the original objective stops
+    increasing), when ell stops changing, or after max_outer levels."""
+    P = _params(problem["params"])
+    if params:
+        P.update(params)
+    T = np.array(problem["poses0"] if poses0 is None else poses0, dtype=np.float64)
+    ell = P["ell"]
+    levels = []
+    for _ in range(max_outer):
+        Q = dict(P, ell=ell)
+        r = lm_solve(problem, T, params=Q)
+        T = r["poses"]
+        g = distance_and_cosine(problem, T, params=Q)["dD_dell"]
+        accepted = len(r["history"]) - 1
+        levels.append(dict(ell=ell, F=r["F"], iters=r["iters"], accepted=accepted, dD_dell=g))
+        if accepted == 0:
+            break
+        nxt = max(ell * (1.0 + decay * float(np.sign(g))), ell_min)
+        if nxt == ell:
+            break
+        ell = nxt
+    return dict(poses=T, ell=ell, levels=levels)
+
+
+# ---------------------------------------------------------------------------
+# icosahedral rotation search (Sec. IV-A)
+# ---------------------------------------------------------------------------
+def _axis_rotation(axis, angle):
+    axis = np.asarray(axis, np.float64) / np.linalg.norm(axis)
+    return se3_exp(np.concatenate([np.zeros(3), angle * axis]))[:3, :3]
+
+
+def icosahedral_rotations():
+    """The 60 rotations of the icosahedron's symmetry group, built as the
+    paper lists them: the identity; a half turn about each of the 15 axes
+    through midpoints of opposite edges; turns of 2pi/3 and 4pi/3 about each
+    of the 10 axes through centres of opposite faces; turns of 2k pi/5,
+    k = 1..4, about each of the 6 axes through opposite vertices."""
+    phi = (1.0 + math.sqrt(5.0)) / 2.0
+    V = []
+    for s1 in (-1.0, 1.0):
+        for s2 in (-1.0, 1.0):
+            V += [(0.0, s1, s2 * phi), (s1, s2 * phi, 0.0), (s2 * phi, 0.0, s1)]
+    V = np.array(V)
+    edge_len = min(np.linalg.norm(V[i] - V[j]) for i in range(12) for j in range(i + 1, 12))
+    edges = [(i, j) for i in range(12) for j in range(i + 1, 12)
+             if abs(np.linalg.norm(V[i] - V[j]) - edge_len) < 1e-9]
+    faces = [(i, j, k) for (i, j) in edges for k in range(j + 1, 12)
+             if (i, k) in edges and (j, k) in edges]
+
+    def half(dirs):
+        out = []
+        for d in dirs:
+            d = d / np.linalg.norm(d)
+            if not any(abs(abs(d @ e) - 1.0) < 1e-9 for e in out):
+                out.append(d)
+        return out
+
+    v_axes = half(list(V))
+    e_axes = half([V[i] + V[j] for i, j in edges])
+    f_axes = half([V[i] + V[j] + V[k] for i, j, k in faces])
+    R = [np.eye(3)]
+    R += [_axis_rotation(a, math.pi) for a in e_axes]
+    R += [_axis_rotation(a, t * 2 * math.pi / 3) for a in f_axes for t in (1, 2)]
+    R += [_axis_rotation(a, t * 2 * math.pi / 5) for a in v_axes for t in (1, 2, 3, 4)]
+    return np.array(R)
+
+
+def rotation_search(problem, a, b, poses, params=None):
+    """Score the 60 candidate rotations of frame b against frame a: candidate k
+    places b at T_a [R_k | mu_a - R_k mu_b] (centroids aligned); the score is
+    the cosine of Sec. IV-A.  Returns (cosines [60], best pose of b)."""
+    P = _params(problem["params"])
+    if params:
+        P.update(params)
+    xa, sa, ca = _frame_inputs(problem, a)
+    xb, sb, cb = _frame_inputs(problem, b)
+    xa = np.asarray(xa, np.float64)
+    xb = np.asarray(xb, np.float64)
+    Sa = self_inner(xa, sa, ca, P)
+    Sb = self_inner(xb, sb, cb, P)
+    mua, mub = xa.mean(0), xb.mean(0)
+    cos = np.zeros(60)
+    cands = []
+    for k, Rk in enumerate(icosahedral_rotations()):
+        C = np.eye(4)
+        C[:3, :3] = Rk
+        C[:3, 3] = mua - Rk @ mub
+        Tb = poses[a] @ C
+        cands.append(Tb)
+        cos[k] = inner_product(xa, xb, poses[a], Tb, sa, sb, ca, cb, P) / math.sqrt(Sa * Sb)
+    return cos, cands[int(np.argmax(cos))]
