@@ -226,6 +226,79 @@ rkhsba_status rkhsba_eval_static(int32_t n_frames, const int64_t* n_points, cons
                                  void* cuda_stream);
 
 /* ------------------------------------------------------------------------
+ * Function-space distance and cosine (Sec. III-A, Eq. dist_rkhs).
+ *
+ * A frame X_m is the function f_{T X}(.) = sum_i l(x_i) k(., T x_i) in the
+ * RKHS of the kernel; two frames compare through
+ *   <f_a, f_b>     = sigma^2 sum_{i,j} c_ij exp(-|T_a x_i - T_b y_j|^2 / 2 ell^2)
+ *   |f_a - f_b|^2  = <f_a, f_a> + <f_b, f_b> - 2 <f_a, f_b>
+ *   cos(f_a, f_b)  = <f_a, f_b> / (|f_a| |f_b|)
+ * with the same sparse sums (pairs closer than r_c) and labels as the
+ * objective.  At host poses [K*16] this writes, each output HOST and
+ * caller-allocated and each may be NULL:
+ *   self_ip [K]  <f_m, f_m> (pose invariant; i = j terms included)
+ *   cross_ip[E]  <f_a, f_b> for edge e = (a, b), the objective's per-edge F
+ *   dist    [E]  |f_a - f_b|^2
+ *   cosine  [E]  cos(f_a, f_b); 0 when a frame has a zero self term
+ *   dD_dell [1]  d (sum_e dist[e]) / d ell = sigma^2 / ell^3 * sum c k |d|^2
+ *                over the same terms (the cutoff held fixed)
+ * The self terms are evaluated on the first call (a second, self-edge
+ * context kept with ctx) and reused.  Synchronous.
+ * ------------------------------------------------------------------------ */
+rkhsba_status rkhsba_inner_products(rkhsba_ctx* ctx, const double* poses, double* self_ip,
+                                    double* cross_ip, double* dist, double* cosine, double* dD_dell);
+
+/* Rotation search of Sec. IV-A: frame b is tried against frame a under the
+ * 60 rotations R_k of the icosahedral group (the identity; half turns about
+ * the 15 axes through opposite edge midpoints; 2pi/3, 4pi/3 about the 10
+ * axes through opposite face centres; 2k pi/5, k = 1..4, about the 6 axes
+ * through opposite vertices; icosahedron with vertices at the cyclic
+ * permutations of (0, +-1, +-phi)).  Candidate k places b at
+ *   T_a [R_k | mu_a - R_k mu_b]      (mu = frame-local centroid)
+ * and is scored by cos(f_a, f_b); the best candidate has the largest cosine
+ * (lowest k on ties).  All 60 candidates are one batched evaluation.
+ *   a, b         frames (a != b, both non-empty)
+ *   poses        [K*16] HOST; only T_a is read
+ *   cosine       [60] HOST out (may be NULL)
+ *   rotations    [60*9] HOST out, row-major R_k (may be NULL)
+ *   best_pose    [16] HOST out: the pose of b of the best candidate (may be NULL)
+ *   best         HOST out: its index k (may be NULL)
+ * Device memory: a temporary context with 1 + 60 copies of frame b. */
+rkhsba_status rkhsba_rotation_search(rkhsba_ctx* ctx, int32_t a, int32_t b, const double* poses,
+                                     double* cosine, double* rotations, double* best_pose,
+                                     int32_t* best);
+
+/* Lengthscale decay (Sec. V-C): an outer loop over ell around the LM solve.
+ * Level t solves the poses at ell_t (rkhsba_solve's loop, from the previous
+ * level's poses), then sets
+ *   ell_{t+1} = max(ell_min, ell_t (1 + decay * sign(dD/dell)))
+ * with dD/dell as in rkhsba_inner_products at the solved poses.  The loop ends
+ * when a level accepts no LM step (the objective at that ell stopped
+ * increasing), when ell stops changing, or after max_outer levels.  ctx keeps
+ * its own ell; each level runs in a temporary context of the same problem. */
+typedef struct {
+    double decay;        /* fraction per outer step, in (0, 1) */
+    double ell_min;      /* floor of ell (>= 0) */
+    int32_t max_outer;   /* levels, >= 1 */
+    int32_t reserved;    /* must be 0 */
+} rkhsba_ell_schedule;
+
+typedef struct {
+    int32_t levels;      /* levels run */
+    int32_t status;      /* status of the last level's solve (OK or ENOTCONV) */
+    double ell_final;    /* ell of the last level */
+    double final_loss;   /* -F at the last level's ell and the returned poses */
+    int64_t iters;       /* LM iterations over all levels */
+    int64_t pair_terms;  /* pair-terms over all evaluations */
+} rkhsba_ell_info;
+
+/*   poses       [K*16] HOST in: initial poses; out: final poses
+ *   ell_levels  [max_outer] HOST out: ell of each level run (may be NULL)
+ *   dD_levels   [max_outer] HOST out: dD/dell after each level (may be NULL) */
+rkhsba_status rkhsba_solve_ell_decay(rkhsba_ctx* ctx, const rkhsba_ell_schedule* sched, double* poses,
+                                     double* ell_levels, double* dD_levels, rkhsba_ell_info* info);
+
+/* ------------------------------------------------------------------------
  * Request server: continuous batching of BA solves on one GPU.
  *
  * Requests (each a problem as for rkhsba_create plus initial poses) are

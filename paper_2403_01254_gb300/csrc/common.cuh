@@ -106,7 +106,8 @@ struct LMState {
     long long n_cand;         // pair-terms of the last evaluation
     int iters, max_iters;
     int done, status;         // status: 0 converged, 4 not converged
-    int first, chol_fail, accepted, pad;
+    int first, chol_fail, accepted;
+    int n_accepted;           // accepted steps after the first evaluation
 };
 
 // ------------------------------------------------------------ launchers ----

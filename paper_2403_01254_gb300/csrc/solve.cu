@@ -384,6 +384,7 @@ __global__ void k_lm_accept(int K, LMState* S, const double* __restrict__ Fc,
                 const double rel = (F - S->F_cur) / fmax(fabs(S->F_cur), 1e-300);
                 acc = 1;
                 S->F_cur = F;
+                S->n_accepted += 1;
                 S->lambda = fmax(S->lambda * 0.1, 1e-12);
                 if (step < S->tol_step || rel < S->tol_rel_f) { S->done = 1; S->status = 0; }
             } else {

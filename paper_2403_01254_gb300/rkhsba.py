@@ -22,7 +22,8 @@ EXPORTS = [
     "rkhsba_set_poses_device", "rkhsba_rebuild", "rkhsba_iterate", "rkhsba_get_state",
     "rkhsba_edge_pairs", "rkhsba_info", "rkhsba_last_error", "rkhsba_launch_count",
     "rkhsba_profile", "rkhsba_server_create", "rkhsba_server_destroy", "rkhsba_submit",
-    "rkhsba_poll", "rkhsba_cancel", "rkhsba_server_stats",
+    "rkhsba_poll", "rkhsba_cancel", "rkhsba_server_stats", "rkhsba_inner_products",
+    "rkhsba_rotation_search", "rkhsba_solve_ell_decay",
 ]
 
 
@@ -52,6 +53,16 @@ class ServerConfig(C.Structure):
 class RequestInfo(C.Structure):
     _fields_ = [("state", C.c_int32), ("status", C.c_int32), ("solve", SolveInfo),
                 ("queue_ms", C.c_double), ("latency_ms", C.c_double), ("device_bytes", C.c_int64)]
+
+
+class EllSchedule(C.Structure):
+    _fields_ = [("decay", C.c_double), ("ell_min", C.c_double), ("max_outer", C.c_int32),
+                ("reserved", C.c_int32)]
+
+
+class EllInfo(C.Structure):
+    _fields_ = [("levels", C.c_int32), ("status", C.c_int32), ("ell_final", C.c_double),
+                ("final_loss", C.c_double), ("iters", C.c_int64), ("pair_terms", C.c_int64)]
 
 
 REQUEST_STATES = {0: "queued", 1: "running", 2: "finished", 3: "failed", 4: "cancelled"}
@@ -102,6 +113,12 @@ def load(build_if_missing=True):
         "rkhsba_poll": [vp, C.c_int64, C.c_int32, P(C.c_double), P(RequestInfo)],
         "rkhsba_cancel": [vp, C.c_int64],
         "rkhsba_server_stats": [vp, P(C.c_int64), P(C.c_int64), P(C.c_int64), P(C.c_int64)],
+        "rkhsba_inner_products": [vp, P(C.c_double), P(C.c_double), P(C.c_double), P(C.c_double),
+                                  P(C.c_double), P(C.c_double)],
+        "rkhsba_rotation_search": [vp, C.c_int32, C.c_int32, P(C.c_double), P(C.c_double), P(C.c_double),
+                                   P(C.c_double), P(C.c_int32)],
+        "rkhsba_solve_ell_decay": [vp, P(EllSchedule), P(C.c_double), P(C.c_double), P(C.c_double),
+                                   P(EllInfo)],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -267,6 +284,43 @@ def rkhsba_profile(ctx, enable, read=False):
     return None
 
 
+def rkhsba_inner_products(ctx, poses, K, E):
+    """Self terms <f_m,f_m> [K], per-edge <f_a,f_b>, |f_a-f_b|^2 and cosine [E],
+    and d(sum dist)/d ell (Eq. dist_rkhs)."""
+    poses = np.ascontiguousarray(poses, dtype=np.float64).reshape(K * 16)
+    self_ip, cross, dist, cos, dD = np.zeros(K), np.zeros(E), np.zeros(E), np.zeros(E), np.zeros(1)
+    _check(load().rkhsba_inner_products(ctx, _ptr(poses, C.c_double), _ptr(self_ip, C.c_double),
+                                        _ptr(cross, C.c_double), _ptr(dist, C.c_double),
+                                        _ptr(cos, C.c_double), _ptr(dD, C.c_double)), ctx)
+    return dict(self=self_ip, cross=cross, dist=dist, cos=cos, dD_dell=float(dD[0]))
+
+
+def rkhsba_rotation_search(ctx, a, b, poses, K):
+    """Cosines of the 60 icosahedral candidates of frame b against frame a,
+    the rotations R_k [60,3,3], the best candidate's pose of b and its index."""
+    poses = np.ascontiguousarray(poses, dtype=np.float64).reshape(K * 16)
+    cos, rot, best_pose, best = np.zeros(60), np.zeros(540), np.zeros(16), C.c_int32()
+    _check(load().rkhsba_rotation_search(ctx, int(a), int(b), _ptr(poses, C.c_double), _ptr(cos, C.c_double),
+                                         _ptr(rot, C.c_double), _ptr(best_pose, C.c_double),
+                                         C.byref(best)), ctx)
+    return dict(cos=cos, rotations=rot.reshape(60, 3, 3), best_pose=best_pose.reshape(4, 4),
+                best=best.value)
+
+
+def rkhsba_solve_ell_decay(ctx, poses, K, decay=0.1, ell_min=0.0, max_outer=10):
+    """Lengthscale-decay outer loop around the LM solve (Sec. V-C)."""
+    T = np.ascontiguousarray(poses, dtype=np.float64).reshape(K * 16).copy()
+    sched = EllSchedule(float(decay), float(ell_min), int(max_outer), 0)
+    ells, dDs, info = np.zeros(max_outer), np.zeros(max_outer), EllInfo()
+    _check(load().rkhsba_solve_ell_decay(ctx, C.byref(sched), _ptr(T, C.c_double), _ptr(ells, C.c_double),
+                                         _ptr(dDs, C.c_double), C.byref(info)), ctx)
+    n = info.levels
+    return T.reshape(K, 4, 4), dict(levels=n, ell=ells[:n].copy(), dD_dell=dDs[:n].copy(),
+                                    status=STATUS_NAMES[info.status], ell_final=info.ell_final,
+                                    final_loss=info.final_loss, iters=int(info.iters),
+                                    pair_terms=int(info.pair_terms))
+
+
 def rkhsba_launch_count():
     return int(load().rkhsba_launch_count())
 
@@ -302,6 +356,15 @@ class Problem:
 
     def edge_pairs(self, poses, edge, capacity=1 << 24):
         return rkhsba_edge_pairs(self.ctx, poses, self.K, edge, capacity)
+
+    def inner_products(self, poses):
+        return rkhsba_inner_products(self.ctx, poses, self.K, self.E)
+
+    def rotation_search(self, a, b, poses):
+        return rkhsba_rotation_search(self.ctx, a, b, poses, self.K)
+
+    def solve_ell_decay(self, poses0, decay=0.1, ell_min=0.0, max_outer=10):
+        return rkhsba_solve_ell_decay(self.ctx, poses0, self.K, decay, ell_min, max_outer)
 
     def info(self):
         return rkhsba_info(self.ctx)

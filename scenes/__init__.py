@@ -175,6 +175,95 @@ def plane_sphere_problem(seed=1334, n=2000, noise=0.01, angle_deg=10.0, trans=0.
 
 
 # --------------------------------------------------------------------------
+# two scans of one asymmetric object under a large rotation (global
+# initialisation protocol of Sec. VI-A: 90 / 180 degrees about a random axis,
+# translation of length 0.5, normal-direction noise with outliers, cropping)
+# --------------------------------------------------------------------------
+def _sample_object(rng, n):
+    """Surface points, unit normals and part index of a body (ellipsoid), a
+    head (cube) and a tail (cylinder); the union has no symmetry."""
+    areas = np.array([0.86, 0.375, 0.226])
+    prim = rng.choice(3, size=n, p=areas / areas.sum())
+    pts = np.empty((n, 3))
+    nrm = np.empty((n, 3))
+    m = prim == 0                                     # ellipsoid, radii (0.4, 0.25, 0.15)
+    rad = np.array([0.4, 0.25, 0.15])
+    v = rng.normal(size=(m.sum(), 3))
+    v /= np.linalg.norm(v, axis=1, keepdims=True)
+    pts[m] = v * rad
+    g = v / rad
+    nrm[m] = g / np.linalg.norm(g, axis=1, keepdims=True)
+    m = prim == 1                                     # cube of side 0.25 at (0.45, 0.2, 0.12)
+    k = int(m.sum())
+    face = rng.integers(0, 6, size=k)
+    uv = rng.uniform(-0.125, 0.125, size=(k, 2))
+    ax = face // 2
+    sgn = np.where(face % 2 == 0, 1.0, -1.0)
+    q = np.zeros((k, 3))
+    e = np.zeros((k, 3))
+    for a in range(3):
+        sel = ax == a
+        o = [b for b in range(3) if b != a]
+        q[sel, a] = 0.125 * sgn[sel]
+        q[sel, o[0]] = uv[sel, 0]
+        q[sel, o[1]] = uv[sel, 1]
+        e[sel, a] = sgn[sel]
+    pts[m] = q + np.array([0.45, 0.2, 0.12])
+    nrm[m] = e
+    m = prim == 2                                     # cylinder r = 0.06, length 0.6
+    k = int(m.sum())
+    d = np.array([-1.0, 0.3, 0.5])
+    d /= np.linalg.norm(d)
+    u1 = np.cross(d, [0.0, 0.0, 1.0])
+    u1 /= np.linalg.norm(u1)
+    u2 = np.cross(d, u1)
+    th = rng.uniform(0, 2 * math.pi, size=k)
+    s = rng.uniform(0, 0.6, size=k)
+    radial = np.cos(th)[:, None] * u1 + np.sin(th)[:, None] * u2
+    pts[m] = np.array([-0.35, 0.0, 0.0]) + s[:, None] * d + 0.06 * radial
+    nrm[m] = radial
+    return pts, nrm, prim
+
+
+def _scan(rng, n, outlier_ratio, crop_ratio):
+    pts, nrm, prim = _sample_object(rng, n)
+    out = rng.uniform(size=n) < outlier_ratio
+    off = np.where(out, rng.uniform(-0.1, 0.1, size=n), rng.normal(scale=0.01, size=n))
+    pts = pts + off[:, None] * nrm
+    if crop_ratio > 0:
+        u = rng.normal(size=3)
+        u /= np.linalg.norm(u)
+        h = pts @ u
+        keep = h <= np.quantile(h, 1.0 - crop_ratio)
+        pts, prim = pts[keep], prim[keep]
+    return pts, prim
+
+
+def object_pair_problem(seed=1834, angle_deg=90.0, trans=0.5, n=2000, outlier_ratio=0.0, crop_ratio=0.0,
+                        ell=0.1, labels=False):
+    """Two independent noisy scans of the object; frame 1 under a rotation of
+    angle_deg about a random axis and a translation of length trans.  With
+    labels, each point carries a Dirichlet class vector peaked at its part
+    (body, head, tail): a pose-invariant descriptor standing in for the
+    per-point features of the label function."""
+    rng = np.random.default_rng(seed)
+    p0, l0 = _scan(rng, n, outlier_ratio, crop_ratio)
+    p1, l1 = _scan(rng, n, outlier_ratio, crop_ratio)
+    T1 = random_pose(rng, angle_deg, trans)
+    sem = [dirichlet_labels(rng, l0, 3), dirichlet_labels(rng, l1, 3)] if labels else None
+    return dict(
+        name="object_pair_%ddeg" % int(round(angle_deg)),
+        xyz=[p0, to_local(p1, T1)],
+        sem=sem,
+        rgb=None,
+        edges=np.array([[0, 1]], dtype=np.int32),
+        poses_gt=np.stack([np.eye(4), T1]),
+        poses0=np.stack([np.eye(4), np.eye(4)]),
+        params=dict(ell=ell, cutoff_mult=3.0, sigma=1.0, ell_color=0.0, sem_bf16=0),
+    )
+
+
+# --------------------------------------------------------------------------
 # LiDAR street scene (configs 2-5)
 # --------------------------------------------------------------------------
 def _street_primitives(rng, x_range=(-70.0, 70.0), half_width=8.0):
