@@ -209,76 +209,76 @@ __global__ void __launch_bounds__(256) k_units(const uint32_t* __restrict__ key,
 
 __device__ __forceinline__ long long to_fixed(float v, float scale) { return __float2ll_rn(v * scale); }
 
-__device__ __forceinline__ long long warp_sum_ll(long long v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
-    return v;
+// ---------------------------------------------------- paired FP32 ops ----
+// Two FP32 lanes in one 64-bit register: fma/mul/add .f32x2 issue one
+// instruction for two IEEE FP32 operations (each rounded as its scalar form).
+typedef unsigned long long u64;
+__device__ __forceinline__ u64 f2(float a, float b) {
+    u64 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ float2 f2_split(u64 v) {
+    float2 r;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(v));
+    return r;
+}
+__device__ __forceinline__ u64 ffma2(u64 a, u64 b, u64 c) {
+    u64 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ u64 fmul2(u64 a, u64 b) {
+    u64 d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ u64 fadd2(u64 a, u64 b) {
+    u64 d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
 }
 
 template <int DP, bool BF16>
 struct Sem;
 
 template <int DP>
-struct Sem<DP, false> {   // FP32 rows of DP floats
-    float q[DP > 0 ? DP : 1];
+struct Sem<DP, false> {   // FP32 label row of DP floats, as DP/2 pairs
+    u64 q2[DP > 0 ? DP / 2 : 1];
     __device__ __forceinline__ void load(const void* base, int s, bool valid) {
-        const float4* row = reinterpret_cast<const float4*>(base) + (size_t)s * (DP / 4);
+        const ulonglong2* row = reinterpret_cast<const ulonglong2*>(base) + (size_t)s * (DP / 4);
 #pragma unroll
         for (int k = 0; k < DP / 4; ++k) {
-            float4 v = valid ? __ldg(row + k) : make_float4(0.f, 0.f, 0.f, 0.f);
-            q[4 * k] = v.x; q[4 * k + 1] = v.y; q[4 * k + 2] = v.z; q[4 * k + 3] = v.w;
+            const ulonglong2 v = valid ? __ldg(row + k) : make_ulonglong2(0ull, 0ull);
+            q2[2 * k] = v.x;
+            q2[2 * k + 1] = v.y;
         }
-    }
-    __device__ __forceinline__ float dot(const void* base, int i) const {
-        if (DP == 0) return 1.f;
-        const float4* row = reinterpret_cast<const float4*>(base) + (size_t)i * (DP / 4);
-        float s0 = 0.f, s1 = 0.f;
-#pragma unroll
-        for (int k = 0; k < DP / 4; ++k) {
-            float4 v = __ldg(row + k);
-            s0 = fmaf(q[4 * k], v.x, s0);
-            s1 = fmaf(q[4 * k + 1], v.y, s1);
-            s0 = fmaf(q[4 * k + 2], v.z, s0);
-            s1 = fmaf(q[4 * k + 3], v.w, s1);
-        }
-        return s0 + s1;
     }
 };
 
 __device__ __forceinline__ float bf_lo(unsigned u) { return __uint_as_float(u << 16); }
 __device__ __forceinline__ float bf_hi(unsigned u) { return __uint_as_float(u & 0xffff0000u); }
+__device__ __forceinline__ u64 bf_pair(unsigned u) { return f2(bf_lo(u), bf_hi(u)); }
 
 template <int DP>
-struct Sem<DP, true> {    // BF16 rows of DP values (DP % 8 == 0), FP32 products
-    float q[DP];
+struct Sem<DP, true> {    // BF16 label row of DP values (DP % 8 == 0), widened to FP32 pairs
+    u64 q2[DP / 2];
     __device__ __forceinline__ void load(const void* base, int s, bool valid) {
         const uint4* row = reinterpret_cast<const uint4*>(base) + (size_t)s * (DP / 8);
 #pragma unroll
         for (int k = 0; k < DP / 8; ++k) {
-            uint4 v = valid ? __ldg(row + k) : make_uint4(0u, 0u, 0u, 0u);
-            q[8 * k + 0] = bf_lo(v.x); q[8 * k + 1] = bf_hi(v.x);
-            q[8 * k + 2] = bf_lo(v.y); q[8 * k + 3] = bf_hi(v.y);
-            q[8 * k + 4] = bf_lo(v.z); q[8 * k + 5] = bf_hi(v.z);
-            q[8 * k + 6] = bf_lo(v.w); q[8 * k + 7] = bf_hi(v.w);
+            const uint4 v = valid ? __ldg(row + k) : make_uint4(0u, 0u, 0u, 0u);
+            q2[4 * k + 0] = bf_pair(v.x);
+            q2[4 * k + 1] = bf_pair(v.y);
+            q2[4 * k + 2] = bf_pair(v.z);
+            q2[4 * k + 3] = bf_pair(v.w);
         }
-    }
-    __device__ __forceinline__ float dot(const void* base, int i) const {
-        const uint4* row = reinterpret_cast<const uint4*>(base) + (size_t)i * (DP / 8);
-        float s0 = 0.f, s1 = 0.f;
-#pragma unroll
-        for (int k = 0; k < DP / 8; ++k) {
-            uint4 v = __ldg(row + k);
-            s0 = fmaf(q[8 * k + 0], bf_lo(v.x), s0); s1 = fmaf(q[8 * k + 1], bf_hi(v.x), s1);
-            s0 = fmaf(q[8 * k + 2], bf_lo(v.y), s0); s1 = fmaf(q[8 * k + 3], bf_hi(v.y), s1);
-            s0 = fmaf(q[8 * k + 4], bf_lo(v.z), s0); s1 = fmaf(q[8 * k + 5], bf_hi(v.z), s1);
-            s0 = fmaf(q[8 * k + 6], bf_lo(v.w), s0); s1 = fmaf(q[8 * k + 7], bf_hi(v.w), s1);
-        }
-        return s0 + s1;
     }
 };
 
 // Label rows staged in shared memory (FP32 or BF16 rows) and their dot
-// product with a row held in registers.
+// product with a row held in registers: even and odd terms summed in the
+// two halves of a pair, then added.
 template <int DP, bool BF16>
 struct SemRow;
 template <int DP>
@@ -291,17 +291,16 @@ struct SemRow<DP, false> {
         for (int k = 0; k < DP / 4; ++k) d[k] = __ldg(src + k);
     }
     __device__ __forceinline__ static float dot(const Sem<DP, false>& q, const float* row) {
-        const float4* r = reinterpret_cast<const float4*>(row);
-        float s0 = 0.f, s1 = 0.f;
+        const ulonglong2* r = reinterpret_cast<const ulonglong2*>(row);
+        u64 acc = 0ull;
 #pragma unroll
         for (int k = 0; k < DP / 4; ++k) {
-            const float4 v = r[k];
-            s0 = fmaf(q.q[4 * k], v.x, s0);
-            s1 = fmaf(q.q[4 * k + 1], v.y, s1);
-            s0 = fmaf(q.q[4 * k + 2], v.z, s0);
-            s1 = fmaf(q.q[4 * k + 3], v.w, s1);
+            const ulonglong2 v = r[k];
+            acc = ffma2(q.q2[2 * k], v.x, acc);
+            acc = ffma2(q.q2[2 * k + 1], v.y, acc);
         }
-        return s0 + s1;
+        const float2 s = f2_split(acc);
+        return s.x + s.y;
     }
 };
 template <int DP>
@@ -315,16 +314,17 @@ struct SemRow<DP, true> {
     }
     __device__ __forceinline__ static float dot(const Sem<DP, true>& q, const float* row) {
         const uint4* r = reinterpret_cast<const uint4*>(row);
-        float s0 = 0.f, s1 = 0.f;
+        u64 acc = 0ull;
 #pragma unroll
         for (int k = 0; k < DP / 8; ++k) {
             const uint4 v = r[k];
-            s0 = fmaf(q.q[8 * k + 0], bf_lo(v.x), s0); s1 = fmaf(q.q[8 * k + 1], bf_hi(v.x), s1);
-            s0 = fmaf(q.q[8 * k + 2], bf_lo(v.y), s0); s1 = fmaf(q.q[8 * k + 3], bf_hi(v.y), s1);
-            s0 = fmaf(q.q[8 * k + 4], bf_lo(v.z), s0); s1 = fmaf(q.q[8 * k + 5], bf_hi(v.z), s1);
-            s0 = fmaf(q.q[8 * k + 6], bf_lo(v.w), s0); s1 = fmaf(q.q[8 * k + 7], bf_hi(v.w), s1);
+            acc = ffma2(q.q2[4 * k + 0], bf_pair(v.x), acc);
+            acc = ffma2(q.q2[4 * k + 1], bf_pair(v.y), acc);
+            acc = ffma2(q.q2[4 * k + 2], bf_pair(v.z), acc);
+            acc = ffma2(q.q2[4 * k + 3], bf_pair(v.w), acc);
         }
-        return s0 + s1;
+        const float2 s = f2_split(acc);
+        return s.x + s.y;
     }
 };
 template <>
@@ -339,8 +339,8 @@ constexpr int PAIR_T = 256;
 #ifndef RK_PAIR_MINB
 #define RK_PAIR_MINB 2              // resident CTAs per SM the register budget targets
 #endif
-constexpr int UQ = UNIT_Q;          // queries per unit (one or two 32-bit mask words)
-static_assert(UQ == 32 || UQ == 64, "units hold 32 or 64 queries");
+constexpr int UQ = UNIT_Q;          // queries per unit: one 32-bit mask word
+static_assert(UQ == 32, "units hold 32 queries");
 
 __device__ __forceinline__ float ex2_approx(float x) {
     float y;
@@ -348,12 +348,16 @@ __device__ __forceinline__ float ex2_approx(float x) {
     return y;
 }
 
-// Per-warp shared memory: the unit's queries and the 9 stencil rows.  A query
-// is kept as m = (-2 y, |y|^2) so that the cutoff test of a candidate x is
-// |y|^2 - 2 x.y < r_c^2 - |x|^2 (three FMA); d = x - y = x + m/2.
+// Per-warp shared memory, queries kept as m = -2 y and |y|^2 so that the
+// cutoff test of a candidate x is |y|^2 - 2 x.y < r_c^2 - |x|^2 (three FMA)
+// and d = x - y = x + m/2:
+//   walk  [UQ]    float4 (m_x, m_y, m_z, m_x): pairs (m_x, m_y), (m_z, m_x)
+//   test  [UQ/2]  8 floats per query pair (j, j+1):
+//                 (m_x j, m_x j+1, m_y j, m_y j+1, m_z j, m_z j+1, |y|^2 j, |y|^2 j+1)
+//   colours [UQ] float4, labels [UQ][row words], stencil rows [40] ints.
 template <int DP, bool BF16, bool COLOR>
 __host__ __device__ constexpr int warp_smem_words() {
-    return UQ * 4 + (COLOR ? UQ * 4 : 0) + UQ * SemRow<DP, BF16>::WORDS + 4 * 10;
+    return UQ * 4 + UQ * 4 + (COLOR ? UQ * 4 : 0) + UQ * SemRow<DP, BF16>::WORDS + 4 * 10;
 }
 
 struct Rows {
@@ -416,33 +420,24 @@ __device__ __forceinline__ int unit_queries(const uint32_t* __restrict__ qkey, l
                                             uint32_t key0, int lane) {
     // units start every UQ queries of a home cell, so a unit holds at most UQ
     // of them even when the cell continues past k0 + UQ
-    const long long k1 = (long long)k0 + lane, k2 = k1 + 32;
+    const long long k1 = (long long)k0 + lane;
     const bool m1 = k1 < Q && qkey[k1] == key0;
-    const bool m2 = UQ > 32 && k2 < Q && qkey[k2] == key0;
-    const int n = __popc(__ballot_sync(FULL, m1)) + __popc(__ballot_sync(FULL, m2));
+    const int n = __popc(__ballot_sync(FULL, m1));
     return n < UQ ? n : UQ;
 }
 
-// cutoff test of the staged candidate (x, thr = r_c^2 - |x|^2) against the
-// unit's queries j in [j0, j0 + 32), bit j - j0 set when inside
-__device__ __forceinline__ unsigned test_word(const float4* __restrict__ sm, int j0, int n, float x0, float x1,
-                                              float x2, float thr) {
-    unsigned mask = 0u;
-    if (n >= 32) {
+// One step of the moment reduce-scatter: lanes whose bit `o` is clear keep
+// the lower half of their values, the others the upper half, and each adds
+// the half its partner sends.
+template <int N>
+__device__ __forceinline__ void reduce_half(long long (&v)[32], int lane) {
+    const bool up = (lane & N) != 0;
 #pragma unroll
-        for (int j = 0; j < 32; ++j) {
-            const float4 m = sm[j0 + j];
-            const float t = fmaf(x0, m.x, fmaf(x1, m.y, fmaf(x2, m.z, m.w)));
-            mask |= (t < thr) ? (1u << j) : 0u;
-        }
-    } else {
-        for (int j = 0; j < n; ++j) {
-            const float4 m = sm[j0 + j];
-            const float t = fmaf(x0, m.x, fmaf(x1, m.y, fmaf(x2, m.z, m.w)));
-            mask |= (t < thr) ? (1u << j) : 0u;
-        }
+    for (int k = 0; k < N; ++k) {
+        const long long send = up ? v[k] : v[k + N];
+        const long long keep = up ? v[k + N] : v[k];
+        v[k] = keep + __shfl_xor_sync(FULL, send, N);
     }
-    return mask;
 }
 
 template <int DP, bool BF16, bool COLOR>
@@ -459,11 +454,15 @@ k_pairs(const int* __restrict__ unit_start, const int* __restrict__ n_units, int
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     float* wb = reinterpret_cast<float*>(smem4) + warp * warp_smem_words<DP, BF16, COLOR>();
-    float4* sm = reinterpret_cast<float4*>(wb);                       // [UQ] (-2y, |y|^2)
-    float4* scq = reinterpret_cast<float4*>(wb + 4 * UQ);             // [UQ] query colours
-    float* ssq = wb + (COLOR ? 8 : 4) * UQ;                           // [UQ][SW] query labels
+    float4* smw = reinterpret_cast<float4*>(wb);                      // [UQ] walk records
+    float* smt = wb + 4 * UQ;                                         // [UQ/2][8] test records
+    float4* scq = reinterpret_cast<float4*>(wb + 8 * UQ);             // [UQ] query colours
+    float* ssq = wb + (COLOR ? 12 : 8) * UQ;                          // [UQ][SW] query labels
     int* ri = reinterpret_cast<int*>(ssq + UQ * SW);
     const Rows R{ri, ri + 9, ri + 18, ri + 27};
+    const ulonglong2* walk2 = reinterpret_cast<const ulonglong2*>(smw);
+    const ulonglong2* test2 = reinterpret_cast<const ulonglong2*>(smt);
+    const u64 H2 = f2(0.5f, 0.5f);
     const int nu = *n_units;
     for (;;) {
         int u = 0;
@@ -479,23 +478,36 @@ k_pairs(const int* __restrict__ unit_start, const int* __restrict__ n_units, int
         const int cell = (int)(key0 - edges[e].bin_off);
         const int hx = cell % dx0, hy = (cell / dx0) % dy0, hz = cell / (dx0 * dy0);
         __syncwarp();
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int q = lane + 32 * h;
+        {
+            const int q = lane;
+            float* tq = smt + 8 * (q >> 1) + (q & 1);
             if (q < qcount) {
                 const float4 r = slots[(long long)k0 + q];
                 const int s = __float_as_int(r.w);
-                sm[q] = make_float4(-2.f * r.x, -2.f * r.y, -2.f * r.z,
-                                    fmaf(r.x, r.x, fmaf(r.y, r.y, r.z * r.z)));
+                const float mx = -2.f * r.x, my = -2.f * r.y, mz = -2.f * r.z;
+                smw[q] = make_float4(mx, my, mz, mx);
+                tq[0] = mx;
+                tq[2] = my;
+                tq[4] = mz;
+                tq[6] = fmaf(r.x, r.x, fmaf(r.y, r.y, r.z * r.z));
                 if (COLOR) scq[q] = __ldg(col4 + s);
                 SemRow<DP, BF16>::stage(ssq + q * SW, sem_sorted, s);
+            } else if (q == qcount && (q & 1)) {
+                // odd count: the partner slot of the last pair never passes
+                tq[0] = 0.f;
+                tq[2] = 0.f;
+                tq[4] = 0.f;
+                tq[6] = __int_as_float(0x7f800000);
             }
         }
         const int C = build_rows(R, cell_start, Fa.cell_off, dx0, dy0, dz0, hx, hy, hz, lane);
+        const int np = (qcount + 1) >> 1;
 
-        float W = 0.f, Dv[3] = {0.f, 0.f, 0.f}, Sy[3] = {0.f, 0.f, 0.f};
-        float Myy[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, Mdy[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-        float Qm[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        // per lane, over its candidates x with sums w0 = sum w, dc = sum w d,
+        // qc = sum w d d^T: W, D, Q and sum w0 x, sum w0 x x^T, sum x dc^T
+        float W = 0.f, Dv[3] = {0.f, 0.f, 0.f}, Qm[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        float Swx[3] = {0.f, 0.f, 0.f}, Swxx[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        float Sxd[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         int cnt = 0;
         for (int c0 = 0; c0 < C; c0 += 32) {
             const int v = c0 + lane;
@@ -513,19 +525,31 @@ k_pairs(const int* __restrict__ unit_start, const int* __restrict__ n_units, int
             if (DP > 0) cs.load(sem_sorted, i, has);
             float4 cc = make_float4(0.f, 0.f, 0.f, 0.f);
             if (COLOR && has) cc = __ldg(col4 + i);
-            unsigned mk0 = test_word(sm, 0, qcount, x0, x1, x2, thr);
-            unsigned mk1 = (qcount > 32) ? test_word(sm, 32, qcount - 32, x0, x1, x2, thr) : 0u;
-            if (!has) mk0 = mk1 = 0u;
-            float w0 = 0.f, d0 = 0.f, d1 = 0.f, d2s = 0.f;
-            float q00 = 0.f, q01 = 0.f, q02 = 0.f, q11 = 0.f, q12 = 0.f, q22 = 0.f;
-            while (__any_sync(FULL, (mk0 | mk1) != 0u)) {
-                if (mk0 | mk1) {
-                    int j;
-                    if (mk0) { j = __ffs(mk0) - 1; mk0 &= mk0 - 1u; }
-                    else { j = 31 + __ffs(mk1); mk1 &= mk1 - 1u; }
-                    const float4 m = sm[j];
-                    const float ex = fmaf(0.5f, m.x, x0), ey = fmaf(0.5f, m.y, x1), ez = fmaf(0.5f, m.z, x2);
-                    const float dd = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
+            // cutoff test against query pairs: bit j set when |x - y_j| < r_c
+            unsigned mk = 0u;
+            {
+                const u64 X0 = f2(x0, x0), X1 = f2(x1, x1), X2 = f2(x2, x2);
+#pragma unroll 4
+                for (int pj = 0; pj < np; ++pj) {
+                    const ulonglong2 a = test2[2 * pj], b = test2[2 * pj + 1];
+                    const float2 t = f2_split(ffma2(X0, a.x, ffma2(X1, a.y, ffma2(X2, b.x, b.y))));
+                    mk |= ((t.x < thr ? 1u : 0u) | (t.y < thr ? 2u : 0u)) << (2 * pj);
+                }
+            }
+            if (!has) mk = 0u;
+            const u64 XA = f2(x0, x1), XB = f2(x2, x0);
+            float w0 = 0.f, dz_s = 0.f, q12 = 0.f, q22 = 0.f;
+            u64 D01 = 0ull, Q0011 = 0ull, Q0201 = 0ull;
+            while (__any_sync(FULL, mk != 0u)) {
+                if (mk) {
+                    const int j = __ffs(mk) - 1;
+                    mk &= mk - 1u;
+                    const ulonglong2 m = walk2[j];
+                    const u64 E01 = ffma2(H2, m.x, XA);                  // (ex, ey)
+                    const u64 E20 = ffma2(H2, m.y, XB);                  // (ez, ex)
+                    const float2 exy = f2_split(E01);
+                    const float ez = f2_split(E20).x;
+                    const float dd = fmaf(exy.x, exy.x, fmaf(exy.y, exy.y, ez * ez));
                     float arg = dd * gp.kg;
                     if (COLOR) {
                         const float4 qc = scq[j];
@@ -534,43 +558,62 @@ k_pairs(const int* __restrict__ unit_start, const int* __restrict__ n_units, int
                     }
                     const float s = SemRow<DP, BF16>::dot(cs, ssq + j * SW);
                     const float w = s * ex2_approx(arg);
-                    const float wx = w * ex, wy = w * ey, wz = w * ez;
+                    const u64 WXY = fmul2(f2(w, w), E01);                // (w ex, w ey)
+                    const float wz = w * ez;
                     w0 += w;
-                    d0 += wx; d1 += wy; d2s += wz;
-                    q00 = fmaf(wx, ex, q00); q01 = fmaf(wx, ey, q01); q02 = fmaf(wx, ez, q02);
-                    q11 = fmaf(wy, ey, q11); q12 = fmaf(wy, ez, q12); q22 = fmaf(wz, ez, q22);
+                    D01 = fadd2(D01, WXY);
+                    dz_s += wz;
+                    Q0011 = ffma2(WXY, E01, Q0011);                      // (q00, q11)
+                    Q0201 = ffma2(WXY, E20, Q0201);                      // (q02, q01)
+                    q12 = fmaf(f2_split(WXY).y, ez, q12);
+                    q22 = fmaf(wz, ez, q22);
                     ++cnt;
                 }
             }
-            // fold the candidate's sums: y' = x - d
+            const float2 dxy = f2_split(D01), q0011 = f2_split(Q0011), q0201 = f2_split(Q0201);
             const float x[3] = {x0, x1, x2};
-            const float dc[3] = {d0, d1, d2s};
-            const float qc6[6] = {q00, q01, q02, q11, q12, q22};
+            const float dc[3] = {dxy.x, dxy.y, dz_s};
             W += w0;
+            Qm[0] += q0011.x;
+            Qm[1] += q0201.y;
+            Qm[2] += q0201.x;
+            Qm[3] += q0011.y;
+            Qm[4] += q12;
+            Qm[5] += q22;
 #pragma unroll
             for (int mm = 0; mm < 3; ++mm) {
                 Dv[mm] += dc[mm];
-                Sy[mm] = fmaf(w0, x[mm], Sy[mm]) - dc[mm];
+                const float wx = w0 * x[mm];
+                Swx[mm] += wx;
+#pragma unroll
+                for (int l = 0; l < 3; ++l) Sxd[3 * mm + l] = fmaf(x[mm], dc[l], Sxd[3 * mm + l]);
+#pragma unroll
+                for (int l = mm; l < 3; ++l) {
+                    const int t6 = mm == 0 ? l : (mm == 1 ? 2 + l : 5);
+                    Swxx[t6] = fmaf(wx, x[l], Swxx[t6]);
+                }
             }
-            int t6 = 0;
-#pragma unroll
-            for (int mm = 0; mm < 3; ++mm)
-#pragma unroll
-                for (int l = mm; l < 3; ++l, ++t6) {
-                    // sum w y'y'^T = W x x^T - x D^T - D x^T + Q
-                    Myy[t6] += fmaf(w0 * x[mm], x[l], -(x[mm] * dc[l] + dc[mm] * x[l])) + qc6[t6];
-                    Qm[t6] += qc6[t6];
-                }
-#pragma unroll
-            for (int mm = 0; mm < 3; ++mm)
-#pragma unroll
-                for (int l = 0; l < 3; ++l) {
-                    // sum w d y'^T = D x^T - Q
-                    const int qi = (mm <= l) ? (mm == 0 ? l : (mm == 1 ? 2 + l : 5))
-                                             : (l == 0 ? mm : (l == 1 ? 2 + mm : 5));
-                    Mdy[3 * mm + l] += fmaf(dc[mm], x[l], -qc6[qi]);
-                }
         }
+        // y' = x - d:  sum w y' = sum w0 x - D;  sum w y'y'^T = sum w0 x x^T -
+        // sum (x dc^T + dc x^T) + Q;  sum w d y'^T = sum dc x^T - Q
+        float Sy[3], Myy[6], Mdy[9];
+#pragma unroll
+        for (int mm = 0; mm < 3; ++mm) Sy[mm] = Swx[mm] - Dv[mm];
+#pragma unroll
+        for (int mm = 0; mm < 3; ++mm)
+#pragma unroll
+            for (int l = mm; l < 3; ++l) {
+                const int t6 = mm == 0 ? l : (mm == 1 ? 2 + l : 5);
+                Myy[t6] = Swxx[t6] - (Sxd[3 * mm + l] + Sxd[3 * l + mm]) + Qm[t6];
+            }
+#pragma unroll
+        for (int mm = 0; mm < 3; ++mm)
+#pragma unroll
+            for (int l = 0; l < 3; ++l) {
+                const int qi = (mm <= l) ? (mm == 0 ? l : (mm == 1 ? 2 + l : 5))
+                                         : (l == 0 ? mm : (l == 1 ? 2 + mm : 5));
+                Mdy[3 * mm + l] = Sxd[3 * l + mm] - Qm[qi];
+            }
         // home-centre coordinates -> frame-a coordinates: y' += o
         const float o[3] = {((float)(hx + Fa.lo[0]) + 0.5f) * gp.hf, ((float)(hy + Fa.lo[1]) + 0.5f) * gp.hf,
                             ((float)(hz + Fa.lo[2]) + 0.5f) * gp.hf};
@@ -588,22 +631,30 @@ k_pairs(const int* __restrict__ unit_start, const int* __restrict__ n_units, int
 #pragma unroll
             for (int mm = 0; mm < 3; ++mm) Sy[mm] = fmaf(W, o[mm], Sy[mm]);
         }
+        // fixed point per lane, then a reduce-scatter over the warp: lane k
+        // ends with the warp total of moment k
         const float* scl = edges[e].scale;
-        long long* dst = acc + (long long)e * ACC_N;
+        long long vals[32];
 #pragma unroll
-        for (int k = 0; k < N_MOM; ++k) {
-            float val;
+        for (int k = 0; k < 32; ++k) {
+            float val = 0.f;
             if (k == 0) val = W;
             else if (k < 4) val = Dv[k - 1];
             else if (k < 7) val = Sy[k - 4];
             else if (k < 13) val = Myy[k - 7];
             else if (k < 22) val = Mdy[k - 13];
-            else val = Qm[(k - 22) % 6];
-            const long long vv = (k == N_MOM - 1) ? (long long)cnt : to_fixed(val, __ldg(scl + moment_class(k)));
-            const long long tot = warp_sum_ll(vv);
-            if (lane == k && tot != 0)
-                atomicAdd(reinterpret_cast<unsigned long long*>(dst + k), (unsigned long long)tot);
+            else if (k < 28) val = Qm[k - 22];
+            vals[k] = (k == N_MOM - 1) ? (long long)cnt
+                    : (k < N_MOM ? to_fixed(val, __ldg(scl + moment_class(k))) : 0ll);
         }
+        reduce_half<16>(vals, lane);
+        reduce_half<8>(vals, lane);
+        reduce_half<4>(vals, lane);
+        reduce_half<2>(vals, lane);
+        reduce_half<1>(vals, lane);
+        if (lane < N_MOM && vals[0] != 0)
+            atomicAdd(reinterpret_cast<unsigned long long*>(acc + (long long)e * ACC_N + lane),
+                      (unsigned long long)vals[0]);
     }
 }
 
