@@ -207,7 +207,24 @@ __global__ void __launch_bounds__(256) k_units(const uint32_t* __restrict__ key,
     }
 }
 
-__device__ __forceinline__ long long to_fixed(float v, float scale) { return __float2ll_rn(v * scale); }
+// round(v * scale) to the nearest integer (ties to even) as int64, for
+// |v * scale| < 2^62, with FP32 adds and integer operations only.  Below 2^22
+// adding 2^23 leaves the rounded magnitude in the mantissa bits; from 2^22 up
+// the value is m * 2^(e - 150) with a 24-bit mantissa m.
+__device__ __forceinline__ long long to_fixed(float v, float scale) {
+    const float x = v * scale;
+    const int b = __float_as_int(x);
+    const int ex = (b >> 23) & 0xff;
+    long long mag;
+    if (ex < 149) {
+        const float t = fabsf(x) + 8388608.0f;
+        mag = __float_as_int(t) & 0x7fffff;
+    } else {
+        const long long m = (b & 0x7fffff) | 0x800000;
+        mag = (ex == 149) ? ((m >> 1) + (m & (m >> 1) & 1)) : (m << (ex - 150));
+    }
+    return b < 0 ? -mag : mag;
+}
 
 // ---------------------------------------------------- paired FP32 ops ----
 // Two FP32 lanes in one 64-bit register: fma/mul/add .f32x2 issue one
@@ -337,7 +354,7 @@ struct SemRow<0, false> {
 
 constexpr int PAIR_T = 256;
 #ifndef RK_PAIR_MINB
-#define RK_PAIR_MINB 2              // resident CTAs per SM the register budget targets
+#define RK_PAIR_MINB 3              // resident CTAs per SM the register budget targets
 #endif
 constexpr int UQ = UNIT_Q;          // queries per unit: one 32-bit mask word
 static_assert(UQ == 32, "units hold 32 queries");
@@ -354,10 +371,17 @@ __device__ __forceinline__ float ex2_approx(float x) {
 //   walk  [UQ]    float4 (m_x, m_y, m_z, m_x): pairs (m_x, m_y), (m_z, m_x)
 //   test  [UQ/2]  8 floats per query pair (j, j+1):
 //                 (m_x j, m_x j+1, m_y j, m_y j+1, m_z j, m_z j+1, |y|^2 j, |y|^2 j+1)
-//   colours [UQ] float4, labels [UQ][row words], stencil rows [40] ints.
+//   colours [UQ] float4, labels [UQ][row words], stencil rows [40] ints,
+//   per-lane unit sums [32][N_ACC] (kept in shared memory to free registers).
+// Per-lane sums over a unit, in this order: W, D (3), Q (6), sum w0 x (3),
+// sum w0 x x^T (6), sum x dc^T (9), with w0 = sum w, dc = sum w d of one
+// candidate over its queries.
+constexpr int N_ACC = 28;
+constexpr int A_W = 0, A_D = 1, A_Q = 4, A_SWX = 10, A_SWXX = 13, A_SXD = 19;
+
 template <int DP, bool BF16, bool COLOR>
 __host__ __device__ constexpr int warp_smem_words() {
-    return UQ * 4 + UQ * 4 + (COLOR ? UQ * 4 : 0) + UQ * SemRow<DP, BF16>::WORDS + 4 * 10;
+    return UQ * 4 + UQ * 4 + (COLOR ? UQ * 4 : 0) + UQ * SemRow<DP, BF16>::WORDS + 4 * 10 + 32 * N_ACC;
 }
 
 struct Rows {
@@ -460,6 +484,7 @@ k_pairs(const int* __restrict__ unit_start, const int* __restrict__ n_units, int
     float* ssq = wb + (COLOR ? 12 : 8) * UQ;                          // [UQ][SW] query labels
     int* ri = reinterpret_cast<int*>(ssq + UQ * SW);
     const Rows R{ri, ri + 9, ri + 18, ri + 27};
+    float4* sacc = reinterpret_cast<float4*>(ri + 40) + lane * (N_ACC / 4);   // this lane's unit sums
     const ulonglong2* walk2 = reinterpret_cast<const ulonglong2*>(smw);
     const ulonglong2* test2 = reinterpret_cast<const ulonglong2*>(smt);
     const u64 H2 = f2(0.5f, 0.5f);
@@ -505,9 +530,8 @@ k_pairs(const int* __restrict__ unit_start, const int* __restrict__ n_units, int
 
         // per lane, over its candidates x with sums w0 = sum w, dc = sum w d,
         // qc = sum w d d^T: W, D, Q and sum w0 x, sum w0 x x^T, sum x dc^T
-        float W = 0.f, Dv[3] = {0.f, 0.f, 0.f}, Qm[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-        float Swx[3] = {0.f, 0.f, 0.f}, Swxx[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-        float Sxd[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int k = 0; k < N_ACC / 4; ++k) sacc[k] = make_float4(0.f, 0.f, 0.f, 0.f);
         int cnt = 0;
         for (int c0 = 0; c0 < C; c0 += 32) {
             const int v = c0 + lane;
@@ -573,27 +597,44 @@ k_pairs(const int* __restrict__ unit_start, const int* __restrict__ n_units, int
             const float2 dxy = f2_split(D01), q0011 = f2_split(Q0011), q0201 = f2_split(Q0201);
             const float x[3] = {x0, x1, x2};
             const float dc[3] = {dxy.x, dxy.y, dz_s};
-            W += w0;
-            Qm[0] += q0011.x;
-            Qm[1] += q0201.y;
-            Qm[2] += q0201.x;
-            Qm[3] += q0011.y;
-            Qm[4] += q12;
-            Qm[5] += q22;
+            const float qc[6] = {q0011.x, q0201.y, q0201.x, q0011.y, q12, q22};
+            float a[N_ACC];
+#pragma unroll
+            for (int k = 0; k < N_ACC / 4; ++k) {
+                const float4 t = sacc[k];
+                a[4 * k] = t.x; a[4 * k + 1] = t.y; a[4 * k + 2] = t.z; a[4 * k + 3] = t.w;
+            }
+            a[A_W] += w0;
+#pragma unroll
+            for (int t6 = 0; t6 < 6; ++t6) a[A_Q + t6] += qc[t6];
 #pragma unroll
             for (int mm = 0; mm < 3; ++mm) {
-                Dv[mm] += dc[mm];
+                a[A_D + mm] += dc[mm];
                 const float wx = w0 * x[mm];
-                Swx[mm] += wx;
+                a[A_SWX + mm] += wx;
 #pragma unroll
-                for (int l = 0; l < 3; ++l) Sxd[3 * mm + l] = fmaf(x[mm], dc[l], Sxd[3 * mm + l]);
+                for (int l = 0; l < 3; ++l) a[A_SXD + 3 * mm + l] = fmaf(x[mm], dc[l], a[A_SXD + 3 * mm + l]);
 #pragma unroll
                 for (int l = mm; l < 3; ++l) {
                     const int t6 = mm == 0 ? l : (mm == 1 ? 2 + l : 5);
-                    Swxx[t6] = fmaf(wx, x[l], Swxx[t6]);
+                    a[A_SWXX + t6] = fmaf(wx, x[l], a[A_SWXX + t6]);
                 }
             }
+#pragma unroll
+            for (int k = 0; k < N_ACC / 4; ++k) sacc[k] = make_float4(a[4 * k], a[4 * k + 1], a[4 * k + 2], a[4 * k + 3]);
         }
+        float a[N_ACC];
+#pragma unroll
+        for (int k = 0; k < N_ACC / 4; ++k) {
+            const float4 t = sacc[k];
+            a[4 * k] = t.x; a[4 * k + 1] = t.y; a[4 * k + 2] = t.z; a[4 * k + 3] = t.w;
+        }
+        const float W = a[A_W];
+        const float Dv[3] = {a[A_D], a[A_D + 1], a[A_D + 2]};
+        const float* Qm = a + A_Q;
+        const float* Swx = a + A_SWX;
+        const float* Swxx = a + A_SWXX;
+        const float* Sxd = a + A_SXD;
         // y' = x - d:  sum w y' = sum w0 x - D;  sum w y'y'^T = sum w0 x x^T -
         // sum (x dc^T + dc x^T) + Q;  sum w d y'^T = sum dc x^T - Q
         float Sy[3], Myy[6], Mdy[9];
