@@ -372,16 +372,19 @@ __device__ __forceinline__ float ex2_approx(float x) {
 //   test  [UQ/2]  8 floats per query pair (j, j+1):
 //                 (m_x j, m_x j+1, m_y j, m_y j+1, m_z j, m_z j+1, |y|^2 j, |y|^2 j+1)
 //   colours [UQ] float4, labels [UQ][row words], stencil rows [40] ints,
-//   per-lane unit sums [32][N_ACC] (kept in shared memory to free registers).
+//   per-lane unit sums [32][N_ACC] (kept in shared memory to free registers),
+//   candidate queue [CQ_N] float4 (x relative to the home centre, point index).
 // Per-lane sums over a unit, in this order: W, D (3), Q (6), sum w0 x (3),
 // sum w0 x x^T (6), sum x dc^T (9), with w0 = sum w, dc = sum w d of one
 // candidate over its queries.
 constexpr int N_ACC = 28;
+constexpr int CQ_N = 64;            // ring of candidates that survived the unit's box test
 constexpr int A_W = 0, A_D = 1, A_Q = 4, A_SWX = 10, A_SWXX = 13, A_SXD = 19;
 
 template <int DP, bool BF16, bool COLOR>
 __host__ __device__ constexpr int warp_smem_words() {
-    return UQ * 4 + UQ * 4 + (COLOR ? UQ * 4 : 0) + UQ * SemRow<DP, BF16>::WORDS + 4 * 10 + 32 * N_ACC;
+    return UQ * 4 + UQ * 4 + (COLOR ? UQ * 4 : 0) + UQ * SemRow<DP, BF16>::WORDS + 4 * 10 + 32 * N_ACC +
+           4 * CQ_N;
 }
 
 struct Rows {
@@ -485,6 +488,7 @@ k_pairs(const int* __restrict__ unit_start, const int* __restrict__ n_units, int
     int* ri = reinterpret_cast<int*>(ssq + UQ * SW);
     const Rows R{ri, ri + 9, ri + 18, ri + 27};
     float4* sacc = reinterpret_cast<float4*>(ri + 40) + lane * (N_ACC / 4);   // this lane's unit sums
+    float4* cq = reinterpret_cast<float4*>(ri + 40) + 32 * (N_ACC / 4);       // candidate ring
     const ulonglong2* walk2 = reinterpret_cast<const ulonglong2*>(smw);
     const ulonglong2* test2 = reinterpret_cast<const ulonglong2*>(smt);
     const u64 H2 = f2(0.5f, 0.5f);
@@ -503,11 +507,17 @@ k_pairs(const int* __restrict__ unit_start, const int* __restrict__ n_units, int
         const int cell = (int)(key0 - edges[e].bin_off);
         const int hx = cell % dx0, hy = (cell / dx0) % dy0, hz = cell / (dx0 * dy0);
         __syncwarp();
+        // bounding box of the unit's queries (home-centre coordinates)
+        float blo0 = __int_as_float(0x7f800000), blo1 = blo0, blo2 = blo0;
+        float bhi0 = -blo0, bhi1 = -blo0, bhi2 = -blo0;
         {
             const int q = lane;
             float* tq = smt + 8 * (q >> 1) + (q & 1);
             if (q < qcount) {
                 const float4 r = slots[(long long)k0 + q];
+                blo0 = bhi0 = r.x;
+                blo1 = bhi1 = r.y;
+                blo2 = bhi2 = r.z;
                 const int s = __float_as_int(r.w);
                 const float mx = -2.f * r.x, my = -2.f * r.y, mz = -2.f * r.z;
                 smw[q] = make_float4(mx, my, mz, mx);
@@ -525,24 +535,63 @@ k_pairs(const int* __restrict__ unit_start, const int* __restrict__ n_units, int
                 tq[6] = __int_as_float(0x7f800000);
             }
         }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            blo0 = fminf(blo0, __shfl_xor_sync(FULL, blo0, o));
+            blo1 = fminf(blo1, __shfl_xor_sync(FULL, blo1, o));
+            blo2 = fminf(blo2, __shfl_xor_sync(FULL, blo2, o));
+            bhi0 = fmaxf(bhi0, __shfl_xor_sync(FULL, bhi0, o));
+            bhi1 = fmaxf(bhi1, __shfl_xor_sync(FULL, bhi1, o));
+            bhi2 = fmaxf(bhi2, __shfl_xor_sync(FULL, bhi2, o));
+        }
         const int C = build_rows(R, cell_start, Fa.cell_off, dx0, dy0, dz0, hx, hy, hz, lane);
         const int np = (qcount + 1) >> 1;
+        // a candidate farther than r_c from the query box pairs with none of
+        // the queries; the margin keeps every candidate the exact test passes
+        const float box_thr = gp.rc2 * 1.0001f;
 
         // per lane, over its candidates x with sums w0 = sum w, dc = sum w d,
         // qc = sum w d d^T: W, D, Q and sum w0 x, sum w0 x x^T, sum x dc^T
 #pragma unroll
         for (int k = 0; k < N_ACC / 4; ++k) sacc[k] = make_float4(0.f, 0.f, 0.f, 0.f);
         int cnt = 0;
-        for (int c0 = 0; c0 < C; c0 += 32) {
-            const int v = c0 + lane;
-            const bool has = v < C;
-            int dx = 0, dy = 0, dz = 0, i = 0;
-            if (has) i = stream_point(R, v, dx, dy, dz);
-            const float4 p = has ? __ldg(pts4 + i) : make_float4(0.f, 0.f, 0.f, 0.f);
+        int c_s = 0, qhead = 0, qlen = 0;            // stream position, ring head and fill
+        while (c_s < C || qlen > 0) {
+            // stream the 27-cell candidates through the box test into the
+            // ring until it holds a full batch (or the stream ends)
+            while (qlen < 32 && c_s < C) {
+                const int v = c_s + lane;
+                bool keep = false;
+                float4 ent = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (v < C) {
+                    int dx, dy, dz;
+                    const int i = stream_point(R, v, dx, dy, dz);
+                    const float4 p = __ldg(pts4 + i);
+                    ent.x = fmaf((float)dx, gp.hf, p.x);
+                    ent.y = fmaf((float)dy, gp.hf, p.y);
+                    ent.z = fmaf((float)dz, gp.hf, p.z);
+                    ent.w = __int_as_float(i);
+                    const float e0 = fmaxf(fmaxf(blo0 - ent.x, ent.x - bhi0), 0.f);
+                    const float e1 = fmaxf(fmaxf(blo1 - ent.y, ent.y - bhi1), 0.f);
+                    const float e2 = fmaxf(fmaxf(blo2 - ent.z, ent.z - bhi2), 0.f);
+                    keep = fmaf(e0, e0, fmaf(e1, e1, e2 * e2)) < box_thr;
+                }
+                const unsigned bal = __ballot_sync(FULL, keep);
+                if (keep) cq[(qhead + qlen + __popc(bal & ((1u << lane) - 1u))) & (CQ_N - 1)] = ent;
+                qlen += __popc(bal);
+                c_s += 32;
+            }
+            __syncwarp();
+            const int nb = qlen < 32 ? qlen : 32;
+            if (nb == 0) break;                      // stream ended with the ring empty
+            const bool has = lane < nb;
+            const float4 ent = has ? cq[(qhead + lane) & (CQ_N - 1)] : make_float4(0.f, 0.f, 0.f, 0.f);
+            qhead = (qhead + nb) & (CQ_N - 1);
+            qlen -= nb;
+            __syncwarp();
+            const int i = __float_as_int(ent.w);
             // candidate relative to the home cell centre
-            const float x0 = fmaf((float)dx, gp.hf, p.x);
-            const float x1 = fmaf((float)dy, gp.hf, p.y);
-            const float x2 = fmaf((float)dz, gp.hf, p.z);
+            const float x0 = ent.x, x1 = ent.y, x2 = ent.z;
             const float xx = fmaf(x0, x0, fmaf(x1, x1, x2 * x2));
             const float thr = gp.rc2 - xx;
             Sem<DP, BF16> cs;
