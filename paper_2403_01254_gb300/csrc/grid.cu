@@ -29,47 +29,88 @@ __device__ __forceinline__ int frame_of(const long long* __restrict__ off, int K
 // floor(x / h) computed as floor(x * h_inv) in FP64; identical in every kernel
 __device__ __forceinline__ double cell_q(double x, double h_inv) { return floor(x * h_inv); }
 
+// Cell-coordinate bounds and label-norm maximum per frame, plus input checks.
+// A warp whose points all belong to one frame reduces its bounds with
+// shuffles and makes one set of atomics; a warp across a frame boundary
+// falls back to per-point atomics.
 __global__ void k_bbox(const double* __restrict__ xyz, const float* __restrict__ sem,
                        const float* __restrict__ rgb, long long N, int K,
                        const long long* __restrict__ pt_off, int sem_dim, double h_inv,
                        int* cmin, int* cmax, unsigned* sem_norm_bits, int* err) {
     const double lim = 536870912.0;   // 2^29
-    for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < N;
-         g += (long long)gridDim.x * blockDim.x) {
-        int f = frame_of(pt_off, K, g);
+    const int lane = threadIdx.x & 31;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long w0 = blockIdx.x * (long long)blockDim.x + (threadIdx.x & ~31); w0 < N; w0 += stride) {
+        const long long g = w0 + lane;
+        const bool valid = g < N;
+        const int f = valid ? frame_of(pt_off, K, g) : -1;
         int bad = 0;
-        int c[3];
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            double x = xyz[3 * g + k];
-            if (!isfinite(x)) { bad |= 1; c[k] = 0; continue; }
-            double q = cell_q(x, h_inv);
-            if (!(fabs(q) < lim)) { bad |= 2; c[k] = 0; continue; }
-            c[k] = (int)q;
-        }
-        if (!bad) {
+        int lo[3] = {0x7fffffff, 0x7fffffff, 0x7fffffff}, hi[3] = {(int)0x80000000, (int)0x80000000,
+                                                                (int)0x80000000};
+        unsigned nrm_bits = 0u;
+        if (valid) {
+            int c[3];
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
-                atomicMin(&cmin[3 * f + k], c[k]);
-                atomicMax(&cmax[3 * f + k], c[k]);
+                double x = xyz[3 * g + k];
+                if (!isfinite(x)) { bad |= 1; c[k] = 0; continue; }
+                double q = cell_q(x, h_inv);
+                if (!(fabs(q) < lim)) { bad |= 2; c[k] = 0; continue; }
+                c[k] = (int)q;
             }
-        }
-        if (sem_dim > 0) {
-            float s = 0.f;
-            for (int k = 0; k < sem_dim; ++k) {
-                float v = sem[g * sem_dim + k];
-                if (!isfinite(v)) bad |= 4;
-                s = fmaf(v, v, s);
-            }
-            float nrm = isfinite(s) ? sqrtf(s) : 0.f;
-            atomicMax(&sem_norm_bits[f], __float_as_uint(nrm));
-        }
-        if (rgb) {
+            if (!bad) {
 #pragma unroll
-            for (int k = 0; k < 3; ++k)
-                if (!isfinite(rgb[3 * g + k])) bad |= 8;
+                for (int k = 0; k < 3; ++k) lo[k] = hi[k] = c[k];
+            }
+            if (sem_dim > 0) {
+                float s = 0.f;
+                for (int k = 0; k < sem_dim; ++k) {
+                    float v = sem[g * sem_dim + k];
+                    if (!isfinite(v)) bad |= 4;
+                    s = fmaf(v, v, s);
+                }
+                nrm_bits = __float_as_uint(isfinite(s) ? sqrtf(s) : 0.f);
+            }
+            if (rgb) {
+#pragma unroll
+                for (int k = 0; k < 3; ++k)
+                    if (!isfinite(rgb[3 * g + k])) bad |= 8;
+            }
         }
-        if (bad) atomicOr(err, bad);
+        const int f0 = __shfl_sync(0xffffffffu, f, 0);
+        if (__all_sync(0xffffffffu, !valid || f == f0)) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    lo[k] = min(lo[k], __shfl_xor_sync(0xffffffffu, lo[k], o));
+                    hi[k] = max(hi[k], __shfl_xor_sync(0xffffffffu, hi[k], o));
+                }
+                nrm_bits = max(nrm_bits, __shfl_xor_sync(0xffffffffu, nrm_bits, o));
+                bad |= __shfl_xor_sync(0xffffffffu, bad, o);
+            }
+            if (lane == 0) {
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    if (lo[k] <= hi[k]) {
+                        atomicMin(&cmin[3 * f0 + k], lo[k]);
+                        atomicMax(&cmax[3 * f0 + k], hi[k]);
+                    }
+                }
+                if (sem_dim > 0) atomicMax(&sem_norm_bits[f0], nrm_bits);
+                if (bad) atomicOr(err, bad);
+            }
+        } else if (valid) {
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                if (lo[k] <= hi[k]) {
+                    atomicMin(&cmin[3 * f + k], lo[k]);
+                    atomicMax(&cmax[3 * f + k], hi[k]);
+                }
+            }
+            if (sem_dim > 0) atomicMax(&sem_norm_bits[f], nrm_bits);
+            if (bad) atomicOr(err, bad);
+        }
     }
 }
 
