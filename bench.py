@@ -203,6 +203,18 @@ class ClockSampler:
 
 
 # -------------------------------------------------------------------- ours --
+def replica_throughput(ms_local, pairs_per_step, steps, world, device=None):
+    """Whole-job throughput of independent replicas: every rank processed
+    pairs_per_step x steps pair-terms; the job time is the slowest rank's
+    (all_reduce MAX over the process group when world > 1)."""
+    import torch
+    t = torch.tensor([float(ms_local)], dtype=torch.float64, device=device)
+    if world > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    ms_max = float(t.item())
+    return pairs_per_step * steps * world / (ms_max / 1e3), ms_max
+
+
 def ours(args, rank, world, local_rank):
     import torch
 
@@ -279,12 +291,7 @@ def ours(args, rank, world, local_rank):
     prof = rb.rkhsba_profile(ctx, 0, read=True)
     clk = clocks.stop()
     ms = sum(a.elapsed_time(b) for a, b in ev)
-    t = torch.tensor([ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-    ms_max = float(t.item())
-    total_pairs = pairs_per_step * args.steps * world
-    value = total_pairs / (ms_max / 1e3)
+    value, ms_max = replica_throughput(ms, pairs_per_step, args.steps, world, dev)
 
     # roofline of the dominant kernel (the pair kernel): FP32 arithmetic
     pair_ms, pair_n = prof["pairs"]
