@@ -146,7 +146,7 @@ void grid_fill(rkhsba_ctx* c, bool* keys_in_alt) {
     while ((1LL << nbits) < c->C_total) ++nbits;
     bool alt = false;
     radix_sort_u32(c->d_keys, c->d_vals, c->d_keys_alt, c->d_vals_alt, c->N, nbits, c->d_hist,
-                   c->d_scan_ws, st, &alt);
+                   c->d_scan_ws, c->d_err + 1, st, &alt);
     const uint32_t* keys = alt ? c->d_keys_alt : c->d_keys;
     const int* perm = alt ? c->d_vals_alt : c->d_vals;
     launch_gather(c->d_xyz, c->d_sem_in, c->d_rgb_in, c->N, c->K, c->d_pt_off, keys, perm, c->gp,
@@ -401,7 +401,7 @@ void run_binning(rkhsba_ctx* c, const double* poses, const int* done) {
                       c->d_qkey, c->d_qval, c->d_qrec, done, st);
     bool alt = false;
     radix_sort_u32(c->d_qkey, c->d_qval, c->d_qkey_alt, c->d_qval_alt, c->Q_total, c->qbits, c->d_qhist,
-                   c->d_scan_ws, st, &alt);
+                   c->d_scan_ws, c->d_err + 1, st, &alt);
     c->q_sorted_key = alt ? c->d_qkey_alt : c->d_qkey;
     const int* qv = alt ? c->d_qval_alt : c->d_qval;
     launch_query_gather(c->q_sorted_key, qv, c->d_qrec, c->Q_total, c->d_slots, c->d_bin_first, done, st);
@@ -603,6 +603,8 @@ rkhsba_status rkhsba_eval(rkhsba_ctx* c, const double* poses, double* loss, doub
     run_eval(c, c->d_poses_cand, nullptr);
     RK_CUDA(c, cudaGetLastError());
     double F = 0.0;
+    int sort_err = 0;
+    RK_CUDA(c, cudaMemcpyAsync(&sort_err, c->d_err + 1, sizeof(int), cudaMemcpyDeviceToHost, st));
     RK_CUDA(c, cudaMemcpyAsync(&F, c->d_F_cand, sizeof(double), cudaMemcpyDeviceToHost, st));
     std::vector<double> b;
     if (grad) {
@@ -618,6 +620,7 @@ rkhsba_status rkhsba_eval(rkhsba_ctx* c, const double* poses, double* loss, doub
         RK_CUDA(c, cudaMemcpyAsync(eo.data(), c->d_eout, sizeof(EdgeOut) * c->E, cudaMemcpyDeviceToHost, st));
     }
     RK_CUDA(c, cudaStreamSynchronize(st));
+    if (sort_err) return fail(c, RKHSBA_ETIMEOUT, "a bounded wait of the radix sort gave up");
     if (loss) *loss = -F;
     if (grad) {
         const double scale = c->p.sigma * c->p.sigma / (c->p.ell * c->p.ell);
@@ -660,11 +663,14 @@ rkhsba_status rkhsba_iterate(rkhsba_ctx* c, int32_t n_iters) {
 rkhsba_status rkhsba_get_state(rkhsba_ctx* c, double* poses, rkhsba_solve_info* info) {
     if (!c) return fail(nullptr, RKHSBA_EINVAL, "ctx is NULL");
     LMState s{};
+    int sort_err = 0;
     RK_CUDA(c, cudaMemcpyAsync(&s, c->d_state, sizeof(LMState), cudaMemcpyDeviceToHost, c->stream));
+    RK_CUDA(c, cudaMemcpyAsync(&sort_err, c->d_err + 1, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     if (poses)
         RK_CUDA(c, cudaMemcpyAsync(poses, c->d_poses_cur, sizeof(double) * 16 * c->K,
                                    cudaMemcpyDeviceToHost, c->stream));
     RK_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (sort_err) return fail(c, RKHSBA_ETIMEOUT, "a bounded wait of the radix sort gave up");
     if (info) {
         info->iters = s.iters;
         info->status = s.done ? s.status : RKHSBA_ENOTCONV;

@@ -112,11 +112,12 @@ struct LMState {
 
 // ------------------------------------------------------------ launchers ----
 // scan.cu
-size_t scan_ws_elems(long long n);
-void scan_exclusive_i64(const long long* in, long long* out, long long n, long long* total,
-                        long long* ws, cudaStream_t st);
+size_t scan_ws_elems(long long n);   // long longs of the radix sort's small workspace
+// Stable LSD sort of the low nbits of keys (payload vals); ends in the *_alt
+// buffers when *in_alt.  hist: radix_hist_elems(n) long longs; ws:
+// scan_ws_elems(n); *err |= 1 if a bounded wait of the look-back gave up.
 void radix_sort_u32(uint32_t* keys, int* vals, uint32_t* keys_alt, int* vals_alt, long long n,
-                    int nbits, long long* hist, long long* ws, cudaStream_t st, bool* in_alt);
+                    int nbits, long long* hist, long long* ws, int* err, cudaStream_t st, bool* in_alt);
 size_t radix_hist_elems(long long n);
 
 // grid.cu

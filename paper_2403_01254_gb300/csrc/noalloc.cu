@@ -327,7 +327,7 @@ extern "C" rkhsba_status rkhsba_eval_static(int32_t n_frames, const int64_t* n_p
     SCK(cudaMemsetAsync(d_cell_start, 0, sizeof(int) * (C + 1), st));
     launch_keys(d_xyz, N, K, d_pt_off, d_frames, gp.h_inv, d_keys, d_vals, st);
     bool alt = false;
-    radix_sort_u32(d_keys, d_vals, d_keys_alt, d_vals_alt, N, cbits, d_hist, d_ws, st, &alt);
+    radix_sort_u32(d_keys, d_vals, d_keys_alt, d_vals_alt, N, cbits, d_hist, d_ws, d_err + 1, st, &alt);
     const uint32_t* pt_cell = alt ? d_keys_alt : d_keys;
     launch_gather(d_xyz, d_sem, gp.color ? d_rgb : nullptr, N, K, d_pt_off, pt_cell, alt ? d_vals_alt : d_vals,
                   gp, C, d_pts4, d_sem_sorted, d_col4, d_perm_local, d_cell_start, d_run, st);
@@ -338,7 +338,7 @@ extern "C" rkhsba_status rkhsba_eval_static(int32_t n_frames, const int64_t* n_p
     SCK(cudaMemsetAsync(d_acc, 0, sizeof(long long) * E * ACC_N, st));
     launch_query_keys(d_edges, E, d_frames, d_xf, pt_cell, d_pts4, gp, Q, d_qkey, d_qval, d_qrec, nullptr, st);
     bool qalt = false;
-    radix_sort_u32(d_qkey, d_qval, d_qkey_alt, d_qval_alt, Q, qbits, d_hist, d_ws, st, &qalt);
+    radix_sort_u32(d_qkey, d_qval, d_qkey_alt, d_qval_alt, Q, qbits, d_hist, d_ws, d_err + 1, st, &qalt);
     const uint32_t* qk = qalt ? d_qkey_alt : d_qkey;
     launch_query_gather(qk, qalt ? d_qval_alt : d_qval, d_qrec, Q, d_slots, d_bin_first, nullptr, st);
     launch_units(qk, d_bin_first, Q, d_units, d_ucount, nullptr, st);
@@ -351,11 +351,14 @@ extern "C" rkhsba_status rkhsba_eval_static(int32_t n_frames, const int64_t* n_p
     // ---- results to the caller's host buffers ----
     double F = 0.0;
     double bvec[6 * MAX_K];
+    int sort_err = 0;
+    SCK(cudaMemcpyAsync(&sort_err, d_err + 1, sizeof(int), cudaMemcpyDeviceToHost, st));
     SCK(cudaMemcpyAsync(&F, d_F, sizeof(double), cudaMemcpyDeviceToHost, st));
     SCK(cudaMemcpyAsync(bvec, d_b, sizeof(double) * 6 * K, cudaMemcpyDeviceToHost, st));
     if (H_full) SCK(cudaMemcpyAsync(H_full, d_H, sizeof(double) * 36LL * K * K, cudaMemcpyDeviceToHost, st));
     SCK(cudaStreamSynchronize(st));
     SCK(cudaGetLastError());
+    if (sort_err) return fail(RKHSBA_ETIMEOUT, "a bounded wait of the radix sort gave up");
     if (loss) *loss = -F;
     if (grad) {
         const double scale = p.sigma * p.sigma / (p.ell * p.ell);

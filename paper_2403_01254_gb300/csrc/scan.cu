@@ -1,208 +1,190 @@
-// Device-wide exclusive scan (int64) and a stable LSD radix sort (uint32 keys,
-// int32 payload).  Both are the plumbing of the grid build (Sec. VI-time
-// analysis: the pair sum needs a spatial index; the paper names GPU voxel
-// hashing as future work) and of the per-evaluation query binning.
+// Stable LSD radix sort of uint32 keys with an int32 payload: the plumbing of
+// the grid build (points by cell) and of the per-evaluation query binning
+// (queries by home cell).  The pair sum needs a spatial index (the paper
+// names GPU voxel hashing as future work); this one is rebuilt by sorting.
+//
+// One counting kernel reads the keys once and histograms every 8-bit digit;
+// each pass is then a single kernel ("one sweep"): a block takes the next
+// tile of 2048 keys (tiles are handed out in order by an atomic counter),
+// ranks its keys stably (match.any inside a warp, per-warp digit counts
+// across warps, rounds of 256 keys in input order), publishes its per-digit
+// counts, and obtains the counts of all earlier tiles by looking back over
+// their published records (decoupled look-back): a record holds a flag
+// (aggregate of the tile / inclusive prefix up to the tile) and a count in
+// one 64-bit word.  Every wait is bounded; a wait that gives up sets an error
+// word and the kernel finishes with what it has.
 #include "common.cuh"
 
 namespace rk {
 
 namespace {
-constexpr int SCAN_T = 512;
-constexpr int SCAN_IPT = 8;
-constexpr int SCAN_TILE = SCAN_T * SCAN_IPT;     // 4096 items per block
-
 constexpr int RAD_T = 256;
 constexpr int RAD_IPT = 8;
-constexpr int RAD_TILE = RAD_T * RAD_IPT;        // 2048 items per block
+constexpr int RAD_TILE = RAD_T * RAD_IPT;        // 2048 keys per tile
 constexpr int RAD_WARPS = RAD_T / 32;
+constexpr int MAX_PASS = 4;
+constexpr unsigned long long ST_AGG = 1ull << 62;      // count = this tile's
+constexpr unsigned long long ST_PRE = 2ull << 62;      // count = tiles 0..t inclusive
+constexpr unsigned long long ST_CNT = (1ull << 62) - 1ull;
+constexpr int SPIN_LIMIT = 1 << 22;
 
-__device__ __forceinline__ long long warp_incl_scan(long long v, int lane) {
+__global__ void __launch_bounds__(RAD_T) k_radix_counts(const uint32_t* __restrict__ keys, long long n,
+                                                        int npass, unsigned long long* __restrict__ counts) {
+    __shared__ int c[MAX_PASS][256];
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        long long u = __shfl_up_sync(0xffffffffu, v, o);
-        if (lane >= o) v += u;
-    }
-    return v;
-}
-
-// exclusive scan of one value per thread over the block; returns the block total
-template <int T>
-__device__ __forceinline__ long long block_excl_scan(long long v, long long* s_warp, long long& total) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    long long inc = warp_incl_scan(v, lane);
-    if (lane == 31) s_warp[warp] = inc;
-    __syncthreads();
-    if (warp == 0) {
-        long long w = lane < T / 32 ? s_warp[lane] : 0;
-        long long wi = warp_incl_scan(w, lane);
-        if (lane < T / 32) s_warp[lane] = wi - w;
-        if (lane == 31) s_warp[T / 32] = wi;
-    }
-    __syncthreads();
-    long long res = s_warp[warp] + inc - v;
-    total = s_warp[T / 32];
-    __syncthreads();
-    return res;
-}
-
-__global__ void __launch_bounds__(SCAN_T) k_scan_reduce(const long long* __restrict__ in, long long n,
-                                                        long long* __restrict__ bsum) {
-    __shared__ long long s_warp[SCAN_T / 32 + 1];
-    const long long base = (long long)blockIdx.x * SCAN_TILE;
-    long long s = 0;
-#pragma unroll
-    for (int k = 0; k < SCAN_IPT; ++k) {
-        long long i = base + (long long)k * SCAN_T + threadIdx.x;
-        if (i < n) s += in[i];
-    }
-    long long tot;
-    block_excl_scan<SCAN_T>(s, s_warp, tot);
-    if (threadIdx.x == 0) bsum[blockIdx.x] = tot;
-}
-
-// single block: exclusive scan of the block sums in place, total to *total
-__global__ void __launch_bounds__(1024) k_scan_top(long long* bsum, long long nb, long long* total) {
-    __shared__ long long s_warp[1024 / 32 + 1];
-    __shared__ long long s_carry;
-    if (threadIdx.x == 0) s_carry = 0;
-    __syncthreads();
-    for (long long base = 0; base < nb; base += 1024) {
-        long long i = base + threadIdx.x;
-        long long v = i < nb ? bsum[i] : 0;
-        long long tot;
-        long long ex = block_excl_scan<1024>(v, s_warp, tot);
-        if (i < nb) bsum[i] = ex + s_carry;
-        __syncthreads();
-        if (threadIdx.x == 0) s_carry += tot;
-        __syncthreads();
-    }
-    if (threadIdx.x == 0 && total) *total = s_carry;
-}
-
-__global__ void __launch_bounds__(SCAN_T) k_scan_down(const long long* in, long long* out, long long n,
-                                                      const long long* __restrict__ boff) {
-    __shared__ long long tile[SCAN_TILE];
-    __shared__ long long s_warp[SCAN_T / 32 + 1];
-    const long long base = (long long)blockIdx.x * SCAN_TILE;
-#pragma unroll
-    for (int k = 0; k < SCAN_IPT; ++k) {
-        long long i = base + (long long)k * SCAN_T + threadIdx.x;
-        tile[k * SCAN_T + threadIdx.x] = i < n ? in[i] : 0;
-    }
-    __syncthreads();
-    long long loc[SCAN_IPT];
-    long long s = 0;
-#pragma unroll
-    for (int k = 0; k < SCAN_IPT; ++k) {
-        loc[k] = s;
-        s += tile[threadIdx.x * SCAN_IPT + k];
-    }
-    long long tot;
-    long long ex = block_excl_scan<SCAN_T>(s, s_warp, tot) + boff[blockIdx.x];
-#pragma unroll
-    for (int k = 0; k < SCAN_IPT; ++k) tile[threadIdx.x * SCAN_IPT + k] = ex + loc[k];
-    __syncthreads();
-#pragma unroll
-    for (int k = 0; k < SCAN_IPT; ++k) {
-        long long i = base + (long long)k * SCAN_T + threadIdx.x;
-        if (i < n) out[i] = tile[k * SCAN_T + threadIdx.x];
-    }
-}
-
-__global__ void __launch_bounds__(RAD_T) k_radix_hist(const uint32_t* __restrict__ keys, long long n,
-                                                      int shift, long long* __restrict__ hist, int nb) {
-    __shared__ int cnt[256];
-    cnt[threadIdx.x] = 0;
+    for (int p = 0; p < MAX_PASS; ++p) c[p][threadIdx.x] = 0;
     __syncthreads();
     const long long base = (long long)blockIdx.x * RAD_TILE;
 #pragma unroll
     for (int k = 0; k < RAD_IPT; ++k) {
-        long long i = base + (long long)k * RAD_T + threadIdx.x;
-        if (i < n) atomicAdd(&cnt[(keys[i] >> shift) & 255u], 1);
+        const long long i = base + (long long)k * RAD_T + threadIdx.x;
+        if (i < n) {
+            const uint32_t key = keys[i];
+            for (int p = 0; p < npass; ++p) atomicAdd(&c[p][(key >> (8 * p)) & 255u], 1);
+        }
     }
     __syncthreads();
-    hist[(long long)threadIdx.x * nb + blockIdx.x] = cnt[threadIdx.x];
+    for (int p = 0; p < npass; ++p)
+        if (c[p][threadIdx.x]) atomicAdd(&counts[256 * p + threadIdx.x], (unsigned long long)c[p][threadIdx.x]);
 }
 
-// Stable scatter: items are taken in input order in rounds of 256; inside a
-// round the rank of an item among equal digits counts lower lanes of its warp
-// (match.any) plus the equal digits of lower warps.
-__global__ void __launch_bounds__(RAD_T) k_radix_scatter(const uint32_t* __restrict__ kin,
-                                                         const int* __restrict__ vin,
-                                                         uint32_t* __restrict__ kout,
-                                                         int* __restrict__ vout, long long n, int shift,
-                                                         const long long* __restrict__ hist, int nb) {
-    __shared__ long long run[256];
-    __shared__ int wcnt[RAD_WARPS][256];
+// exclusive scan of one value per thread over a 256-thread block
+__device__ __forceinline__ long long block_excl_scan256(long long v, long long* s_warp) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    run[threadIdx.x] = hist[(long long)threadIdx.x * nb + blockIdx.x];
-    const unsigned lt = (1u << lane) - 1u;
-    const long long base = (long long)blockIdx.x * RAD_TILE;
-    for (int r = 0; r < RAD_IPT; ++r) {
+    long long inc = v;
 #pragma unroll
-        for (int w = 0; w < RAD_WARPS; ++w) wcnt[w][threadIdx.x] = 0;
+    for (int o = 1; o < 32; o <<= 1) {
+        const long long u = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += u;
+    }
+    if (lane == 31) s_warp[warp] = inc;
+    __syncthreads();
+    long long before = 0;
+    for (int w = 0; w < warp; ++w) before += s_warp[w];
+    __syncthreads();
+    return before + inc - v;
+}
+
+__global__ void __launch_bounds__(RAD_T) k_onesweep(const uint32_t* __restrict__ kin,
+                                                    const int* __restrict__ vin,
+                                                    uint32_t* __restrict__ kout, int* __restrict__ vout,
+                                                    long long n, int shift,
+                                                    const unsigned long long* __restrict__ counts,
+                                                    unsigned long long* status, int* tile_ctr, int* err) {
+    __shared__ int s_tile;
+    __shared__ int run[256];
+    __shared__ int wcnt[RAD_WARPS][256];
+    __shared__ long long s_base[256];
+    __shared__ long long s_warp[RAD_WARPS];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) s_tile = atomicAdd(tile_ctr, 1);
+    run[tid] = 0;
+#pragma unroll
+    for (int w = 0; w < RAD_WARPS; ++w) wcnt[w][tid] = 0;
+    __syncthreads();
+    const int t = s_tile;
+    const long long base = (long long)t * RAD_TILE;
+    const unsigned lt = (1u << lane) - 1u;
+    uint32_t key[RAD_IPT];
+    int val[RAD_IPT], dig[RAD_IPT], rank[RAD_IPT];
+    // stable ranks inside the tile: round r holds keys base + 256 r + tid
+#pragma unroll
+    for (int r = 0; r < RAD_IPT; ++r) {
+        const long long i = base + (long long)r * RAD_T + tid;
+        const bool valid = i < n;
+        key[r] = valid ? kin[i] : 0u;
+        val[r] = valid ? vin[i] : 0;
+        const int d = valid ? (int)((key[r] >> shift) & 255u) : 256;
+        dig[r] = d;
+        const unsigned peers = __match_any_sync(0xffffffffu, d);
+        const int lr = __popc(peers & lt);
+        if (valid && lr == 0) wcnt[warp][d] = __popc(peers);
         __syncthreads();
-        long long i = base + (long long)r * RAD_T + threadIdx.x;
-        bool valid = i < n;
-        uint32_t key = valid ? kin[i] : 0u;
-        int digit = valid ? (int)((key >> shift) & 255u) : 256;
-        unsigned peers = __match_any_sync(0xffffffffu, digit);
-        int rank = __popc(peers & lt);
-        if (valid && (peers & lt) == 0) wcnt[warp][digit] = __popc(peers);
-        __syncthreads();
+        rank[r] = 0;
         if (valid) {
-            long long off = run[digit] + rank;
-            for (int w = 0; w < warp; ++w) off += wcnt[w][digit];
-            kout[off] = key;
-            vout[off] = vin[i];
+            int off = run[d] + lr;
+            for (int w = 0; w < warp; ++w) off += wcnt[w][d];
+            rank[r] = off;
         }
         __syncthreads();
-        long long add = 0;
+        int add = 0;
 #pragma unroll
-        for (int w = 0; w < RAD_WARPS; ++w) add += wcnt[w][threadIdx.x];
-        run[threadIdx.x] += add;
+        for (int w = 0; w < RAD_WARPS; ++w) {
+            add += wcnt[w][tid];
+            wcnt[w][tid] = 0;
+        }
+        run[tid] += add;
         __syncthreads();
+    }
+    // publish this tile's count of digit tid, then look back for the prefix
+    const int d = tid;
+    const long long cnt = run[d];
+    volatile unsigned long long* st = status + (long long)t * 256 + d;
+    long long excl = 0;
+    if (t == 0) {
+        *st = ST_PRE | (unsigned long long)cnt;
+    } else {
+        *st = ST_AGG | (unsigned long long)cnt;
+        bool gave_up = false;
+        for (int p = t - 1; p >= 0 && !gave_up; --p) {
+            volatile unsigned long long* sp = status + (long long)p * 256 + d;
+            unsigned long long v = *sp;
+            int spins = 0;
+            while ((v >> 62) == 0ull) {
+                if (++spins > SPIN_LIMIT) {   // give up: the prefix stays short, writes stay in bounds
+                    atomicOr(err, 1);
+                    gave_up = true;
+                    break;
+                }
+                __nanosleep(32);
+                v = *sp;
+            }
+            excl += (long long)(v & ST_CNT);
+            if ((v >> 62) == 2ull) break;
+        }
+        *st = ST_PRE | (unsigned long long)(excl + cnt);
+    }
+    s_base[d] = block_excl_scan256((long long)counts[d], s_warp) + excl;
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < RAD_IPT; ++r) {
+        const long long i = base + (long long)r * RAD_T + tid;
+        if (i < n) {
+            const long long o = s_base[dig[r]] + rank[r];
+            kout[o] = key[r];
+            vout[o] = val[r];
+        }
     }
 }
 }  // namespace
 
-size_t scan_ws_elems(long long n) {
-    long long nb = (n + SCAN_TILE - 1) / SCAN_TILE;
-    return (size_t)(nb + 2);
-}
-
-void scan_exclusive_i64(const long long* in, long long* out, long long n, long long* total,
-                        long long* ws, cudaStream_t st) {
-    if (n <= 0) {
-        if (total) cudaMemsetAsync(total, 0, sizeof(long long), st);
-        return;
-    }
-    long long nb = (n + SCAN_TILE - 1) / SCAN_TILE;
-    k_scan_reduce<<<(unsigned)nb, SCAN_T, 0, st>>>(in, n, ws);
-    k_scan_top<<<1, 1024, 0, st>>>(ws, nb, total);
-    k_scan_down<<<(unsigned)nb, SCAN_T, 0, st>>>(in, out, n, ws);
-    count_launch(3);
-}
+size_t scan_ws_elems(long long) { return (size_t)(MAX_PASS * 256 + 2 * MAX_PASS); }
 
 size_t radix_hist_elems(long long n) {
-    long long nb = (n + RAD_TILE - 1) / RAD_TILE;
-    return (size_t)(256 * (nb > 0 ? nb : 1));
+    const long long nb = (n + RAD_TILE - 1) / RAD_TILE;
+    return (size_t)(MAX_PASS * 256 * (nb > 0 ? nb : 1));
 }
 
 void radix_sort_u32(uint32_t* keys, int* vals, uint32_t* keys_alt, int* vals_alt, long long n,
-                    int nbits, long long* hist, long long* ws, cudaStream_t st, bool* in_alt) {
+                    int nbits, long long* hist, long long* ws, int* err, cudaStream_t st, bool* in_alt) {
     *in_alt = false;
-    if (n <= 0) return;
+    if (n <= 0 || nbits <= 0) return;
     const int nb = (int)((n + RAD_TILE - 1) / RAD_TILE);
+    const int npass = (nbits + 7) / 8;
+    unsigned long long* status = reinterpret_cast<unsigned long long*>(hist);
+    unsigned long long* counts = reinterpret_cast<unsigned long long*>(ws);
+    int* ctr = reinterpret_cast<int*>(ws + MAX_PASS * 256);
+    cudaMemsetAsync(status, 0, sizeof(unsigned long long) * 256 * (size_t)nb * npass, st);
+    cudaMemsetAsync(ws, 0, sizeof(long long) * scan_ws_elems(n), st);
+    k_radix_counts<<<nb, RAD_T, 0, st>>>(keys, n, npass, counts);
+    count_launch();
     uint32_t* ki = keys;
     int* vi = vals;
     uint32_t* ko = keys_alt;
     int* vo = vals_alt;
-    for (int shift = 0; shift < nbits; shift += 8) {
-        k_radix_hist<<<nb, RAD_T, 0, st>>>(ki, n, shift, hist, nb);
-        count_launch();
-        scan_exclusive_i64(hist, hist, 256LL * nb, nullptr, ws, st);
-        k_radix_scatter<<<nb, RAD_T, 0, st>>>(ki, vi, ko, vo, n, shift, hist, nb);
+    for (int p = 0; p < npass; ++p) {
+        k_onesweep<<<nb, RAD_T, 0, st>>>(ki, vi, ko, vo, n, 8 * p, counts + 256 * p,
+                                         status + (size_t)256 * nb * p, ctr + p, err);
         count_launch();
         uint32_t* tk = ki; ki = ko; ko = tk;
         int* tv = vi; vi = vo; vo = tv;
