@@ -346,6 +346,9 @@ def ours(args, rank, world, local_rank):
     serve = None
     if rank == 0 and world == 1 and not args.no_serving and args.workload == WORKLOAD:
         serve = serving(pk)
+    funcs = None
+    if rank == 0 and world == 1 and not args.no_functions and args.workload == WORKLOAD:
+        funcs = function_space(pk, prob)
 
     if rank == 0:
         line = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps,
@@ -358,8 +361,72 @@ def ours(args, rank, world, local_rank):
                                 step="grid build + evaluation + one LM iteration (2 evaluations)",
                                 parallelism="replicas" if world > 1 else "single GPU"),
                     roofline=roofline, cpu_baseline=cpu_base, e2e=e2e, gpu_launches=int(n_launch),
-                    clocks=clk, serving=serve)
+                    clocks=clk, serving=serve, functions=funcs)
         print(json.dumps(line), flush=True)
+
+
+def function_space(pk, prob):
+    """Latency of the function-space calls (host wall time around the
+    synchronous C-ABI calls, median of repeats):
+      - two-view global registration of Sec. VI-A on the object-pair scene
+        (90 deg about a random axis, 0.5 m, 12.5% outliers and cropping, part
+        labels) at 1000-8000 points per scan: the 60-rotation search, and the
+        search followed by the LM solve at ell = 0.1, 0.05, 0.03;
+      - inner products, distances and cosines of every edge of the bench
+        workload (the self terms cached after the first call);
+      - the lengthscale-decay loop on a 4-frame x 5000-point LiDAR problem."""
+    import scenes
+
+    def med(f, reps):
+        ts = []
+        for _ in range(reps):
+            t0 = time.perf_counter()
+            out = f()
+            ts.append(time.perf_counter() - t0)
+        return 1e3 * float(np.median(ts)), out
+
+    reg = []
+    for n in (1000, 2000, 4000, 8000):
+        p = scenes.object_pair_problem(seed=300 + n, angle_deg=90.0, n=n, outlier_ratio=0.125, crop_ratio=0.125,
+                                       ell=0.1, labels=True)
+        g = pk.Problem.from_scene(p)
+        try:
+            g.rotation_search(0, 1, p["poses0"])
+            ms_search, out = med(lambda: g.rotation_search(0, 1, p["poses0"]), 5)
+        finally:
+            g.close()
+
+        def full():
+            T = np.stack([np.eye(4), out["best_pose"]])
+            for ell in (0.1, 0.05, 0.03):
+                h = pk.Problem.from_scene(p, ell=ell, max_iters=40)
+                try:
+                    T, _ = h.solve(T)
+                finally:
+                    h.close()
+            return T
+        ms_full, T = med(full, 3)
+        E = np.linalg.inv(p["poses_gt"][1]) @ T[1]
+        rot_err = float(np.arccos(np.clip((np.trace(E[:3, :3]) - 1) / 2, -1, 1)))
+        reg.append(dict(points=n, search_ms=ms_search, search_plus_lm_ms=ms_full, rot_err_rad=rot_err))
+
+    g = pk.Problem.from_scene(prob)
+    try:
+        g.inner_products(prob["poses0"])
+        ms_ip, _ = med(lambda: g.inner_products(prob["poses0"]), 10)
+    finally:
+        g.close()
+    small = scenes.lidar_street_problem(seed=1435, n_frames=4, n_points=5000)
+    g = pk.Problem.from_scene(small, max_iters=30)
+    try:
+        ms_decay, (T, info) = med(lambda: g.solve_ell_decay(small["poses0"], decay=0.2, ell_min=0.1,
+                                                              max_outer=5), 3)
+    finally:
+        g.close()
+    return dict(two_view_registration=reg, inner_products_ms=ms_ip,
+                ell_decay=dict(problem="lidar 4x5000", ms=ms_decay, levels=info["levels"],
+                               ell=[float(x) for x in info["ell"]]),
+                timing="host wall time around synchronous calls, median")
 
 
 def serving(pk, seed=1634, n_requests=200, pool_size=8, max_iters=30, load_factor=0.8):
@@ -485,6 +552,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-functions", action="store_true")
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(WORKLOADS),
                     help="other workloads of the paper's shapes (the driver uses the default)")
     ap.add_argument("--oracle-sample", default=None)

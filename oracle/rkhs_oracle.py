@@ -30,6 +30,10 @@ Readings of points the paper leaves open (each also listed in the design doc):
     J_b = -R_b [I | -[y_j]x]  (rho first, then phi, per the wedge).
   * RKHS distance |f_a - f_b|^2 = <f_a,f_a> + <f_b,f_b> - 2 <f_a,f_b> with the
     same sparse sums (Eq. dist_rkhs); cosine <f_a,f_b> / (|f_a| |f_b|).
+  * Variants (Sec. VI time analysis, Sec. VII), off by default: pairs whose
+    semantic kernel <l_i, l_j> is below sem_min are dropped; with top_k > 0
+    every point of an edge's second frame keeps only its top_k pairs of
+    largest w (ties: smaller index first).
   * Lengthscale decay (Sec. V-C): ell <- ell (1 + decay sign(dD/dell)) after
     each inner solve; stop when an inner solve accepts no step.
   * Rotation search (Sec. IV-A): candidate k places frame b at
@@ -52,12 +56,12 @@ from scipy.spatial import cKDTree
 __all__ = [
     "DEFAULTS", "hat", "wedge", "se3_exp", "se3_log", "pose_error",
     "label_weights", "pairs_bruteforce", "pairs_kdtree", "edge_terms",
-    "evaluate", "lm_solve", "irls_frozen_solve", "edge_pairs", "inner_product", "self_inner",
+    "evaluate", "lm_solve", "irls_frozen_solve", "edge_pairs", "select_pairs", "inner_product", "self_inner",
     "distance_and_cosine", "ell_decay_solve", "icosahedral_rotations", "rotation_search",
 ]
 
 DEFAULTS = dict(ell=0.1, cutoff_mult=3.0, sigma=1.0, ell_color=0.0, sem_bf16=0,
-                max_iters=100, lambda0=1e-4, tol_step=1e-10, tol_rel_f=1e-12)
+                max_iters=100, lambda0=1e-4, tol_step=1e-10, tol_rel_f=1e-12, top_k=0, sem_min=0.0)
 
 
 def _params(p):
@@ -239,6 +243,9 @@ def edge_terms(xa, xb, Ta, Tb, sem_a=None, sem_b=None, rgb_a=None, rgb_b=None,
     p = _transform(Ta, xa)          # T_a x_i
     q = _transform(Tb, xb)          # T_b y_j
     i, j = enumerate_pairs(p, q, rc)
+    if P["sem_min"] > 0 or P["top_k"] > 0:
+        keep = select_pairs(p, q, i, j, sem_a, sem_b, rgb_a, rgb_b, P)
+        i, j = i[keep], j[keep]
     out = dict(F=0.0, E=0.0, n_pairs=int(len(i)), b=np.zeros(12), H=np.zeros((12, 12)),
                W=0.0)
     Ra, Rb = Ta[:3, :3], Tb[:3, :3]
@@ -265,6 +272,31 @@ def edge_terms(xa, xb, Ta, Tb, sem_a=None, sem_b=None, rgb_a=None, rgb_b=None,
         Jf = J.reshape(-1, 12)
         out["H"] += (Jf * np.repeat(w, 3)[:, None]).T @ Jf
     return out
+
+
+def select_pairs(p, q, i, j, sem_a, sem_b, rgb_a, rgb_b, P):
+    """Variants of the sparse sum (Sec. VI time analysis, Sec. VII): drop the
+    pairs whose semantic kernel <l_i, l_j> is below sem_min, then keep for
+    every point j of the edge's second frame only the top_k pairs with the
+    largest weight w (ties: smaller i first).  Returns a boolean mask."""
+    keep = np.ones(len(i), dtype=bool)
+    if P["sem_min"] > 0 and sem_a is not None:
+        la = np.asarray(sem_a, dtype=np.float64)[i]
+        lb = np.asarray(sem_b, dtype=np.float64)[j]
+        keep &= np.einsum("nk,nk->n", la, lb) >= P["sem_min"]
+    if P["top_k"] > 0 and len(i):
+        d = p[i] - q[j]
+        w = label_weights(sem_a, sem_b, rgb_a, rgb_b, i, j, P["ell_color"]) * \
+            np.exp(-np.einsum("nk,nk->n", d, d) / (2.0 * P["ell"] ** 2))
+        idx = np.nonzero(keep)[0]
+        order = idx[np.lexsort((i[idx], -w[idx], j[idx]))]       # by j, then w descending, then i
+        jj = j[order]
+        first = np.r_[True, jj[1:] != jj[:-1]]
+        start = np.maximum.accumulate(np.where(first, np.arange(len(jj)), 0))
+        rank = np.arange(len(jj)) - start
+        keep[:] = False
+        keep[order[rank < P["top_k"]]] = True
+    return keep
 
 
 def edge_pairs(problem, poses, e, enumerate_pairs=pairs_kdtree):
