@@ -374,6 +374,8 @@ def function_space(pk, prob):
         search followed by the LM solve at ell = 0.1, 0.05, 0.03;
       - inner products, distances and cosines of every edge of the bench
         workload (the self terms cached after the first call);
+      - one evaluation of the bench workload with the top-8 neighbour limit
+        and with semantic pruning at 0.1;
       - the lengthscale-decay loop on a 4-frame x 5000-point LiDAR problem."""
     import scenes
 
@@ -416,6 +418,15 @@ def function_space(pk, prob):
         ms_ip, _ = med(lambda: g.inner_products(prob["poses0"]), 10)
     finally:
         g.close()
+    variants = {}
+    for name, over in (("top_8", dict(top_k=8)), ("sem_min_0.1", dict(sem_min=0.1))):
+        g = pk.Problem.from_scene(prob, **over)
+        try:
+            g.eval(prob["poses0"], want_H=False)
+            ms_v, out_v = med(lambda: g.eval(prob["poses0"], want_H=False), 5)
+        finally:
+            g.close()
+        variants[name] = dict(eval_ms=ms_v, pair_terms=int(out_v["n_pairs"]))
     small = scenes.lidar_street_problem(seed=1435, n_frames=4, n_points=5000)
     g = pk.Problem.from_scene(small, max_iters=30)
     try:
@@ -423,7 +434,7 @@ def function_space(pk, prob):
                                                               max_outer=5), 3)
     finally:
         g.close()
-    return dict(two_view_registration=reg, inner_products_ms=ms_ip,
+    return dict(two_view_registration=reg, inner_products_ms=ms_ip, sparse_sum_variants=variants,
                 ell_decay=dict(problem="lidar 4x5000", ms=ms_decay, levels=info["levels"],
                                ell=[float(x) for x in info["ell"]]),
                 timing="host wall time around synchronous calls, median")

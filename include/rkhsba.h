@@ -69,10 +69,16 @@ typedef struct {
     int32_t sem_dim;     /* floats per label vector, 0..32; 0 = no labels */
     int32_t sem_bf16;    /* 1: keep labels on the device as bfloat16 (rounded) */
     int32_t max_iters;   /* LM evaluations after the first (default 100) */
-    int32_t reserved;    /* must be 0 */
+    int32_t top_k;       /* 0: every pair inside r_c (default).  1..8: for every point
+                            of an edge's second frame only the top_k pairs of largest
+                            w count (the 8-neighbour variant of Sec. VI, time
+                            analysis; ties: the candidate met first in the
+                            grid's cell order) */
     double lambda0;      /* initial LM damping (default 1e-4) */
     double tol_step;     /* stop when an accepted step has |delta|_inf below (1e-10) */
     double tol_rel_f;    /* stop when an accepted step gains less than this relative F (1e-12) */
+    double sem_min;      /* > 0: drop pairs whose semantic kernel <l_i, l_j> is below
+                            sem_min (the semantic pruning of Sec. VII); 0: off */
 } rkhsba_params;
 
 typedef struct {
@@ -271,7 +277,7 @@ rkhsba_status rkhsba_rotation_search(rkhsba_ctx* ctx, int32_t a, int32_t b, cons
 /* Lengthscale decay (Sec. V-C): an outer loop over ell around the LM solve.
  * Level t solves the poses at ell_t (rkhsba_solve's loop, from the previous
  * level's poses), then sets
- *   ell_{t+1} = max(ell_min, ell_t (1 + decay * sign(dD/dell)))
+ *   ell_{t+1} = max(ell_min, ell_t (1 - decay * sign(dD/dell)))
  * with dD/dell as in rkhsba_inner_products at the solved poses.  The loop ends
  * when a level accepts no LM step (the objective at that ell stopped
  * increasing), when ell stops changing, or after max_outer levels.  ctx keeps

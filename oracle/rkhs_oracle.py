@@ -34,7 +34,7 @@ Readings of points the paper leaves open (each also listed in the design doc):
     semantic kernel <l_i, l_j> is below sem_min are dropped; with top_k > 0
     every point of an edge's second frame keeps only its top_k pairs of
     largest w (ties: smaller index first).
-  * Lengthscale decay (Sec. V-C): ell <- ell (1 + decay sign(dD/dell)) after
+  * Lengthscale decay (Sec. V-C): ell <- ell (1 - decay sign(dD/dell)) after
     each inner solve; stop when an inner solve accepts no step.
   * Rotation search (Sec. IV-A): candidate k places frame b at
     T_a [R_k | mu_a - R_k mu_b] (frame centroids aligned; the paper leaves the
@@ -494,7 +494,7 @@ def distance_and_cosine(problem, poses, params=None):
 
 def ell_decay_solve(problem, poses0=None, params=None, decay=0.1, ell_min=0.0, max_outer=10):
     """Inner-outer loop of Sec. V-C.  Inner: the LM pose solve at fixed ell.
-    Outer: ell <- ell (1 + decay * sign(dD/dell)), D the summed edge distance
+    Outer: ell <- ell (1 - decay * sign(dD/dell)), D the summed edge distance
     of Eq. dist_rkhs at the solved poses, floored at ell_min.  The loop ends
     when an inner solve accepts no step (the original objective stops
     increasing), when ell stops changing, or after max_outer levels."""
@@ -513,7 +513,7 @@ def ell_decay_solve(problem, poses0=None, params=None, decay=0.1, ell_min=0.0, m
         levels.append(dict(ell=ell, F=r["F"], iters=r["iters"], accepted=accepted, dD_dell=g))
         if accepted == 0:
             break
-        nxt = max(ell * (1.0 + decay * float(np.sign(g))), ell_min)
+        nxt = max(ell * (1.0 - decay * float(np.sign(g))), ell_min)
         if nxt == ell:
             break
         ell = nxt

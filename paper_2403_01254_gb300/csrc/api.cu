@@ -84,7 +84,9 @@ rkhsba_status normalize_params(rkhsba_ctx* ctx, const rkhsba_params* in) {
     if (p.lambda0 == 0.0) p.lambda0 = 1e-4;
     if (p.tol_step == 0.0) p.tol_step = 1e-10;
     if (p.tol_rel_f == 0.0) p.tol_rel_f = 1e-12;
-    if (p.reserved != 0) return fail(ctx, RKHSBA_EINVAL, "params.reserved must be 0");
+    if (p.top_k < 0 || p.top_k > TOPK_MAX) return fail(ctx, RKHSBA_EINVAL, "params.top_k must be in [0, 8]");
+    if (!(p.sem_min >= 0.0) || !std::isfinite(p.sem_min))
+        return fail(ctx, RKHSBA_EINVAL, "params.sem_min must be finite and >= 0");
     ctx->p = p;
     const double rc = p.cutoff_mult * p.ell;
     GridParams& g = ctx->gp;
@@ -101,6 +103,8 @@ rkhsba_status normalize_params(rkhsba_ctx* ctx, const rkhsba_params* in) {
     g.sem_dim = p.sem_dim;
     g.sem_bf16 = p.sem_bf16 ? 1 : 0;
     g.sem_pad = sem_pad_for(p.sem_dim, g.sem_bf16);
+    g.top_k = p.top_k;
+    g.sem_min = (p.sem_min > 0.0 && p.sem_dim > 0) ? (float)p.sem_min : -__builtin_huge_valf();
     if (p.sem_dim > 0 && g.sem_pad == 0) return fail(ctx, RKHSBA_EINVAL, "unsupported sem_dim");
     return RKHSBA_OK;
 }

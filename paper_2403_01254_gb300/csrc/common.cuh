@@ -95,7 +95,11 @@ struct GridParams {
     float kg;             // -log2(e) / (2 ell^2)
     float kc;             // -log2(e) / (2 ell_c^2), 0 without colour
     int sem_dim, sem_pad, sem_bf16, color;
+    int top_k;            // 0: every pair; else the top_k pairs of largest w per query
+    float sem_min;        // pairs with <l_i, l_j> below this are dropped (-inf: off)
 };
+
+constexpr int TOPK_MAX = 8;   // largest top_k of the neighbour-limited variant
 
 struct LMState {
     double lambda;

@@ -419,7 +419,7 @@ rkhsba_status rkhsba_solve_ell_decay(rkhsba_ctx* c, const rkhsba_ell_schedule* s
         out.pair_terms += si.pair_terms;
         if (s.n_accepted == 0) break;
         const double sgn = g > 0.0 ? 1.0 : (g < 0.0 ? -1.0 : 0.0);
-        const double nxt = std::max(ell * (1.0 + sched->decay * sgn), sched->ell_min);
+        const double nxt = std::max(ell * (1.0 - sched->decay * sgn), sched->ell_min);
         if (!(nxt > 0.0)) break;
         if (nxt == ell) break;
         ell = nxt;

@@ -176,6 +176,11 @@ extern "C" rkhsba_status rkhsba_eval_static(int32_t n_frames, const int64_t* n_p
     gp.sem_bf16 = p.sem_bf16 ? 1 : 0;
     gp.sem_pad = pad_for(p.sem_dim, gp.sem_bf16);
     if (p.sem_dim > 0 && gp.sem_pad == 0) return fail(RKHSBA_EINVAL, "unsupported sem_dim");
+    if (p.top_k < 0 || p.top_k > TOPK_MAX) return fail(RKHSBA_EINVAL, "params.top_k must be in [0, 8]");
+    if (!(p.sem_min >= 0.0) || !std::isfinite(p.sem_min))
+        return fail(RKHSBA_EINVAL, "params.sem_min must be finite and >= 0");
+    gp.top_k = p.top_k;
+    gp.sem_min = (p.sem_min > 0.0 && p.sem_dim > 0) ? (float)p.sem_min : -__builtin_huge_valf();
 
     unsigned char* base = nullptr;
     rkhsba_status st0 = scratch_base(&base);

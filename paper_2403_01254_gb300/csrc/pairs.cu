@@ -467,6 +467,54 @@ __device__ __forceinline__ void reduce_half(long long (&v)[32], int lane) {
     }
 }
 
+// Unit end, shared by the pair kernels: the lane's moments about the home
+// cell centre move to frame-a coordinates (y' += o), are rounded to 64-bit
+// fixed point and reduce-scattered over the warp (lane k ends with the warp
+// total of moment k), and added to the edge's accumulators with one integer
+// atomic per moment.
+__device__ __forceinline__ void store_moments(float W, const float (&Dv)[3], float (&Sy)[3], float (&Myy)[6],
+                                              float (&Mdy)[9], const float* Qm, int cnt, const FrameDev& Fa,
+                                              int hx, int hy, int hz, const GridParams& gp,
+                                              const float* __restrict__ scl, long long* __restrict__ acc_e,
+                                              int lane) {
+    const float o[3] = {((float)(hx + Fa.lo[0]) + 0.5f) * gp.hf, ((float)(hy + Fa.lo[1]) + 0.5f) * gp.hf,
+                        ((float)(hz + Fa.lo[2]) + 0.5f) * gp.hf};
+    {
+        int t6 = 0;
+#pragma unroll
+        for (int mm = 0; mm < 3; ++mm)
+#pragma unroll
+            for (int l = mm; l < 3; ++l, ++t6)
+                Myy[t6] += Sy[mm] * o[l] + o[mm] * Sy[l] + W * o[mm] * o[l];
+#pragma unroll
+        for (int mm = 0; mm < 3; ++mm)
+#pragma unroll
+            for (int l = 0; l < 3; ++l) Mdy[3 * mm + l] = fmaf(Dv[mm], o[l], Mdy[3 * mm + l]);
+#pragma unroll
+        for (int mm = 0; mm < 3; ++mm) Sy[mm] = fmaf(W, o[mm], Sy[mm]);
+    }
+    long long vals[32];
+#pragma unroll
+    for (int k = 0; k < 32; ++k) {
+        float val = 0.f;
+        if (k == 0) val = W;
+        else if (k < 4) val = Dv[k - 1];
+        else if (k < 7) val = Sy[k - 4];
+        else if (k < 13) val = Myy[k - 7];
+        else if (k < 22) val = Mdy[k - 13];
+        else if (k < 28) val = Qm[k - 22];
+        vals[k] = (k == N_MOM - 1) ? (long long)cnt
+                : (k < N_MOM ? to_fixed(val, __ldg(scl + moment_class(k))) : 0ll);
+    }
+    reduce_half<16>(vals, lane);
+    reduce_half<8>(vals, lane);
+    reduce_half<4>(vals, lane);
+    reduce_half<2>(vals, lane);
+    reduce_half<1>(vals, lane);
+    if (lane < N_MOM && vals[0] != 0)
+        atomicAdd(reinterpret_cast<unsigned long long*>(acc_e + lane), (unsigned long long)vals[0]);
+}
+
 template <int DP, bool BF16, bool COLOR>
 __global__ void __launch_bounds__(PAIR_T, RK_PAIR_MINB)
 k_pairs(const int* __restrict__ unit_start, const int* __restrict__ n_units, int* unit_counter,
@@ -630,7 +678,8 @@ k_pairs(const int* __restrict__ unit_start, const int* __restrict__ n_units, int
                         arg = fmaf(fmaf(cr, cr, fmaf(cg, cg, cb * cb)), gp.kc, arg);
                     }
                     const float s = SemRow<DP, BF16>::dot(cs, ssq + j * SW);
-                    const float w = s * ex2_approx(arg);
+                    const bool kept = s >= gp.sem_min;                  // semantic pruning (off: -inf)
+                    const float w = kept ? s * ex2_approx(arg) : 0.f;
                     const u64 WXY = fmul2(f2(w, w), E01);                // (w ex, w ey)
                     const float wz = w * ez;
                     w0 += w;
@@ -640,7 +689,7 @@ k_pairs(const int* __restrict__ unit_start, const int* __restrict__ n_units, int
                     Q0201 = ffma2(WXY, E20, Q0201);                      // (q02, q01)
                     q12 = fmaf(f2_split(WXY).y, ez, q12);
                     q22 = fmaf(wz, ez, q22);
-                    ++cnt;
+                    cnt += kept ? 1 : 0;
                 }
             }
             const float2 dxy = f2_split(D01), q0011 = f2_split(Q0011), q0201 = f2_split(Q0201);
@@ -704,47 +753,189 @@ k_pairs(const int* __restrict__ unit_start, const int* __restrict__ n_units, int
                                          : (l == 0 ? mm : (l == 1 ? 2 + mm : 5));
                 Mdy[3 * mm + l] = Sxd[3 * l + mm] - Qm[qi];
             }
-        // home-centre coordinates -> frame-a coordinates: y' += o
-        const float o[3] = {((float)(hx + Fa.lo[0]) + 0.5f) * gp.hf, ((float)(hy + Fa.lo[1]) + 0.5f) * gp.hf,
-                            ((float)(hz + Fa.lo[2]) + 0.5f) * gp.hf};
-        {
-            int t6 = 0;
+        store_moments(W, Dv, Sy, Myy, Mdy, Qm, cnt, Fa, hx, hy, hz, gp, edges[e].scale,
+                      acc + (long long)e * ACC_N, lane);
+    }
+}
+
+// Neighbour-limited variant (top_k > 0): the same candidate stream, cutoff
+// test and weight, with lanes over the unit's queries.  Each lane keeps the
+// TOPK_MAX pairs of largest w of its query (candidates broadcast from shared
+// memory in stream order; a later candidate displaces only a strictly smaller
+// w), then sums its first top_k: W, D = sum w d, Q = sum w d d^T, and with
+// y' the query itself sum w y' = W y, sum w y'y'^T = W y y^T,
+// sum w d y'^T = D y^T.
+template <int DP, bool BF16, bool COLOR>
+__host__ __device__ constexpr int warp_smem_words_topk() {
+    return 32 * 4 + 32 * SemRow<DP, BF16>::WORDS + (COLOR ? 32 * 4 : 0) + 4 * CQ_N + 4 * 10;
+}
+
+template <int DP, bool BF16, bool COLOR>
+__global__ void __launch_bounds__(PAIR_T, 2)
+k_pairs_topk(const int* __restrict__ unit_start, const int* __restrict__ n_units, int* unit_counter,
+             const uint32_t* __restrict__ qkey, const float4* __restrict__ slots, long long Q,
+             const EdgeDev* __restrict__ edges, int E, const FrameDev* __restrict__ frames,
+             const int* __restrict__ cell_start, const float4* __restrict__ pts4,
+             const void* __restrict__ sem_sorted, const float4* __restrict__ col4, GridParams gp,
+             long long* __restrict__ acc, const int* done) {
+    if (done && *done) return;
+    extern __shared__ float4 smem4[];
+    constexpr int SW = SemRow<DP, BF16>::WORDS;
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    float* wb = reinterpret_cast<float*>(smem4) + warp * warp_smem_words_topk<DP, BF16, COLOR>();
+    float4* scx = reinterpret_cast<float4*>(wb);                      // [32] staged candidates (x, index)
+    float* srow = wb + 4 * 32;                                        // [32][SW] their label rows
+    float4* scc = reinterpret_cast<float4*>(srow + 32 * SW);          // [32] their colours
+    float4* cq = reinterpret_cast<float4*>(wb + 4 * 32 + 32 * SW + (COLOR ? 4 * 32 : 0));   // ring
+    int* ri = reinterpret_cast<int*>(cq + CQ_N);
+    const Rows R{ri, ri + 9, ri + 18, ri + 27};
+    const float NEG_INF = -__int_as_float(0x7f800000);
+    const int nu = *n_units;
+    for (;;) {
+        int u = 0;
+        if (lane == 0) u = atomicAdd(unit_counter, 1);
+        u = __shfl_sync(FULL, u, 0);
+        if (u >= nu) break;
+        const int k0 = unit_start[u];
+        const uint32_t key0 = qkey[k0];
+        const int qcount = unit_queries(qkey, Q, k0, key0, lane);
+        const int e = find_edge_bin(edges, E, key0);
+        const FrameDev& Fa = frames[edges[e].a];
+        const int dx0 = Fa.dim[0], dy0 = Fa.dim[1], dz0 = Fa.dim[2];
+        const int cell = (int)(key0 - edges[e].bin_off);
+        const int hx = cell % dx0, hy = (cell / dx0) % dy0, hz = cell / (dx0 * dy0);
+        // this lane's query
+        const bool qv = lane < qcount;
+        const float4 r = qv ? slots[(long long)k0 + lane] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const int sidx = __float_as_int(r.w);
+        const float mx = -2.f * r.x, my = -2.f * r.y, mz = -2.f * r.z;
+        const float mw = fmaf(r.x, r.x, fmaf(r.y, r.y, r.z * r.z));
+        Sem<DP, BF16> qs;
+        if (DP > 0) qs.load(sem_sorted, sidx, qv);
+        float4 qc = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (COLOR && qv) qc = __ldg(col4 + sidx);
+        float blo0 = qv ? r.x : -NEG_INF, blo1 = qv ? r.y : -NEG_INF, blo2 = qv ? r.z : -NEG_INF;
+        float bhi0 = qv ? r.x : NEG_INF, bhi1 = qv ? r.y : NEG_INF, bhi2 = qv ? r.z : NEG_INF;
 #pragma unroll
-            for (int mm = 0; mm < 3; ++mm)
-#pragma unroll
-                for (int l = mm; l < 3; ++l, ++t6)
-                    Myy[t6] += Sy[mm] * o[l] + o[mm] * Sy[l] + W * o[mm] * o[l];
-#pragma unroll
-            for (int mm = 0; mm < 3; ++mm)
-#pragma unroll
-                for (int l = 0; l < 3; ++l) Mdy[3 * mm + l] = fmaf(Dv[mm], o[l], Mdy[3 * mm + l]);
-#pragma unroll
-            for (int mm = 0; mm < 3; ++mm) Sy[mm] = fmaf(W, o[mm], Sy[mm]);
+        for (int o = 16; o > 0; o >>= 1) {
+            blo0 = fminf(blo0, __shfl_xor_sync(FULL, blo0, o));
+            blo1 = fminf(blo1, __shfl_xor_sync(FULL, blo1, o));
+            blo2 = fminf(blo2, __shfl_xor_sync(FULL, blo2, o));
+            bhi0 = fmaxf(bhi0, __shfl_xor_sync(FULL, bhi0, o));
+            bhi1 = fmaxf(bhi1, __shfl_xor_sync(FULL, bhi1, o));
+            bhi2 = fmaxf(bhi2, __shfl_xor_sync(FULL, bhi2, o));
         }
-        // fixed point per lane, then a reduce-scatter over the warp: lane k
-        // ends with the warp total of moment k
-        const float* scl = edges[e].scale;
-        long long vals[32];
+        __syncwarp();
+        const int C = build_rows(R, cell_start, Fa.cell_off, dx0, dy0, dz0, hx, hy, hz, lane);
+        const float box_thr = gp.rc2 * 1.0001f;
+        float tw[TOPK_MAX], t0[TOPK_MAX], t1[TOPK_MAX], t2[TOPK_MAX];   // w descending, d = x - y
 #pragma unroll
-        for (int k = 0; k < 32; ++k) {
-            float val = 0.f;
-            if (k == 0) val = W;
-            else if (k < 4) val = Dv[k - 1];
-            else if (k < 7) val = Sy[k - 4];
-            else if (k < 13) val = Myy[k - 7];
-            else if (k < 22) val = Mdy[k - 13];
-            else if (k < 28) val = Qm[k - 22];
-            vals[k] = (k == N_MOM - 1) ? (long long)cnt
-                    : (k < N_MOM ? to_fixed(val, __ldg(scl + moment_class(k))) : 0ll);
+        for (int k = 0; k < TOPK_MAX; ++k) {
+            tw[k] = NEG_INF;
+            t0[k] = t1[k] = t2[k] = 0.f;
         }
-        reduce_half<16>(vals, lane);
-        reduce_half<8>(vals, lane);
-        reduce_half<4>(vals, lane);
-        reduce_half<2>(vals, lane);
-        reduce_half<1>(vals, lane);
-        if (lane < N_MOM && vals[0] != 0)
-            atomicAdd(reinterpret_cast<unsigned long long*>(acc + (long long)e * ACC_N + lane),
-                      (unsigned long long)vals[0]);
+        int c_s = 0, qhead = 0, qlen = 0;
+        while (c_s < C || qlen > 0) {
+            while (qlen < 32 && c_s < C) {
+                const int v = c_s + lane;
+                bool keep = false;
+                float4 ent = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (v < C) {
+                    int dx, dy, dz;
+                    const int i = stream_point(R, v, dx, dy, dz);
+                    const float4 p = __ldg(pts4 + i);
+                    ent.x = fmaf((float)dx, gp.hf, p.x);
+                    ent.y = fmaf((float)dy, gp.hf, p.y);
+                    ent.z = fmaf((float)dz, gp.hf, p.z);
+                    ent.w = __int_as_float(i);
+                    const float e0 = fmaxf(fmaxf(blo0 - ent.x, ent.x - bhi0), 0.f);
+                    const float e1 = fmaxf(fmaxf(blo1 - ent.y, ent.y - bhi1), 0.f);
+                    const float e2 = fmaxf(fmaxf(blo2 - ent.z, ent.z - bhi2), 0.f);
+                    keep = fmaf(e0, e0, fmaf(e1, e1, e2 * e2)) < box_thr;
+                }
+                const unsigned bal = __ballot_sync(FULL, keep);
+                if (keep) cq[(qhead + qlen + __popc(bal & ((1u << lane) - 1u))) & (CQ_N - 1)] = ent;
+                qlen += __popc(bal);
+                c_s += 32;
+            }
+            __syncwarp();
+            const int nb = qlen < 32 ? qlen : 32;
+            if (nb == 0) break;
+            if (lane < nb) {
+                const float4 ent = cq[(qhead + lane) & (CQ_N - 1)];
+                const int i = __float_as_int(ent.w);
+                scx[lane] = ent;
+                SemRow<DP, BF16>::stage(srow + lane * SW, sem_sorted, i);
+                if (COLOR) scc[lane] = __ldg(col4 + i);
+            }
+            qhead = (qhead + nb) & (CQ_N - 1);
+            qlen -= nb;
+            __syncwarp();
+            for (int c = 0; c < nb; ++c) {
+                const float4 xe = scx[c];
+                const float thr = gp.rc2 - fmaf(xe.x, xe.x, fmaf(xe.y, xe.y, xe.z * xe.z));
+                const float t = fmaf(xe.x, mx, fmaf(xe.y, my, fmaf(xe.z, mz, mw)));
+                if (qv && t < thr) {
+                    const float ex = fmaf(0.5f, mx, xe.x), ey = fmaf(0.5f, my, xe.y), ez = fmaf(0.5f, mz, xe.z);
+                    const float dd = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
+                    float arg = dd * gp.kg;
+                    if (COLOR) {
+                        const float4 cc = scc[c];
+                        const float cr = cc.x - qc.x, cg = cc.y - qc.y, cb = cc.z - qc.z;
+                        arg = fmaf(fmaf(cr, cr, fmaf(cg, cg, cb * cb)), gp.kc, arg);
+                    }
+                    const float s = SemRow<DP, BF16>::dot(qs, srow + c * SW);
+                    if (s >= gp.sem_min) {
+                        float cw = s * ex2_approx(arg);
+                        if (cw > tw[TOPK_MAX - 1]) {
+                            float c0 = ex, c1 = ey, c2 = ez;
+#pragma unroll
+                            for (int k = 0; k < TOPK_MAX; ++k) {
+                                const bool sw = cw > tw[k];
+                                const float a = tw[k], b0 = t0[k], b1 = t1[k], b2 = t2[k];
+                                tw[k] = sw ? cw : a;
+                                t0[k] = sw ? c0 : b0;
+                                t1[k] = sw ? c1 : b1;
+                                t2[k] = sw ? c2 : b2;
+                                cw = sw ? a : cw;
+                                c0 = sw ? b0 : c0;
+                                c1 = sw ? b1 : c1;
+                                c2 = sw ? b2 : c2;
+                            }
+                        }
+                    }
+                }
+            }
+            __syncwarp();
+        }
+        float W = 0.f, Dv[3] = {0.f, 0.f, 0.f}, Qm[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        int cnt = 0;
+#pragma unroll
+        for (int k = 0; k < TOPK_MAX; ++k) {
+            if (k < gp.top_k && tw[k] > NEG_INF) {
+                const float w = tw[k];
+                const float wx = w * t0[k], wy = w * t1[k], wz = w * t2[k];
+                W += w;
+                Dv[0] += wx; Dv[1] += wy; Dv[2] += wz;
+                Qm[0] = fmaf(wx, t0[k], Qm[0]); Qm[1] = fmaf(wx, t1[k], Qm[1]); Qm[2] = fmaf(wx, t2[k], Qm[2]);
+                Qm[3] = fmaf(wy, t1[k], Qm[3]); Qm[4] = fmaf(wy, t2[k], Qm[4]); Qm[5] = fmaf(wz, t2[k], Qm[5]);
+                ++cnt;
+            }
+        }
+        const float y[3] = {r.x, r.y, r.z};
+        float Sy[3], Myy[6], Mdy[9];
+        int t6 = 0;
+#pragma unroll
+        for (int mm = 0; mm < 3; ++mm) {
+            Sy[mm] = W * y[mm];
+#pragma unroll
+            for (int l = 0; l < 3; ++l) Mdy[3 * mm + l] = Dv[mm] * y[l];
+#pragma unroll
+            for (int l = mm; l < 3; ++l, ++t6) Myy[t6] = W * y[mm] * y[l];
+        }
+        store_moments(W, Dv, Sy, Myy, Mdy, Qm, cnt, Fa, hx, hy, hz, gp, edges[e].scale,
+                      acc + (long long)e * ACC_N, lane);
     }
 }
 
@@ -821,6 +1012,27 @@ inline unsigned blocks_for(long long n, int t) {
 }
 
 template <int DP, bool BF16, bool COLOR>
+void run_pairs_topk(unsigned grid, cudaStream_t st, const int* unit_start, const int* n_units,
+                    int* unit_counter, const uint32_t* qkey, const float4* slots, long long Q,
+                    const EdgeDev* edges, int E, const FrameDev* frames, const int* cell_start,
+                    const float4* pts4, const void* sem, const float4* col4, GridParams gp,
+                    long long* acc, const int* done) {
+    const size_t smem = sizeof(float) * (PAIR_T / 32) * warp_smem_words_topk<DP, BF16, COLOR>();
+    static int blocks_per_sm = 0;
+    if (!blocks_per_sm) {
+        cudaFuncSetAttribute(k_pairs_topk<DP, BF16, COLOR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_pairs_topk<DP, BF16, COLOR>, PAIR_T,
+                                                      smem);
+        if (blocks_per_sm < 1) blocks_per_sm = 1;
+    }
+    grid *= (unsigned)blocks_per_sm;
+    k_pairs_topk<DP, BF16, COLOR><<<grid, PAIR_T, smem, st>>>(unit_start, n_units, unit_counter, qkey, slots,
+                                                              Q, edges, E, frames, cell_start, pts4, sem,
+                                                              col4, gp, acc, done);
+}
+
+template <int DP, bool BF16, bool COLOR>
 void run_pairs(unsigned grid, cudaStream_t st, const int* unit_start, const int* n_units,
                int* unit_counter, const uint32_t* qkey, const float4* slots, long long Q,
                const EdgeDev* edges, int E, const FrameDev* frames, const int* cell_start,
@@ -834,6 +1046,12 @@ void run_pairs(unsigned grid, cudaStream_t st, const int* unit_start, const int*
         if (blocks_per_sm < 1) blocks_per_sm = 1;
     }
     grid *= (unsigned)blocks_per_sm;
+    if (gp.top_k > 0) {
+        run_pairs_topk<DP, BF16, COLOR>(grid / (unsigned)blocks_per_sm, st, unit_start, n_units, unit_counter,
+                                        qkey, slots, Q, edges, E, frames, cell_start, pts4, sem, col4, gp, acc,
+                                        done);
+        return;
+    }
     k_pairs<DP, BF16, COLOR><<<grid, PAIR_T, smem, st>>>(unit_start, n_units, unit_counter, qkey, slots,
                                                          Q, edges, E, frames, cell_start, pts4, sem,
                                                          col4, gp, acc, done);

@@ -36,8 +36,8 @@ class RkhsbaError(RuntimeError):
 class Params(C.Structure):
     _fields_ = [("ell", C.c_double), ("cutoff_mult", C.c_double), ("sigma", C.c_double),
                 ("ell_color", C.c_double), ("sem_dim", C.c_int32), ("sem_bf16", C.c_int32),
-                ("max_iters", C.c_int32), ("reserved", C.c_int32), ("lambda0", C.c_double),
-                ("tol_step", C.c_double), ("tol_rel_f", C.c_double)]
+                ("max_iters", C.c_int32), ("top_k", C.c_int32), ("lambda0", C.c_double),
+                ("tol_step", C.c_double), ("tol_rel_f", C.c_double), ("sem_min", C.c_double)]
 
 
 class SolveInfo(C.Structure):
@@ -144,10 +144,10 @@ def _check(status, ctx=None):
 
 
 def make_params(ell, cutoff_mult=3.0, sigma=1.0, ell_color=0.0, sem_dim=0, sem_bf16=0, max_iters=100,
-                lambda0=1e-4, tol_step=1e-10, tol_rel_f=1e-12):
+                lambda0=1e-4, tol_step=1e-10, tol_rel_f=1e-12, top_k=0, sem_min=0.0):
     return Params(float(ell), float(cutoff_mult), float(sigma), float(ell_color), int(sem_dim),
-                  int(bool(sem_bf16)), int(max_iters), 0, float(lambda0), float(tol_step),
-                  float(tol_rel_f))
+                  int(bool(sem_bf16)), int(max_iters), int(top_k), float(lambda0), float(tol_step),
+                  float(tol_rel_f), float(sem_min))
 
 
 # ---------------------------------------------------------------- C-ABI ----
@@ -331,13 +331,13 @@ class Problem:
 
     def __init__(self, xyz, sem=None, rgb=None, edges=None, ell=0.1, cutoff_mult=3.0, sigma=1.0,
                  ell_color=0.0, sem_bf16=False, max_iters=100, lambda0=1e-4, tol_step=1e-10,
-                 tol_rel_f=1e-12, stream=None):
+                 tol_rel_f=1e-12, top_k=0, sem_min=0.0, stream=None):
         self.K = len(xyz)
         self.edges = np.asarray(edges, np.int32).reshape(-1, 2)
         self.E = len(self.edges)
         sem_dim = 0 if sem is None else int(np.asarray(sem[0]).shape[-1])
         self.params = make_params(ell, cutoff_mult, sigma, ell_color, sem_dim, sem_bf16, max_iters,
-                                  lambda0, tol_step, tol_rel_f)
+                                  lambda0, tol_step, tol_rel_f, top_k, sem_min)
         self.ctx = rkhsba_create(xyz, sem, rgb, self.edges, self.params, stream)
 
     @classmethod
@@ -345,7 +345,7 @@ class Problem:
         p = dict(prob["params"])
         p.update(over)
         keep = {k: p[k] for k in ("ell", "cutoff_mult", "sigma", "ell_color", "sem_bf16", "max_iters",
-                                  "lambda0", "tol_step", "tol_rel_f") if k in p}
+                                  "lambda0", "tol_step", "tol_rel_f", "top_k", "sem_min") if k in p}
         return cls(prob["xyz"], prob.get("sem"), prob.get("rgb"), prob["edges"], **keep)
 
     def eval(self, poses, want_H=True, want_blocks=False):
@@ -432,7 +432,8 @@ class Server:
         params = make_params(p["ell"], p.get("cutoff_mult", 3.0), p.get("sigma", 1.0),
                              p.get("ell_color", 0.0), sem_dim, p.get("sem_bf16", 0),
                              p.get("max_iters", 100), p.get("lambda0", 1e-4),
-                             p.get("tol_step", 1e-10), p.get("tol_rel_f", 1e-12))
+                             p.get("tol_step", 1e-10), p.get("tol_rel_f", 1e-12), p.get("top_k", 0),
+                             p.get("sem_min", 0.0))
         n = np.array([len(x) for x in prob["xyz"]], np.int64)
         xyz = np.ascontiguousarray(np.concatenate([np.asarray(x, np.float64).reshape(-1, 3)
                                                    for x in prob["xyz"]]))

@@ -151,17 +151,25 @@ def test_ell_derivative_matches_central_differences():
     np.testing.assert_allclose(g, (D(0.2 + h) - D(0.2 - h)) / (2 * h), rtol=1e-6)
 
 
-def test_ell_decay_shrinks_ell_for_two_points():
-    # two single points: dist(ell) = 2 - 2 exp(-r^2 / 2 ell^2) falls with ell,
-    # so every outer step multiplies ell by (1 - decay)
-    p = _problem([[[0.0, 0, 0]], [[0.05, 0, 0]]], [[0, 1]], ell=0.2, max_iters=30)
-    p["poses0"] = np.stack([np.eye(4), O.se3_exp(np.array([0.02, 0.01, 0, 0, 0, 0]))])
-    out = O.ell_decay_solve(p, decay=0.1, ell_min=0.05, max_outer=6)
-    ells = [lv["ell"] for lv in out["levels"]]
-    assert all(lv["dD_dell"] < 0 for lv in out["levels"])
-    for e0, e1 in zip(ells, ells[1:]):
-        assert abs(e1 - max(e0 * 0.9, 0.05)) < 1e-15
-    assert 1 <= len(ells) <= 6
+def test_ell_step_lowers_the_distance():
+    # each outer step multiplies ell by (1 - decay sign(dD/dell)): at the poses
+    # a level solved, the summed distance at the next level's ell is lower
+    # (every pair kept, so D is smooth in ell and dD/dell is its derivative)
+    rng = np.random.default_rng(10)
+    x = rng.uniform(0, 2, (150, 3))
+    p = _problem([x, x + 0.15], [[0, 1]], ell=0.2, max_iters=20, **ALL)
+    out = O.ell_decay_solve(p, decay=0.1, ell_min=0.05, max_outer=3)
+    lv = out["levels"]
+    assert len(lv) >= 2
+    for k in range(len(lv) - 1):
+        assert abs(lv[k + 1]["ell"] - max(lv[k]["ell"] * (1 - 0.1 * np.sign(lv[k]["dD_dell"])), 0.05)) < 1e-15
+    T = O.lm_solve(p, p["poses0"], params=dict(ell=lv[0]["ell"]))["poses"]
+    D0 = O.distance_and_cosine(p, T, params=dict(ell=lv[0]["ell"]))["dist"].sum()
+    D1 = O.distance_and_cosine(p, T, params=dict(ell=lv[1]["ell"]))["dist"].sum()
+    assert D1 < D0
+    # two single points at distance r: D = 2 - 2 exp(-r^2 / 2 ell^2) falls with ell
+    two = _problem([[[0.0, 0, 0]], [[0.05, 0, 0]]], [[0, 1]], ell=0.2)
+    assert O.distance_and_cosine(two, two["poses0"])["dD_dell"] < 0
 
 
 # ------------------------------------------------------- rotation search ----
