@@ -24,6 +24,8 @@
 // with error-free transformations (Dekker product, Knuth sum) on the FP32 pipe.
 #include "common.cuh"
 
+#include <type_traits>
+
 namespace rk {
 
 namespace {
@@ -373,18 +375,20 @@ __device__ __forceinline__ float ex2_approx(float x) {
 //                 (m_x j, m_x j+1, m_y j, m_y j+1, m_z j, m_z j+1, |y|^2 j, |y|^2 j+1)
 //   colours [UQ] float4, labels [UQ][row words], stencil rows [40] ints,
 //   per-lane unit sums [32][N_ACC] (kept in shared memory to free registers),
-//   candidate queue [CQ_N] float4 (x relative to the home centre, point index).
+//   candidate queue [CQ_N] float4 (x relative to the home centre, point index),
+//   with BF16 labels the batch's label Gram [32 candidates][GRAM_LD] floats.
 // Per-lane sums over a unit, in this order: W, D (3), Q (6), sum w0 x (3),
 // sum w0 x x^T (6), sum x dc^T (9), with w0 = sum w, dc = sum w d of one
 // candidate over its queries.
 constexpr int N_ACC = 28;
 constexpr int CQ_N = 64;            // ring of candidates that survived the unit's box test
+constexpr int GRAM_LD = 34;         // row stride (floats) of the BF16 label Gram tile
 constexpr int A_W = 0, A_D = 1, A_Q = 4, A_SWX = 10, A_SWXX = 13, A_SXD = 19;
 
 template <int DP, bool BF16, bool COLOR>
 __host__ __device__ constexpr int warp_smem_words() {
     return UQ * 4 + UQ * 4 + (COLOR ? UQ * 4 : 0) + UQ * SemRow<DP, BF16>::WORDS + 4 * 10 + 32 * N_ACC +
-           4 * CQ_N;
+           4 * CQ_N + ((BF16 && DP > 0) ? 32 * GRAM_LD : 0);
 }
 
 struct Rows {
@@ -515,8 +519,68 @@ __device__ __forceinline__ void store_moments(float W, const float (&Dv)[3], flo
         atomicAdd(reinterpret_cast<unsigned long long*>(acc_e + lane), (unsigned long long)vals[0]);
 }
 
+// BF16 labels: the candidate x query label products of a batch come from the
+// tensor cores (mma.sync m16n8k16, BF16 in, FP32 accumulate; BF16 products
+// are exact in FP32) into a shared-memory tile; the walk reads one float per
+// pair instead of forming the dot product.
+__device__ __forceinline__ void mma_bf16_16816(float (&d)[4], const unsigned (&a)[4], unsigned b0, unsigned b1) {
+    asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+                 "{%0,%1,%2,%3};"
+                 : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+                 : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+template <int DP>
+__device__ __forceinline__ void label_gram_bf16(const unsigned* __restrict__ semw, const float* ssq, int cand_i,
+                                                unsigned has_mask, int lane, float* G) {
+    constexpr int KS = (DP + 15) / 16;   // k16 steps; words beyond DP are zero
+    constexpr int RW = DP / 2;           // 32-bit words per label row
+    const int g = lane >> 2, t4 = lane & 3;
+    const unsigned* qw = reinterpret_cast<const unsigned*>(ssq);
+    float acc[2][4][4];
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+        for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) acc[mt][nt][k] = 0.f;
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt) {
+        const int r0 = 16 * mt + g, r1 = r0 + 8;                 // candidate rows of this lane
+        const int i0 = __shfl_sync(FULL, cand_i, r0), i1 = __shfl_sync(FULL, cand_i, r1);
+        const bool v0 = (has_mask >> r0) & 1u, v1 = (has_mask >> r1) & 1u;
+        const unsigned* row0 = semw + (size_t)i0 * RW;
+        const unsigned* row1 = semw + (size_t)i1 * RW;
+#pragma unroll
+        for (int ks = 0; ks < KS; ++ks) {
+            const int w0 = 8 * ks + t4, w1 = w0 + 4;             // words of k = 16 ks + 2 t, + 8
+            unsigned a[4];
+            a[0] = (v0 && w0 < RW) ? __ldg(row0 + w0) : 0u;
+            a[1] = (v1 && w0 < RW) ? __ldg(row1 + w0) : 0u;
+            a[2] = (v0 && w1 < RW) ? __ldg(row0 + w1) : 0u;
+            a[3] = (v1 && w1 < RW) ? __ldg(row1 + w1) : 0u;
+#pragma unroll
+            for (int nt = 0; nt < 4; ++nt) {
+                const unsigned* qrow = qw + (8 * nt + g) * RW;
+                const unsigned b0 = (w0 < RW) ? qrow[w0] : 0u;
+                const unsigned b1 = (w1 < RW) ? qrow[w1] : 0u;
+                mma_bf16_16816(acc[mt][nt], a, b0, b1);
+            }
+        }
+    }
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+        for (int nt = 0; nt < 4; ++nt) {
+            float* p0 = G + (16 * mt + g) * GRAM_LD + 8 * nt + 2 * t4;
+            float* p1 = p0 + 8 * GRAM_LD;
+            *reinterpret_cast<float2*>(p0) = make_float2(acc[mt][nt][0], acc[mt][nt][1]);
+            *reinterpret_cast<float2*>(p1) = make_float2(acc[mt][nt][2], acc[mt][nt][3]);
+        }
+}
+
 template <int DP, bool BF16, bool COLOR>
-__global__ void __launch_bounds__(PAIR_T, RK_PAIR_MINB)
+__global__ void __launch_bounds__(PAIR_T, (BF16 && DP > 0) ? 2 : RK_PAIR_MINB)
 k_pairs(const int* __restrict__ unit_start, const int* __restrict__ n_units, int* unit_counter,
         const uint32_t* __restrict__ qkey, const float4* __restrict__ slots, long long Q,
         const EdgeDev* __restrict__ edges, int E, const FrameDev* __restrict__ frames,
@@ -537,6 +601,7 @@ k_pairs(const int* __restrict__ unit_start, const int* __restrict__ n_units, int
     const Rows R{ri, ri + 9, ri + 18, ri + 27};
     float4* sacc = reinterpret_cast<float4*>(ri + 40) + lane * (N_ACC / 4);   // this lane's unit sums
     float4* cq = reinterpret_cast<float4*>(ri + 40) + 32 * (N_ACC / 4);       // candidate ring
+    float* gram = reinterpret_cast<float*>(cq + CQ_N);                        // [32][GRAM_LD] (BF16 labels)
     const ulonglong2* walk2 = reinterpret_cast<const ulonglong2*>(smw);
     const ulonglong2* test2 = reinterpret_cast<const ulonglong2*>(smt);
     const u64 H2 = f2(0.5f, 0.5f);
@@ -643,7 +708,7 @@ k_pairs(const int* __restrict__ unit_start, const int* __restrict__ n_units, int
             const float xx = fmaf(x0, x0, fmaf(x1, x1, x2 * x2));
             const float thr = gp.rc2 - xx;
             Sem<DP, BF16> cs;
-            if (DP > 0) cs.load(sem_sorted, i, has);
+            if (DP > 0 && !BF16) cs.load(sem_sorted, i, has);
             float4 cc = make_float4(0.f, 0.f, 0.f, 0.f);
             if (COLOR && has) cc = __ldg(col4 + i);
             // cutoff test against query pairs: bit j set when |x - y_j| < r_c
@@ -658,40 +723,56 @@ k_pairs(const int* __restrict__ unit_start, const int* __restrict__ n_units, int
                 }
             }
             if (!has) mk = 0u;
+            if constexpr (BF16 && DP > 0) {
+                label_gram_bf16<DP>(reinterpret_cast<const unsigned*>(sem_sorted), ssq, i, __ballot_sync(FULL, has),
+                                    lane, gram);
+                __syncwarp();
+            }
+            const float* grow = gram + lane * GRAM_LD;
             const u64 XA = f2(x0, x1), XB = f2(x2, x0);
             float w0 = 0.f, dz_s = 0.f, q12 = 0.f, q22 = 0.f;
             u64 D01 = 0ull, Q0011 = 0ull, Q0201 = 0ull;
-            while (__any_sync(FULL, mk != 0u)) {
-                if (mk) {
-                    const int j = __ffs(mk) - 1;
-                    mk &= mk - 1u;
-                    const ulonglong2 m = walk2[j];
-                    const u64 E01 = ffma2(H2, m.x, XA);                  // (ex, ey)
-                    const u64 E20 = ffma2(H2, m.y, XB);                  // (ez, ex)
-                    const float2 exy = f2_split(E01);
-                    const float ez = f2_split(E20).x;
-                    const float dd = fmaf(exy.x, exy.x, fmaf(exy.y, exy.y, ez * ez));
-                    float arg = dd * gp.kg;
-                    if (COLOR) {
-                        const float4 qc = scq[j];
-                        const float cr = cc.x - qc.x, cg = cc.y - qc.y, cb = cc.z - qc.z;
-                        arg = fmaf(fmaf(cr, cr, fmaf(cg, cg, cb * cb)), gp.kc, arg);
+            // the bit walk, compiled twice: with the semantic-pruning test
+            // only when pruning is on (a uniform branch per batch)
+            auto walk = [&](auto prune) {
+                constexpr bool PRUNE = decltype(prune)::value;
+                while (__any_sync(FULL, mk != 0u)) {
+                    if (mk) {
+                        const int j = __ffs(mk) - 1;
+                        mk &= mk - 1u;
+                        const ulonglong2 m = walk2[j];
+                        const u64 E01 = ffma2(H2, m.x, XA);              // (ex, ey)
+                        const u64 E20 = ffma2(H2, m.y, XB);              // (ez, ex)
+                        const float2 exy = f2_split(E01);
+                        const float ez = f2_split(E20).x;
+                        const float dd = fmaf(exy.x, exy.x, fmaf(exy.y, exy.y, ez * ez));
+                        float arg = dd * gp.kg;
+                        if (COLOR) {
+                            const float4 qc = scq[j];
+                            const float cr = cc.x - qc.x, cg = cc.y - qc.y, cb = cc.z - qc.z;
+                            arg = fmaf(fmaf(cr, cr, fmaf(cg, cg, cb * cb)), gp.kc, arg);
+                        }
+                        float s;
+                        if constexpr (BF16 && DP > 0) s = grow[j];
+                        else s = SemRow<DP, BF16>::dot(cs, ssq + j * SW);
+                        bool kept = true;
+                        if constexpr (PRUNE) kept = s >= gp.sem_min;
+                        const float w = kept ? s * ex2_approx(arg) : 0.f;
+                        const u64 WXY = fmul2(f2(w, w), E01);            // (w ex, w ey)
+                        const float wz = w * ez;
+                        w0 += w;
+                        D01 = fadd2(D01, WXY);
+                        dz_s += wz;
+                        Q0011 = ffma2(WXY, E01, Q0011);                  // (q00, q11)
+                        Q0201 = ffma2(WXY, E20, Q0201);                  // (q02, q01)
+                        q12 = fmaf(f2_split(WXY).y, ez, q12);
+                        q22 = fmaf(wz, ez, q22);
+                        cnt += kept ? 1 : 0;
                     }
-                    const float s = SemRow<DP, BF16>::dot(cs, ssq + j * SW);
-                    const bool kept = s >= gp.sem_min;                  // semantic pruning (off: -inf)
-                    const float w = kept ? s * ex2_approx(arg) : 0.f;
-                    const u64 WXY = fmul2(f2(w, w), E01);                // (w ex, w ey)
-                    const float wz = w * ez;
-                    w0 += w;
-                    D01 = fadd2(D01, WXY);
-                    dz_s += wz;
-                    Q0011 = ffma2(WXY, E01, Q0011);                      // (q00, q11)
-                    Q0201 = ffma2(WXY, E20, Q0201);                      // (q02, q01)
-                    q12 = fmaf(f2_split(WXY).y, ez, q12);
-                    q22 = fmaf(wz, ez, q22);
-                    cnt += kept ? 1 : 0;
                 }
-            }
+            };
+            if (DP > 0 && gp.sem_min > -__int_as_float(0x7f800000)) walk(std::true_type{});
+            else walk(std::false_type{});
             const float2 dxy = f2_split(D01), q0011 = f2_split(Q0011), q0201 = f2_split(Q0201);
             const float x[3] = {x0, x1, x2};
             const float dc[3] = {dxy.x, dxy.y, dz_s};
