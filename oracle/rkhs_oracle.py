@@ -56,7 +56,8 @@ from scipy.spatial import cKDTree
 __all__ = [
     "DEFAULTS", "hat", "wedge", "se3_exp", "se3_log", "pose_error",
     "label_weights", "pairs_bruteforce", "pairs_kdtree", "edge_terms",
-    "evaluate", "lm_solve", "irls_frozen_solve", "edge_pairs", "select_pairs", "inner_product", "self_inner",
+    "evaluate", "lm_solve", "irls_frozen_solve", "edge_pairs", "select_pairs", "kernel_sums", "inner_product",
+    "self_inner",
     "distance_and_cosine", "ell_decay_solve", "icosahedral_rotations", "rotation_search",
 ]
 
@@ -447,9 +448,31 @@ def irls_frozen_solve(xa, xb, i, j, w, Ta, Tb, iters=50, lam=0.0):
 # ---------------------------------------------------------------------------
 # inner products, RKHS distance and cosine (Sec. III-A, Eq. dist_rkhs)
 # ---------------------------------------------------------------------------
+def kernel_sums(xa, xb, Ta, Tb, sem_a=None, sem_b=None, rgb_a=None, rgb_b=None, params=None, chunk=500000):
+    """F = sigma^2 sum w and E = sum w |d|^2 over the pairs inside the cutoff,
+    w = c k (no Jacobians: the function-space quantities need only these)."""
+    P = _params(params)
+    ell, sigma = P["ell"], P["sigma"]
+    p = _transform(Ta, np.asarray(xa, np.float64))
+    q = _transform(Tb, np.asarray(xb, np.float64))
+    i, j = pairs_kdtree(p, q, P["cutoff_mult"] * ell)
+    if P["sem_min"] > 0 or P["top_k"] > 0:
+        keep = select_pairs(p, q, i, j, sem_a, sem_b, rgb_a, rgb_b, P)
+        i, j = i[keep], j[keep]
+    F = E = 0.0
+    for s in range(0, len(i), chunk):
+        ii, jj = i[s:s + chunk], j[s:s + chunk]
+        d = p[ii] - q[jj]
+        d2 = np.einsum("nk,nk->n", d, d)
+        w = label_weights(sem_a, sem_b, rgb_a, rgb_b, ii, jj, P["ell_color"]) * np.exp(-d2 / (2.0 * ell * ell))
+        F += sigma * sigma * float(w.sum())
+        E += float((w * d2).sum())
+    return dict(F=F, E=E, n_pairs=int(len(i)))
+
+
 def inner_product(xa, xb, Ta, Tb, sem_a=None, sem_b=None, rgb_a=None, rgb_b=None, params=None):
     """<f_{T_a X_a}, f_{T_b X_b}> over the pairs inside the cutoff (Eq. double_sum)."""
-    return edge_terms(xa, xb, Ta, Tb, sem_a, sem_b, rgb_a, rgb_b, params)["F"]
+    return kernel_sums(xa, xb, Ta, Tb, sem_a, sem_b, rgb_a, rgb_b, params)["F"]
 
 
 def self_inner(x, sem=None, rgb=None, params=None):
@@ -472,7 +495,7 @@ def distance_and_cosine(problem, poses, params=None):
     s_terms = []
     for m in range(K):
         x, s, c = _frame_inputs(problem, m)
-        s_terms.append(edge_terms(x, x, I, I, s, s, c, c, P))
+        s_terms.append(kernel_sums(x, x, I, I, s, s, c, c, P))
     selfs = np.array([t["F"] for t in s_terms])
     self_E = np.array([t["E"] for t in s_terms])
     dist, cos, cross, cross_E = [], [], [], []
@@ -480,7 +503,7 @@ def distance_and_cosine(problem, poses, params=None):
         a, b = int(a), int(b)
         xa, sa, ca = _frame_inputs(problem, a)
         xb, sb, cb = _frame_inputs(problem, b)
-        t = edge_terms(xa, xb, poses[a], poses[b], sa, sb, ca, cb, P)
+        t = kernel_sums(xa, xb, poses[a], poses[b], sa, sb, ca, cb, P)
         cross.append(t["F"])
         cross_E.append(t["E"])
         dist.append(selfs[a] + selfs[b] - 2.0 * t["F"])

@@ -222,3 +222,51 @@ def test_ell_decay_rejects_bad_schedule(pk):
                 g.solve_ell_decay(prob["poses0"], **kw)
     finally:
         g.close()
+
+
+# ------------------------------------------------- full-size, sampled --------
+def test_inner_products_full_size_sampled(pk):
+    """Bench workload (8 x 20k LiDAR points, 28 edges): the GPU's values for
+    two sampled edges and their frames' self terms against the oracle."""
+    prob = scenes.lidar_street_problem(seed=1434)
+    g = pk.Problem.from_scene(prob)
+    try:
+        out = g.inner_products(prob["poses0"])
+    finally:
+        g.close()
+    edges = np.asarray(prob["edges"])
+    for e in (0, 17):
+        a, b = (int(v) for v in edges[e])
+        sub = dict(prob, xyz=[prob["xyz"][a], prob["xyz"][b]], sem=[prob["sem"][a], prob["sem"][b]],
+                   edges=np.array([[0, 1]], np.int32))
+        ref = O.distance_and_cosine(sub, prob["poses0"][[a, b]])
+        np.testing.assert_allclose(out["self"][[a, b]], ref["self"], rtol=TOL)
+        np.testing.assert_allclose(out["cross"][e], ref["cross"][0], rtol=TOL)
+        np.testing.assert_allclose(out["cos"][e], ref["cos"][0], atol=TOL)
+
+
+def test_rotation_search_full_size_sampled(pk):
+    """8000-point scans (the largest size of the paper's timing study): the
+    cosines of sampled candidates against the oracle's inner products
+    at those candidate poses (three sampled, the best among them)."""
+    prob = scenes.object_pair_problem(seed=210, angle_deg=180.0, n=8000, outlier_ratio=0.125, crop_ratio=0.125,
+                                      ell=0.1, labels=True)
+    g = pk.Problem.from_scene(prob)
+    try:
+        out = g.rotation_search(0, 1, prob["poses0"])
+    finally:
+        g.close()
+    xa, xb = prob["xyz"]
+    sa, sb = prob["sem"]
+    P = dict(O.DEFAULTS)
+    P.update(prob["params"])
+    Sa = O.self_inner(xa, sa, None, P)
+    Sb = O.self_inner(xb, sb, None, P)
+    mua, mub = xa.mean(0), xb.mean(0)
+    for k in sorted({0, 29, int(out["best"])}):
+        R = out["rotations"][k]
+        Tb = np.eye(4)
+        Tb[:3, :3] = R
+        Tb[:3, 3] = mua - R @ mub
+        cos = O.inner_product(xa, xb, np.eye(4), Tb, sa, sb, None, None, P) / np.sqrt(Sa * Sb)
+        assert abs(out["cos"][k] - cos) <= TOL, (k, out["cos"][k], cos)
