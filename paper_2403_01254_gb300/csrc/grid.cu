@@ -160,16 +160,25 @@ __global__ void k_gather(const double* __restrict__ xyz, const float* __restrict
             }
         }
         if (gp.color) col4[s] = make_float4(rgb[3 * g], rgb[3 * g + 1], rgb[3 * g + 2], 0.f);
-        // cell_start over every cell of every frame; a run start fills the gap
         const long long key = keys[s];
-        const bool start = (s == 0) || ((long long)keys[s - 1] != key);
-        run_flag[s] = start ? 1 : 0;
-        if (start) {
-            long long prev = (s == 0) ? -1 : (long long)keys[s - 1];
-            for (long long k = prev + 1; k <= key; ++k) cell_start[k] = (int)s;
+        run_flag[s] = ((s == 0) || ((long long)keys[s - 1] != key)) ? 1 : 0;
+    }
+}
+
+// cell_start[c] = first sorted point whose cell key is >= c, for c in
+// [0, C_total] (a lower bound in the sorted keys; empty cells get the start
+// of the next occupied one, the end entry N).
+__global__ void k_cell_start(const uint32_t* __restrict__ keys, long long N, long long C_total,
+                             int* __restrict__ cell_start) {
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c <= C_total;
+         c += (long long)gridDim.x * blockDim.x) {
+        long long lo = 0, hi = N;
+        while (lo < hi) {
+            const long long mid = (lo + hi) >> 1;
+            if ((long long)keys[mid] < c) lo = mid + 1;
+            else hi = mid;
         }
-        if (s == N - 1)
-            for (long long k = key + 1; k <= C_total; ++k) cell_start[k] = (int)N;
+        cell_start[c] = (int)lo;
     }
 }
 
@@ -204,7 +213,8 @@ void launch_gather(const double* xyz, const float* sem, const float* rgb, long l
     if (N <= 0) return;
     k_gather<<<grid_for(N), GT, 0, st>>>(xyz, sem, rgb, N, K, pt_off, keys, perm, gp, C_total,
                                          pts4, sem_sorted, col4, perm_local, cell_start, run_flag);
-    count_launch();
+    k_cell_start<<<grid_for(C_total + 1), GT, 0, st>>>(keys, N, C_total, cell_start);
+    count_launch(2);
 }
 
 }  // namespace rk

@@ -87,13 +87,18 @@ __global__ void __launch_bounds__(RAD_T) k_onesweep(const uint32_t* __restrict__
     const unsigned lt = (1u << lane) - 1u;
     uint32_t key[RAD_IPT];
     int val[RAD_IPT], dig[RAD_IPT], rank[RAD_IPT];
+    // all loads of the tile first (independent), then the ranking rounds
+#pragma unroll
+    for (int r = 0; r < RAD_IPT; ++r) {
+        const long long i = base + (long long)r * RAD_T + tid;
+        key[r] = i < n ? kin[i] : 0u;
+        val[r] = i < n ? vin[i] : 0;
+    }
     // stable ranks inside the tile: round r holds keys base + 256 r + tid
 #pragma unroll
     for (int r = 0; r < RAD_IPT; ++r) {
         const long long i = base + (long long)r * RAD_T + tid;
         const bool valid = i < n;
-        key[r] = valid ? kin[i] : 0u;
-        val[r] = valid ? vin[i] : 0;
         const int d = valid ? (int)((key[r] >> shift) & 255u) : 256;
         dig[r] = d;
         const unsigned peers = __match_any_sync(0xffffffffu, d);
