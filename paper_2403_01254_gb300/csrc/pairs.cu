@@ -376,13 +376,15 @@ __device__ __forceinline__ float ex2_approx(float x) {
 //   colours [UQ] float4, labels [UQ][row words], stencil rows [40] ints,
 //   per-lane unit sums [32][N_ACC] (kept in shared memory to free registers),
 //   candidate queue [CQ_N] float4 (x relative to the home centre, point index),
-//   with BF16 labels the batch's label Gram [32 candidates][GRAM_LD] floats.
+//   with BF16 labels the batch's label Gram [32 queries][GRAM_LD] floats.
 // Per-lane sums over a unit, in this order: W, D (3), Q (6), sum w0 x (3),
 // sum w0 x x^T (6), sum x dc^T (9), with w0 = sum w, dc = sum w d of one
 // candidate over its queries.
 constexpr int N_ACC = 28;
 constexpr int CQ_N = 64;            // ring of candidates that survived the unit's box test
-constexpr int GRAM_LD = 34;         // row stride (floats) of the BF16 label Gram tile
+constexpr int GRAM_LD = 32;         // row stride (floats) of the BF16 label Gram tile, stored
+                                    // [query][candidate]: the walk's lane c reads column c,
+                                    // one bank per lane
 constexpr int A_W = 0, A_D = 1, A_Q = 4, A_SWX = 10, A_SWXX = 13, A_SXD = 19;
 
 template <int DP, bool BF16, bool COLOR>
@@ -572,10 +574,11 @@ __device__ __forceinline__ void label_gram_bf16(const unsigned* __restrict__ sem
     for (int mt = 0; mt < 2; ++mt)
 #pragma unroll
         for (int nt = 0; nt < 4; ++nt) {
-            float* p0 = G + (16 * mt + g) * GRAM_LD + 8 * nt + 2 * t4;
-            float* p1 = p0 + 8 * GRAM_LD;
-            *reinterpret_cast<float2*>(p0) = make_float2(acc[mt][nt][0], acc[mt][nt][1]);
-            *reinterpret_cast<float2*>(p1) = make_float2(acc[mt][nt][2], acc[mt][nt][3]);
+            const int c = 16 * mt + g, q = 8 * nt + 2 * t4;      // candidate row, query column
+            G[q * GRAM_LD + c] = acc[mt][nt][0];
+            G[(q + 1) * GRAM_LD + c] = acc[mt][nt][1];
+            G[q * GRAM_LD + c + 8] = acc[mt][nt][2];
+            G[(q + 1) * GRAM_LD + c + 8] = acc[mt][nt][3];
         }
 }
 
@@ -601,7 +604,7 @@ k_pairs(const int* __restrict__ unit_start, const int* __restrict__ n_units, int
     const Rows R{ri, ri + 9, ri + 18, ri + 27};
     float4* sacc = reinterpret_cast<float4*>(ri + 40) + lane * (N_ACC / 4);   // this lane's unit sums
     float4* cq = reinterpret_cast<float4*>(ri + 40) + 32 * (N_ACC / 4);       // candidate ring
-    float* gram = reinterpret_cast<float*>(cq + CQ_N);                        // [32][GRAM_LD] (BF16 labels)
+    float* gram = reinterpret_cast<float*>(cq + CQ_N);                        // [query][candidate] (BF16)
     const ulonglong2* walk2 = reinterpret_cast<const ulonglong2*>(smw);
     const ulonglong2* test2 = reinterpret_cast<const ulonglong2*>(smt);
     const u64 H2 = f2(0.5f, 0.5f);
@@ -728,7 +731,7 @@ k_pairs(const int* __restrict__ unit_start, const int* __restrict__ n_units, int
                                     lane, gram);
                 __syncwarp();
             }
-            const float* grow = gram + lane * GRAM_LD;
+            const float* gcol = gram + lane;                      // column of this lane's candidate
             const u64 XA = f2(x0, x1), XB = f2(x2, x0);
             float w0 = 0.f, dz_s = 0.f, q12 = 0.f, q22 = 0.f;
             u64 D01 = 0ull, Q0011 = 0ull, Q0201 = 0ull;
@@ -753,7 +756,7 @@ k_pairs(const int* __restrict__ unit_start, const int* __restrict__ n_units, int
                             arg = fmaf(fmaf(cr, cr, fmaf(cg, cg, cb * cb)), gp.kc, arg);
                         }
                         float s;
-                        if constexpr (BF16 && DP > 0) s = grow[j];
+                        if constexpr (BF16 && DP > 0) s = gcol[j * GRAM_LD];
                         else s = SemRow<DP, BF16>::dot(cs, ssq + j * SW);
                         bool kept = true;
                         if constexpr (PRUNE) kept = s >= gp.sem_min;
