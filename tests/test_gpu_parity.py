@@ -263,3 +263,52 @@ def test_solve_recovers_ground_truth_on_identical_clouds(pk):
         g.close()
     dr, dt = O.pose_error(T[1], prob["poses_gt"][1])
     assert dr < 1e-5 and dt < 1e-5, (dr, dt, info)
+
+
+# ------------------------------------------------ every label width -----------
+@pytest.mark.parametrize("bf16", [False, True])
+@pytest.mark.parametrize("sem_dim", [1, 5, 9, 13, 17, 21, 25, 32])
+def test_every_label_width(pk, sem_dim, bf16):
+    """Each padded label width of the pair kernel (FP32 rows of 4..32 floats,
+    BF16 rows of 8..32 values on the tensor-core Gram path, one or two k16
+    steps) against the oracle, with and without the top-k variant."""
+    rng = np.random.default_rng(sem_dim)
+    prob = scenes.tiny_problem(seed=80 + sem_dim, n_frames=3, n=300, extent=1.0, ell=0.15)
+    lab = [rng.dirichlet(np.ones(sem_dim), len(x)).astype(np.float32) for x in prob["xyz"]]
+    if bf16:
+        lab = [scenes.round_to_bf16(s) for s in lab]
+    prob["sem"] = lab
+    prob["params"] = dict(prob["params"], sem_bf16=int(bf16))
+    check_eval(pk, prob, prob["poses0"])
+    prob["params"] = dict(prob["params"], top_k=5)
+    check_eval(pk, prob, prob["poses0"])
+
+
+def test_many_frames(pk):
+    """4096 frames (the frame limit) of 12 points on a chain of 4095 edges:
+    loss and gradient against the oracle's per-edge sums (the 6K x 6K matrix
+    is not formed on the host)."""
+    rng = np.random.default_rng(4096)
+    K, n = 4096, 12
+    base = rng.uniform(0, 0.4, (n, 3))
+    xyz = [base + rng.normal(scale=0.02, size=base.shape) for _ in range(K)]
+    edges = np.array([[m, m + 1] for m in range(K - 1)], np.int32)
+    poses = np.stack([scenes.random_pose(rng, 1.0, 0.01) for _ in range(K)])
+    poses[0] = np.eye(4)
+    prob = dict(xyz=xyz, sem=None, rgb=None, edges=edges, poses0=poses,
+                params=dict(ell=0.1, cutoff_mult=3.0, sigma=1.0, ell_color=0.0, sem_bf16=0))
+    g = pk.Problem.from_scene(prob)
+    try:
+        out = g.eval(poses, want_H=False)
+    finally:
+        g.close()
+    F = 0.0
+    b = np.zeros(6 * K)
+    for a, c in edges:
+        t = O.edge_terms(xyz[a], xyz[c], poses[a], poses[c], params=prob["params"])
+        F += t["F"]
+        b[6 * a:6 * a + 6] += t["b"][:6]
+        b[6 * c:6 * c + 6] += t["b"][6:]
+    grad = b / 0.1 ** 2
+    assert abs(out["loss"] + F) <= LOSS_TOL * F
+    assert _reln(out["grad"], grad) <= GRAD_TOL
