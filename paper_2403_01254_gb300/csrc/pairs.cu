@@ -736,41 +736,58 @@ k_pairs(const int* __restrict__ unit_start, const int* __restrict__ n_units, int
             float w0 = 0.f, dz_s = 0.f, q12 = 0.f, q22 = 0.f;
             u64 D01 = 0ull, Q0011 = 0ull, Q0201 = 0ull;
             // the bit walk, compiled twice: with the semantic-pruning test
-            // only when pruning is on (a uniform branch per batch)
+            // only when pruning is on (a uniform branch per batch).  Each
+            // iteration takes two of the lane's pairs, two independent
+            // dependency chains (the second weighs zero when one is left).
             auto walk = [&](auto prune) {
                 constexpr bool PRUNE = decltype(prune)::value;
+                auto pair_w = [&](int j, u64& E01, u64& E20, float& ez, bool& kept) -> float {
+                    const ulonglong2 m = walk2[j];
+                    E01 = ffma2(H2, m.x, XA);
+                    E20 = ffma2(H2, m.y, XB);
+                    const float2 exy = f2_split(E01);
+                    ez = f2_split(E20).x;
+                    const float dd = fmaf(exy.x, exy.x, fmaf(exy.y, exy.y, ez * ez));
+                    float arg = dd * gp.kg;
+                    if (COLOR) {
+                        const float4 qc = scq[j];
+                        const float cr = cc.x - qc.x, cg = cc.y - qc.y, cb = cc.z - qc.z;
+                        arg = fmaf(fmaf(cr, cr, fmaf(cg, cg, cb * cb)), gp.kc, arg);
+                    }
+                    float s;
+                    if constexpr (BF16 && DP > 0) s = gcol[j * GRAM_LD];
+                    else s = SemRow<DP, BF16>::dot(cs, ssq + j * SW);
+                    kept = true;
+                    if constexpr (PRUNE) kept = s >= gp.sem_min;
+                    return kept ? s * ex2_approx(arg) : 0.f;
+                };
+                auto add = [&](float w, u64 E01, u64 E20, float ez, bool kept) {
+                    const u64 WXY = fmul2(f2(w, w), E01);
+                    const float wz = w * ez;
+                    w0 += w;
+                    D01 = fadd2(D01, WXY);
+                    dz_s += wz;
+                    Q0011 = ffma2(WXY, E01, Q0011);
+                    Q0201 = ffma2(WXY, E20, Q0201);
+                    q12 = fmaf(f2_split(WXY).y, ez, q12);
+                    q22 = fmaf(wz, ez, q22);
+                    cnt += kept ? 1 : 0;
+                };
                 while (__any_sync(FULL, mk != 0u)) {
                     if (mk) {
-                        const int j = __ffs(mk) - 1;
+                        const int j1 = __ffs(mk) - 1;
                         mk &= mk - 1u;
-                        const ulonglong2 m = walk2[j];
-                        const u64 E01 = ffma2(H2, m.x, XA);              // (ex, ey)
-                        const u64 E20 = ffma2(H2, m.y, XB);              // (ez, ex)
-                        const float2 exy = f2_split(E01);
-                        const float ez = f2_split(E20).x;
-                        const float dd = fmaf(exy.x, exy.x, fmaf(exy.y, exy.y, ez * ez));
-                        float arg = dd * gp.kg;
-                        if (COLOR) {
-                            const float4 qc = scq[j];
-                            const float cr = cc.x - qc.x, cg = cc.y - qc.y, cb = cc.z - qc.z;
-                            arg = fmaf(fmaf(cr, cr, fmaf(cg, cg, cb * cb)), gp.kc, arg);
-                        }
-                        float s;
-                        if constexpr (BF16 && DP > 0) s = gcol[j * GRAM_LD];
-                        else s = SemRow<DP, BF16>::dot(cs, ssq + j * SW);
-                        bool kept = true;
-                        if constexpr (PRUNE) kept = s >= gp.sem_min;
-                        const float w = kept ? s * ex2_approx(arg) : 0.f;
-                        const u64 WXY = fmul2(f2(w, w), E01);            // (w ex, w ey)
-                        const float wz = w * ez;
-                        w0 += w;
-                        D01 = fadd2(D01, WXY);
-                        dz_s += wz;
-                        Q0011 = ffma2(WXY, E01, Q0011);                  // (q00, q11)
-                        Q0201 = ffma2(WXY, E20, Q0201);                  // (q02, q01)
-                        q12 = fmaf(f2_split(WXY).y, ez, q12);
-                        q22 = fmaf(wz, ez, q22);
-                        cnt += kept ? 1 : 0;
+                        const bool has2 = mk != 0u;
+                        const int j2 = has2 ? __ffs(mk) - 1 : j1;
+                        if (has2) mk &= mk - 1u;
+                        u64 Ea1, Eb1, Ea2, Eb2;
+                        float ez1, ez2;
+                        bool k1, k2;
+                        const float w1 = pair_w(j1, Ea1, Eb1, ez1, k1);
+                        float w2 = pair_w(j2, Ea2, Eb2, ez2, k2);
+                        add(w1, Ea1, Eb1, ez1, k1);
+                        if (!has2) { w2 = 0.f; k2 = false; }
+                        add(w2, Ea2, Eb2, ez2, k2);
                     }
                 }
             };
