@@ -737,8 +737,9 @@ k_pairs(const int* __restrict__ unit_start, const int* __restrict__ n_units, int
             u64 D01 = 0ull, Q0011 = 0ull, Q0201 = 0ull;
             // the bit walk, compiled twice: with the semantic-pruning test
             // only when pruning is on (a uniform branch per batch).  Each
-            // iteration takes two of the lane's pairs, two independent
-            // dependency chains (the second weighs zero when one is left).
+            // iteration takes U of the lane's pairs as independent dependency
+            // chains (missing ones weigh zero): 2 with FP32 label dots, 4
+            // with the short BF16 Gram lookups.
             auto walk = [&](auto prune) {
                 constexpr bool PRUNE = decltype(prune)::value;
                 auto pair_w = [&](int j, u64& E01, u64& E20, float& ez, bool& kept) -> float {
@@ -773,21 +774,27 @@ k_pairs(const int* __restrict__ unit_start, const int* __restrict__ n_units, int
                     q22 = fmaf(wz, ez, q22);
                     cnt += kept ? 1 : 0;
                 };
+                constexpr int U = (BF16 && DP > 0) ? 4 : 2;   // pairs per iteration
                 while (__any_sync(FULL, mk != 0u)) {
                     if (mk) {
-                        const int j1 = __ffs(mk) - 1;
-                        mk &= mk - 1u;
-                        const bool has2 = mk != 0u;
-                        const int j2 = has2 ? __ffs(mk) - 1 : j1;
-                        if (has2) mk &= mk - 1u;
-                        u64 Ea1, Eb1, Ea2, Eb2;
-                        float ez1, ez2;
-                        bool k1, k2;
-                        const float w1 = pair_w(j1, Ea1, Eb1, ez1, k1);
-                        float w2 = pair_w(j2, Ea2, Eb2, ez2, k2);
-                        add(w1, Ea1, Eb1, ez1, k1);
-                        if (!has2) { w2 = 0.f; k2 = false; }
-                        add(w2, Ea2, Eb2, ez2, k2);
+                        int jj[U];
+                        bool hv[U];
+#pragma unroll
+                        for (int u = 0; u < U; ++u) {
+                            hv[u] = mk != 0u;
+                            jj[u] = hv[u] ? __ffs(mk) - 1 : 0;
+                            if (hv[u]) mk &= mk - 1u;
+                        }
+                        u64 Ea[U], Eb[U];
+                        float ez[U], w[U];
+                        bool kp[U];
+#pragma unroll
+                        for (int u = 0; u < U; ++u) w[u] = pair_w(jj[u], Ea[u], Eb[u], ez[u], kp[u]);
+#pragma unroll
+                        for (int u = 0; u < U; ++u) {
+                            if (!hv[u]) { w[u] = 0.f; kp[u] = false; }
+                            add(w[u], Ea[u], Eb[u], ez[u], kp[u]);
+                        }
                     }
                 }
             };
