@@ -356,7 +356,7 @@ struct SemRow<0, false> {
 
 constexpr int PAIR_T = 256;
 #ifndef RK_PAIR_MINB
-#define RK_PAIR_MINB 3              // resident CTAs per SM the register budget targets
+#define RK_PAIR_MINB 2              // resident CTAs per SM the register budget targets
 #endif
 constexpr int UQ = UNIT_Q;          // queries per unit: one 32-bit mask word
 static_assert(UQ == 32, "units hold 32 queries");
@@ -737,9 +737,10 @@ k_pairs(const int* __restrict__ unit_start, const int* __restrict__ n_units, int
             u64 D01 = 0ull, Q0011 = 0ull, Q0201 = 0ull;
             // the bit walk, compiled twice: with the semantic-pruning test
             // only when pruning is on (a uniform branch per batch).  Each
-            // iteration takes U of the lane's pairs as independent dependency
-            // chains (missing ones weigh zero): 2 with FP32 label dots, 4
-            // with the short BF16 Gram lookups.
+            // iteration takes 4 of the lane's pairs as independent dependency
+            // chains (missing ones weigh zero); at 2 CTAs per SM the registers
+            // for them are there, and the ILP hides more latency than a third
+            // CTA's warps did.
             auto walk = [&](auto prune) {
                 constexpr bool PRUNE = decltype(prune)::value;
                 auto pair_w = [&](int j, u64& E01, u64& E20, float& ez, bool& kept) -> float {
@@ -774,7 +775,7 @@ k_pairs(const int* __restrict__ unit_start, const int* __restrict__ n_units, int
                     q22 = fmaf(wz, ez, q22);
                     cnt += kept ? 1 : 0;
                 };
-                constexpr int U = (BF16 && DP > 0) ? 4 : 2;   // pairs per iteration
+                constexpr int U = 4;   // pairs per iteration
                 while (__any_sync(FULL, mk != 0u)) {
                     if (mk) {
                         int jj[U];
