@@ -288,17 +288,21 @@ __global__ void __launch_bounds__(LM_T) k_lm_solve(int K, const double* __restri
     double* rinv = y + n;
     const int warp = tid >> 5, lane = tid & 31;
     constexpr int NW = LM_T / 32;
-    for (int k = 0; k < n; ++k) {
-        if (tid == 0) {
-            const double d = A[(long long)k * n + k];
-            const double r = rsqrt_nr(d);
-            if (!(d > 0.0) || !(r > 0.0) || !isfinite(r)) fail = 1;
-            else {
-                A[(long long)k * n + k] = d * r;   // sqrt(d)
-                rinv[k] = r;
-            }
+    // pivot k: thread 0 (for k > 0 right after its own update of A_kk,
+    // which row k + 1 of warp 0, lane 0 holds, so the pivot's chain overlaps
+    // the other warps' updates instead of costing a barrier of its own)
+    auto pivot = [&](int k) {
+        const double d = A[(long long)k * n + k];
+        const double r = rsqrt_nr(d);
+        if (!(d > 0.0) || !(r > 0.0) || !isfinite(r)) fail = 1;
+        else {
+            A[(long long)k * n + k] = d * r;   // sqrt(d)
+            rinv[k] = r;
         }
-        __syncthreads();
+    };
+    if (tid == 0 && n > 0) pivot(0);
+    __syncthreads();
+    for (int k = 0; k < n; ++k) {
         if (fail) break;
         const double r = rinv[k];
         for (int i = k + 1 + tid; i < n; i += LM_T) A[(long long)i * n + k] *= r;
@@ -309,6 +313,7 @@ __global__ void __launch_bounds__(LM_T) k_lm_solve(int K, const double* __restri
             for (int j = k + 1 + lane; j <= i; j += 32)
                 A[(long long)i * n + j] = fma(-lik, A[(long long)j * n + k], A[(long long)i * n + j]);
         }
+        if (tid == 0 && k + 1 < n) pivot(k + 1);
         __syncthreads();
     }
     if (!fail) {
