@@ -1,14 +1,17 @@
 #!/usr/bin/env python
 """Throughput of the RKHS-BA hot path on GB300: pair-terms/s for
-loss + gradient + Gauss-Newton blocks, measured on the 8-frame x 20k-point
-LiDAR multi-view registration workload (28 frame pairs, 19-class FP32 label
-distributions, ell = 0.3 m, r_c = 0.9 m), synthetic and seeded.
+loss + gradient + Gauss-Newton blocks, measured on the global-mapping
+workload (64 frames x 100k LiDAR points on a loop with loop closures, 516
+frame pairs, 19-class labels stored as BF16, ell = 0.3 m, r_c = 0.9 m),
+synthetic and seeded; the 8 x 20k multi-view registration and the 10 x 50k
+sliding-window workloads are measured beside it.
 
 One step = one pass of the whole hot path over the resident problem:
 grid build of every frame, the evaluation at the initial poses (transform,
 binning, pair kernel, FP64 assembly) and one Levenberg-Marquardt iteration
-(Cholesky solve, SE(3) update, evaluation at the candidate, accept/reject).
-Pair-terms counted are those of the two evaluations of the step.
+(Cholesky solve of the 6K x 6K system, SE(3) update, evaluation at the
+candidate, accept/reject).  Pair-terms counted are those of the two
+evaluations of the step.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 Under torchrun every rank runs its own replica (the path shards by problem;
@@ -31,7 +34,8 @@ sys.path.insert(0, ROOT)
 
 METRIC = "pair-terms/s for RKHS-BA loss+grad+Hessian; served BA solves/s, p50/p99 latency"
 UNIT = "pair-terms/s"
-WORKLOAD = "lidar_street_8x20000"
+WORKLOAD = "mapping_64x100000"
+SECONDARY = ("lidar_street_8x20000", "window_10x50000")
 L2_FLUSH_BYTES = 256 << 20
 
 
@@ -64,10 +68,18 @@ def recorded_traffic(workload_name):
     return ent.get("bytes_per_launch")
 
 
-def flops_per_pair(sem_dim, color):
-    """Algorithmic FP32 flops of one pair-term (FMA = 2): d (3), |d|^2 (5),
-    exponent (1), label dot (2 D), w = s k (1), sums W, D, Q (1 + 3 + 3 + 12);
-    colour factor adds 9."""
+# Algorithmic FP32 work of one pair-term (what the method must do per pair
+# inside r_c): d and |d|^2 (3 sub + 3 FMA), the exponent and one exp, the
+# 19-term label dot (19 FMA) and the updates of the 28 edge moments: about 60
+# FP32 instructions, 110 flops.  The roofline fraction is stated on this basis.
+FLOPS_PER_PAIR = 110
+
+
+def kernel_flops_per_pair(sem_dim, color):
+    """FP32 flops the pair kernel itself spends per pair-term (FMA = 2): d
+    (3), |d|^2 (5), exponent (1), label dot (2 D), w = s k (1), per-pair sums
+    W, D, Q (1 + 3 + 3 + 12); the 28 moments are folded once per candidate,
+    not per pair.  Colour adds 9.  Reported beside the algorithmic basis."""
     return 29 + 2 * sem_dim + (9 if color else 0)
 
 
@@ -87,62 +99,82 @@ def workload(name=None):
 
 
 # ------------------------------------------------------------------ oracle --
-def oracle_sample(kind):
-    """Run the FP64 oracle on a bounded sample of the workload (CPU only)."""
-    import oracle
-    prob = workload()
-    if kind == "baseline":
-        # two full frame pairs (0,1) and (0,2) at the initial poses
-        sub = dict(prob, edges=np.asarray(prob["edges"])[[0, 1]])
-        desc = "edges (0,1),(0,2) of the 8x20k workload at the initial poses"
-    else:
-        # frame pair (0,1), every 4th point of frame 1
-        sub = dict(prob, edges=np.asarray(prob["edges"])[[0]])
-        sub["xyz"] = list(prob["xyz"])
-        sub["sem"] = list(prob["sem"])
-        sub["xyz"][1] = prob["xyz"][1][::4]
-        sub["sem"][1] = prob["sem"][1][::4]
-        desc = "edge (0,1) of the 8x20k workload with every 4th point of frame 1"
-    t0 = time.perf_counter()
-    r = oracle.evaluate(sub, prob["poses0"])
-    dt = time.perf_counter() - t0
-    return dict(pairs=int(r["n_pairs"]), seconds=dt, sample=desc)
+def _oracle_edges(prob, name):
+    """Frame pairs of the CPU samples: for the mapping workload the first
+    odometry edge (0,1) and the first loop-closure edge (0,16); otherwise the
+    first two edges."""
+    E = np.asarray(prob["edges"])
+    if name.startswith("mapping"):
+        return [0, int(np.nonzero(E[:, 1] - E[:, 0] > 7)[0][0])]
+    return [0, 1]
 
 
-def run_oracle_subprocess(kind):
-    env = dict(os.environ)
-    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
-        env[v] = "1"
-    env["CUDA_VISIBLE_DEVICES"] = ""
-    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-sample", kind],
-                       capture_output=True, text=True, env=env, timeout=900)
-    if r.returncode != 0:
-        raise RuntimeError("oracle sample failed: " + r.stderr[-2000:])
-    return json.loads(r.stdout.strip().splitlines()[-1])
+def _truncated(prob, e, n_b):
+    """The problem with the second frame of edge e cut to its first n_b points."""
+    b = int(np.asarray(prob["edges"])[e][1])
+    sub = dict(prob, xyz=list(prob["xyz"]), sem=list(prob["sem"]) if prob.get("sem") is not None else None)
+    sub["xyz"][b] = prob["xyz"][b][:n_b]
+    if sub["sem"] is not None:
+        sub["sem"][b] = prob["sem"][b][:n_b]
+    return sub
+
+
+def oracle_baseline(prob, name):
+    """The FP64 oracle timed on the host cores on a bounded sample of the
+    workload: every core (a spawned pool, each worker single-threaded, the
+    edges' sums split over slices of frame b's points), and one core on a
+    smaller sample.  Value = pair-terms / wall time."""
+    from oracle.split_sum import evaluate_split, make_pool
+    ids = _oracle_edges(prob, name)
+    E = np.asarray(prob["edges"])
+    T = prob["poses0"]
+    cores = os.cpu_count() or 1
+    with make_pool(cores) as pool:
+        pool.submit(int, 0).result()                       # workers up before the clock starts
+        r = evaluate_split(prob, T, ids, pool=pool)
+    one_sub = _truncated(prob, ids[0], 8000)
+    with make_pool(1) as pool:
+        pool.submit(int, 0).result()
+        r1 = evaluate_split(one_sub, T, [ids[0]], pool=pool)
+    pairs = "+".join("(%d,%d)" % tuple(int(v) for v in E[e]) for e in ids)
+    return dict(value=r["n_pairs"] / r["wall_s"], unit=UNIT, cores=r["workers"], kind="oracle",
+                sample="edges %s of %s at the initial poses, full density (%d pair-terms, %.1f s wall on %d "
+                       "processes)" % (pairs, name, r["n_pairs"], r["wall_s"], r["workers"]),
+                single_core=dict(value=r1["n_pairs"] / r1["wall_s"], cores=1,
+                                 sample="edge (%d,%d) of %s, first 8000 points of frame %d (%d pair-terms, %.1f s)"
+                                        % (int(E[ids[0]][0]), int(E[ids[0]][1]), name, int(E[ids[0]][1]),
+                                           r1["n_pairs"], r1["wall_s"])))
 
 
 def reference_arm(args, rank):
+    """The oracle as the reference arm: each step evaluates a bounded sample
+    of the workload (edge (0,1), the first 16000 points of frame 1, at the
+    initial poses) on every host core; warm-up steps first."""
     if rank != 0:
         return
-    env_cores = 1
-    # warm-up steps, then K timed steps, each a bounded sample on 1 host core
-    for _ in range(args.warmup):
-        run_oracle_subprocess("step")
+    from oracle.split_sum import evaluate_split, make_pool
+    prob = workload(args.workload)
+    sub = _truncated(prob, 0, 16000)
+    b = int(np.asarray(prob["edges"])[0][1])
+    desc = ("edge (0,%d) of %s with the first 16000 points of frame %d, at the initial poses, "
+            "on every host core" % (b, args.workload, b))
+    cores = os.cpu_count() or 1
     tot_pairs, tot_s = 0, 0.0
-    desc = ""
-    for _ in range(args.steps):
-        r = run_oracle_subprocess("step")
-        tot_pairs += r["pairs"]
-        tot_s += r["seconds"]
-        desc = r["sample"]
+    with make_pool(cores) as pool:
+        pool.submit(int, 0).result()
+        for _ in range(args.warmup):
+            evaluate_split(sub, prob["poses0"], [0], slice_points=1000, pool=pool)
+        for _ in range(args.steps):
+            r = evaluate_split(sub, prob["poses0"], [0], slice_points=1000, pool=pool)
+            tot_pairs += r["n_pairs"]
+            tot_s += r["wall_s"]
     value = tot_pairs / tot_s
     line = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=args.gpus, steps=args.steps,
                 warmup=args.warmup, ms_per_step=1e3 * tot_s / args.steps, higher_is_better=True,
                 scaling="weak", vs_baseline=None, dtype="f64", data="synthetic",
                 impl="reference",
-                config=dict(workload=WORKLOAD, sample=desc),
-                cpu_baseline=dict(value=value, unit=UNIT, cores=env_cores, kind="oracle",
-                                  sample=desc),
+                config=dict(workload=args.workload, sample=desc),
+                cpu_baseline=dict(value=value, unit=UNIT, cores=cores, kind="oracle", sample=desc),
                 e2e=dict(value=value, unit=UNIT, h2d_bytes_per_step=0, d2h_bytes_per_step=0))
     print(json.dumps(line), flush=True)
 
@@ -215,153 +247,208 @@ def replica_throughput(ms_local, pairs_per_step, steps, world, device=None):
     return pairs_per_step * steps * world / (ms_max / 1e3), ms_max
 
 
-def ours(args, rank, world, local_rank):
-    import torch
-
-    import paper_2403_01254_gb300 as pk
-    from paper_2403_01254_gb300 import rkhsba as rb
-
-    cpu_base = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        # before the first CUDA call: the oracle runs in a fresh process
-        cb = run_oracle_subprocess("baseline")
-        cpu_base = dict(value=cb["pairs"] / cb["seconds"], unit=UNIT, cores=1, kind="oracle",
-                        sample=cb["sample"] + " (%d pair-terms, %.1f s)" % (cb["pairs"], cb["seconds"]))
-
-    torch.cuda.set_device(local_rank)
-    dev = torch.device("cuda", local_rank)
-    pk.load()
-    prob = workload(args.workload)
+def _flat_inputs(prob):
     K = len(prob["xyz"])
     sem_dim = prob["sem"][0].shape[1]
-    n_points = np.array([len(x) for x in prob["xyz"]], np.int64)
-    xyz_h = np.ascontiguousarray(np.concatenate(prob["xyz"]))
-    sem_h = np.ascontiguousarray(np.concatenate(prob["sem"]).astype(np.float32))
-    poses0 = np.ascontiguousarray(prob["poses0"].reshape(K * 16))
-    edges = np.asarray(prob["edges"], np.int32)
     P = prob["params"]
     color = prob.get("rgb") is not None and P.get("ell_color", 0.0) > 0
-    rgb_h = np.ascontiguousarray(np.concatenate(prob["rgb"]).astype(np.float32)) if color else None
-    params = pk.make_params(P["ell"], P["cutoff_mult"], P["sigma"], P.get("ell_color", 0.0), sem_dim,
+    return dict(
+        K=K, sem_dim=sem_dim, P=P, color=color,
+        n_points=np.array([len(x) for x in prob["xyz"]], np.int64),
+        xyz=np.ascontiguousarray(np.concatenate(prob["xyz"])),
+        sem=np.ascontiguousarray(np.concatenate(prob["sem"]).astype(np.float32)),
+        rgb=np.ascontiguousarray(np.concatenate(prob["rgb"]).astype(np.float32)) if color else None,
+        poses0=np.ascontiguousarray(prob["poses0"].reshape(K * 16)),
+        edges=np.asarray(prob["edges"], np.int32))
+
+
+def measure_device(pk, rb, prob, steps, warmup, dev, stream, flush, world=1, clocks_index=None):
+    """Time `steps` bench steps of the resident problem with CUDA events on
+    the library's stream (L2 flushed between steps, outside the events);
+    phase times from the library's own events.  Returns pair-terms per step,
+    summed step time, phase times, launch count and clock samples."""
+    import torch
+    f = _flat_inputs(prob)
+    P = f["P"]
+    params = pk.make_params(P["ell"], P["cutoff_mult"], P["sigma"], P.get("ell_color", 0.0), f["sem_dim"],
                             P.get("sem_bf16", 0), max_iters=1000)
-    stream = torch.cuda.Stream(device=dev)
-    xyz_d = torch.from_numpy(xyz_h).to(dev)
-    sem_d = torch.from_numpy(sem_h).to(dev)
-    rgb_d = torch.from_numpy(rgb_h).to(dev) if color else None
-    poses_d = torch.from_numpy(poses0).to(dev)
+    xyz_d = torch.from_numpy(f["xyz"]).to(dev)
+    sem_d = torch.from_numpy(f["sem"]).to(dev)
+    rgb_d = torch.from_numpy(f["rgb"]).to(dev) if f["color"] else None
+    poses_d = torch.from_numpy(f["poses0"]).to(dev)
     torch.cuda.synchronize()
-    ctx = pk.rkhsba_create_device(n_points, xyz_d.data_ptr(), sem_d.data_ptr(),
-                                  rgb_d.data_ptr() if color else None, edges, params, stream.cuda_stream)
-    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    ctx = pk.rkhsba_create_device(f["n_points"], xyz_d.data_ptr(), sem_d.data_ptr(),
+                                  rgb_d.data_ptr() if f["color"] else None, f["edges"], params, stream.cuda_stream)
 
     def step():
         rb.rkhsba_rebuild(ctx)
         rb.rkhsba_set_poses_device(ctx, poses_d.data_ptr())
         rb.rkhsba_iterate(ctx, 1)
 
-    with torch.cuda.stream(stream):
-        for _ in range(max(args.warmup, 1)):
-            flush.zero_()
-            step()
-    stream.synchronize()
-    _, st = rb.rkhsba_get_state(ctx, K)
-    pairs_per_step = st["pair_terms"]
-
-    clocks = ClockSampler(local_rank)
-    time.sleep(0.3)
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-          for _ in range(args.steps)]
-    if world > 1:
-        torch.distributed.barrier()
-    torch.cuda.synchronize()
-    rb.rkhsba_profile(ctx, 1)
-    n_launch0 = pk.rkhsba_launch_count()
-    clocks.mark(True)
-    with torch.cuda.stream(stream):
-        for k in range(args.steps):
-            flush.zero_()                      # L2 flush between steps, outside the events
-            ev[k][0].record(stream)
-            step()
-            ev[k][1].record(stream)
-    torch.cuda.synchronize()
-    clocks.mark(False)
-    if world > 1:
-        torch.distributed.barrier()
-    n_launch = pk.rkhsba_launch_count() - n_launch0
-    prof = rb.rkhsba_profile(ctx, 0, read=True)
-    clk = clocks.stop()
+    try:
+        with torch.cuda.stream(stream):
+            for _ in range(max(warmup, 1)):
+                flush.zero_()
+                step()
+        stream.synchronize()
+        _, st = rb.rkhsba_get_state(ctx, f["K"])
+        pairs_per_step = st["pair_terms"]
+        clocks = ClockSampler(clocks_index) if clocks_index is not None else None
+        if clocks:
+            time.sleep(0.3)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        rb.rkhsba_profile(ctx, 1)
+        n_launch0 = pk.rkhsba_launch_count()
+        if clocks:
+            clocks.mark(True)
+        with torch.cuda.stream(stream):
+            for k in range(steps):
+                flush.zero_()                      # L2 flush between steps, outside the events
+                ev[k][0].record(stream)
+                step()
+                ev[k][1].record(stream)
+        torch.cuda.synchronize()
+        if clocks:
+            clocks.mark(False)
+        if world > 1:
+            torch.distributed.barrier()
+        n_launch = pk.rkhsba_launch_count() - n_launch0
+        prof = rb.rkhsba_profile(ctx, 0, read=True)
+        clk = clocks.stop() if clocks else None
+    finally:
+        rb.rkhsba_destroy(ctx)
     ms = sum(a.elapsed_time(b) for a, b in ev)
-    value, ms_max = replica_throughput(ms, pairs_per_step, args.steps, world, dev)
+    return dict(pairs_per_step=int(pairs_per_step), ms=ms, prof=prof, launches=int(n_launch), clocks=clk,
+                flat=f)
 
-    # roofline of the dominant kernel (the pair kernel): FP32 arithmetic
-    pair_ms, pair_n = prof["pairs"]
-    fl = flops_per_pair(sem_dim, color)
-    achieved = pairs_per_step * args.steps * fl / (pair_ms / 1e3) / 1e12 if pair_ms > 0 else None
+
+def roofline_of(name, m, steps, dev, sm_max):
+    """Roofline of the dominant kernel (the pair kernel, bound by FP32 issue):
+    achieved = algorithmic flops (110 per pair-term) of the pair-terms one
+    launch processes / that launch's CUDA-event time; peak = SMs x 128 FP32
+    lanes x 2 flop x clock."""
+    import torch
+    pair_ms, pair_n = m["prof"]["pairs"]
     props = torch.cuda.get_device_properties(dev)
-    sm_max = (clk or {}).get("sm_max_mhz") or 2070.0
     peak = props.multi_processor_count * 128 * 2 * sm_max * 1e6 / 1e12
-    roofline = dict(bound="alu", achieved=achieved, peak=peak, unit="TFLOP/s",
-                    frac=(achieved / peak) if achieved else None, traffic=recorded_traffic(args.workload),
-                    kernel="k_pairs", flops_per_pair_term=fl,
-                    peak_basis="%d SMs x 128 FP32 lanes x 2 flop x %.0f MHz" %
-                               (props.multi_processor_count, sm_max),
-                    pair_kernel_ms_per_launch=pair_ms / max(pair_n, 1),
-                    phases_ms_per_step={k: v[0] / args.steps for k, v in prof.items()})
-    rb.rkhsba_destroy(ctx)
+    terms = m["pairs_per_step"] * steps
+    achieved = terms * FLOPS_PER_PAIR / (pair_ms / 1e3) / 1e12 if pair_ms > 0 else None
+    kfl = kernel_flops_per_pair(m["flat"]["sem_dim"], m["flat"]["color"])
+    k_achieved = terms * kfl / (pair_ms / 1e3) / 1e12 if pair_ms > 0 else None
+    return dict(bound="alu", achieved=achieved, peak=peak, unit="TFLOP/s",
+                frac=(achieved / peak) if achieved else None, traffic=recorded_traffic(name),
+                kernel="k_pairs", flops_per_pair_term=FLOPS_PER_PAIR,
+                peak_basis="%d SMs x 128 FP32 lanes x 2 flop x %.0f MHz (nominal unit counts; no measured FP32 peak)"
+                           % (props.multi_processor_count, sm_max),
+                kernel_flops_per_pair_term=kfl,
+                frac_kernel_flops=(k_achieved / peak) if k_achieved else None,
+                pair_terms_per_launch=m["pairs_per_step"] / 2,
+                pair_kernel_ms_per_launch=pair_ms / max(pair_n, 1),
+                pair_terms_per_s_in_kernel=terms / (pair_ms / 1e3) if pair_ms > 0 else None,
+                phases_ms_per_step={k: v[0] / steps for k, v in m["prof"].items()})
 
-    # end to end through the C ABI with host buffers (pinned)
+
+def measure_e2e(pk, rb, f, stream, n_steps):
+    """Same metric through the public C ABI from pinned HOST buffers: each
+    step is rkhsba_create (H2D of points and labels, grid build) +
+    rkhsba_solve with max_iters 1 (two evaluations, D2H of the poses) +
+    rkhsba_destroy, timed on the host around synchronous calls."""
+    import torch
+    P = f["P"]
+
+    def pinned(a, dt):
+        if a is None:
+            return None
+        out = torch.empty(a.shape, dtype=dt, pin_memory=True).numpy()
+        out[:] = a
+        return out
+    xyz_p = pinned(f["xyz"], torch.float64)
+    sem_p = pinned(f["sem"], torch.float32)
+    rgb_p = pinned(f["rgb"], torch.float32)
+    pos_p = pinned(f["poses0"], torch.float64)
+    params1 = pk.make_params(P["ell"], P["cutoff_mult"], P["sigma"], P.get("ell_color", 0.0), f["sem_dim"],
+                             P.get("sem_bf16", 0), max_iters=1)
+    pairs, secs = 0, 0.0
+    for k in range(n_steps + 2):
+        pos_p[:] = f["poses0"]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        c2 = rb.rkhsba_create_flat(f["n_points"], xyz_p, sem_p, rgb_p, f["edges"], params1, stream.cuda_stream)
+        T, info = rb.rkhsba_solve(c2, pos_p, f["K"])
+        rb.rkhsba_destroy(c2)
+        dt = time.perf_counter() - t0
+        if k >= 2:
+            pairs += info["pair_terms"]
+            secs += dt
+    h2d = (f["xyz"].nbytes + f["sem"].nbytes + (f["rgb"].nbytes if f["color"] else 0) + f["poses0"].nbytes +
+           f["edges"].nbytes + f["n_points"].nbytes)
+    return dict(value=pairs / secs, unit=UNIT, h2d_bytes_per_step=int(h2d),
+                d2h_bytes_per_step=int(f["poses0"].nbytes + 64), steps=n_steps,
+                step="create (H2D + grids) + solve with max_iters 1 + destroy")
+
+
+def ours(args, rank, world, local_rank):
+    import torch
+
+    import paper_2403_01254_gb300 as pk
+    from paper_2403_01254_gb300 import rkhsba as rb
+
+    prob = workload(args.workload)
+    cpu_base = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        # before the first CUDA call; the oracle runs in spawned processes
+        cpu_base = oracle_baseline(prob, args.workload)
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    pk.load()
+    stream = torch.cuda.Stream(device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    m = measure_device(pk, rb, prob, args.steps, args.warmup, dev, stream, flush, world, clocks_index=local_rank)
+    value, ms_max = replica_throughput(m["ms"], m["pairs_per_step"], args.steps, world, dev)
+    clk = m["clocks"]
+    sm_max = (clk or {}).get("sm_max_mhz") or 2070.0
+    roofline = roofline_of(args.workload, m, args.steps, dev, sm_max)
+    f = m["flat"]
+
     e2e = None
     if not args.no_e2e:
-        xyz_p = torch.empty(xyz_h.shape, dtype=torch.float64, pin_memory=True).numpy()
-        sem_p = torch.empty(sem_h.shape, dtype=torch.float32, pin_memory=True).numpy()
-        pos_p = torch.empty(poses0.shape, dtype=torch.float64, pin_memory=True).numpy()
-        xyz_p[:] = xyz_h
-        sem_p[:] = sem_h
-        params1 = pk.make_params(P["ell"], P["cutoff_mult"], P["sigma"], P.get("ell_color", 0.0),
-                                 sem_dim, P.get("sem_bf16", 0), max_iters=1)
-        rgb_p = None
-        if color:
-            rgb_p = torch.empty(rgb_h.shape, dtype=torch.float32, pin_memory=True).numpy()
-            rgb_p[:] = rgb_h
-        n_e2e = max(3, min(args.steps, 20))
-        e2e_pairs, e2e_s = 0, 0.0
-        for k in range(n_e2e + 2):
-            pos_p[:] = poses0
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            c2 = rb.rkhsba_create_flat(n_points, xyz_p, sem_p, rgb_p, edges, params1,
-                                       stream.cuda_stream)
-            T, info = rb.rkhsba_solve(c2, pos_p, K)
-            rb.rkhsba_destroy(c2)
-            dt = time.perf_counter() - t0
-            if k >= 2:
-                e2e_pairs += info["pair_terms"]
-                e2e_s += dt
-        h2d = (xyz_h.nbytes + sem_h.nbytes + (rgb_h.nbytes if color else 0) + poses0.nbytes +
-               edges.nbytes + n_points.nbytes)
-        e2e = dict(value=e2e_pairs / e2e_s, unit=UNIT, h2d_bytes_per_step=int(h2d),
-                   d2h_bytes_per_step=int(poses0.nbytes + 64), steps=n_e2e,
-                   step="create (H2D + grids) + solve with max_iters 1 + destroy")
+        e2e = measure_e2e(pk, rb, f, stream, max(3, min(args.steps, 20)))
 
+    secondary = None
+    if rank == 0 and world == 1 and not args.no_secondary and args.workload == WORKLOAD:
+        secondary = {}
+        for name in SECONDARY:
+            p2 = workload(name)
+            steps2 = 50
+            m2 = measure_device(pk, rb, p2, steps2, 5, dev, stream, flush)
+            secondary[name] = dict(
+                value=m2["pairs_per_step"] * steps2 / (m2["ms"] / 1e3), unit=UNIT, steps=steps2,
+                ms_per_step=m2["ms"] / steps2, pair_terms_per_step=m2["pairs_per_step"],
+                roofline=roofline_of(name, m2, steps2, dev, sm_max))
     serve = None
     if rank == 0 and world == 1 and not args.no_serving and args.workload == WORKLOAD:
         serve = serving(pk)
     funcs = None
     if rank == 0 and world == 1 and not args.no_functions and args.workload == WORKLOAD:
-        funcs = function_space(pk, prob)
+        funcs = function_space(pk, workload(SECONDARY[0]))
 
     if rank == 0:
         line = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps,
                     warmup=args.warmup, ms_per_step=ms_max / args.steps, higher_is_better=True,
                     scaling="weak", vs_baseline=None, dtype="f32", data="synthetic",
-                    config=dict(workload=args.workload, frames=K, points=int(n_points.sum()),
-                                edges=len(edges), sem_dim=sem_dim, ell=P["ell"],
-                                pair_terms_per_step=int(pairs_per_step),
+                    config=dict(workload=args.workload, frames=f["K"], points=int(f["n_points"].sum()),
+                                edges=len(f["edges"]), sem_dim=f["sem_dim"],
+                                labels="bf16" if f["P"].get("sem_bf16", 0) else "f32", ell=f["P"]["ell"],
+                                pair_terms_per_step=int(m["pairs_per_step"]),
                                 l2="256 MiB buffer written between steps, outside the timed events",
                                 step="grid build + evaluation + one LM iteration (2 evaluations)",
                                 parallelism="replicas" if world > 1 else "single GPU"),
-                    roofline=roofline, cpu_baseline=cpu_base, e2e=e2e, gpu_launches=int(n_launch),
-                    clocks=clk, serving=serve, functions=funcs)
+                    roofline=roofline, cpu_baseline=cpu_base, e2e=e2e, gpu_launches=m["launches"],
+                    clocks=clk, secondary=secondary, serving=serve, functions=funcs)
         print(json.dumps(line), flush=True)
 
 
@@ -440,14 +527,26 @@ def function_space(pk, prob):
                 timing="host wall time around synchronous calls, median")
 
 
-def serving(pk, seed=1634, n_requests=200, pool_size=8, max_iters=30, load_factor=0.8):
-    """Served BA solves: a Poisson stream of requests (2-10 frames x 5k-100k
-    LiDAR points, log-uniform, 19-class labels) at load_factor x the measured
-    single-stream capacity.  Served form: the request server (continuous
-    batching, BF16 labels on the device).  Plain form: one request at a time
-    through rkhsba_create + rkhsba_solve with FP32 labels.  Requests are drawn
-    from a pool of pool_size generated problems (generation of 200 distinct
-    LiDAR problems would dominate the run)."""
+def _pose_diff(Ta, Tb):
+    """Largest rotation angle (rad) and translation (m) between two pose sets."""
+    dr = dt = 0.0
+    for A, B in zip(Ta, Tb):
+        E = np.linalg.inv(B) @ A
+        c = np.clip((np.trace(E[:3, :3]) - 1.0) / 2.0, -1.0, 1.0)
+        dr = max(dr, float(np.arccos(c)))
+        dt = max(dt, float(np.linalg.norm(E[:3, 3])))
+    return dr, dt
+
+
+def serving(pk, seed=1634, n_requests=200, pool_size=50, max_iters=30, loads=(0.5, 1.0, 1.5)):
+    """Served BA solves: a Poisson stream of n_requests requests (2-10 frames x
+    5k-100k LiDAR points, log-uniform, 19-class labels) drawn in turn from
+    pool_size generated problems, at several loads (x the measured plain
+    single-stream capacity).  Served form: the request server (continuous
+    batching, BF16 labels on the device, up to 8 in flight).  Plain form: one
+    request at a time through rkhsba_create + rkhsba_solve with FP32 labels.
+    Accuracy: the served poses of every pool problem against the plain FP32
+    poses of the same problem (both run max_iters LM iterations at most)."""
     import threading
 
     import scenes
@@ -458,100 +557,94 @@ def serving(pk, seed=1634, n_requests=200, pool_size=8, max_iters=30, load_facto
                                         n_points=sp["n_points"], sem_bf16=1)
         p["params"] = dict(p["params"], max_iters=max_iters)
         pool.append(p)
-    rng = np.random.default_rng(seed)
     order = [i % pool_size for i in range(n_requests)]
+    plain_res, served_res = {}, {}
 
-    def plain_solve(p):
-        g = pk.Problem.from_scene(p, sem_bf16=0)
+    def plain_solve(i):
+        g = pk.Problem.from_scene(pool[i], sem_bf16=0)
         try:
-            return g.solve(p["poses0"])
+            T, info = g.solve(pool[i]["poses0"])
         finally:
             g.close()
-
-    # single-stream capacity from the plain form on every pool problem
-    plain_solve(pool[0])
-    svc = []
-    for p in pool:
-        t0 = time.perf_counter()
-        plain_solve(p)
-        svc.append(time.perf_counter() - t0)
-    mean_svc = sum(svc[order[i]] for i in range(n_requests)) / n_requests
-    rate = load_factor / mean_svc
-    arrivals = np.cumsum(rng.exponential(1.0 / rate, size=n_requests))
+        plain_res.setdefault(i, T)
+        return T, info
 
     def pct(x, q):
         return float(np.percentile(np.asarray(x), q))
 
-    # served form
-    srv = pk.Server(max_inflight=8)
-    lat, done_t = [None] * n_requests, [None] * n_requests
-    tickets = [None] * n_requests
-    ready = threading.Event()
-    fail = []
+    # plain single-stream service times (capacity) over the pool
+    plain_solve(0)
+    svc = []
+    for i in range(pool_size):
+        t0 = time.perf_counter()
+        plain_solve(i)
+        svc.append(time.perf_counter() - t0)
+    mean_svc = sum(svc[order[i]] for i in range(n_requests)) / n_requests
 
-    def poller():
-        ready.wait()
+    def run_served(arrivals):
+        srv = pk.Server(max_inflight=8)
+        lat, done_t = [None] * n_requests, [None] * n_requests
+        tickets = [None] * n_requests
+        fail = []
+
+        def poller():
+            for i in range(n_requests):
+                while tickets[i] is None:
+                    time.sleep(0.0002)
+                r = srv.poll(tickets[i], timeout_ms=-1)
+                done_t[i] = time.perf_counter()
+                lat[i] = r[1]["latency_ms"]
+                if r[1]["state"] != "finished":
+                    fail.append(r[1])
+                else:
+                    served_res.setdefault(order[i], r[0])
+
+        th = threading.Thread(target=poller)
+        th.start()
+        t0 = time.perf_counter()
         for i in range(n_requests):
-            while tickets[i] is None:
-                time.sleep(0.0002)
-            r = srv.poll(tickets[i], timeout_ms=-1)
-            done_t[i] = time.perf_counter()
-            lat[i] = r[1]["latency_ms"]
-            if r[1]["state"] != "finished":
-                fail.append(r[1])
+            if arrivals is not None:
+                dt = t0 + arrivals[i] - time.perf_counter()
+                if dt > 0:
+                    time.sleep(dt)
+            tickets[i] = srv.submit(pool[order[i]])
+        th.join()
+        srv.close()
+        wall = max(done_t) - t0
+        return dict(solves_per_s=n_requests / wall, p50_ms=pct(lat, 50), p99_ms=pct(lat, 99), failed=len(fail))
 
-    th = threading.Thread(target=poller)
-    th.start()
-    t0 = time.perf_counter()
-    ready.set()
-    for i in range(n_requests):
-        dt = t0 + arrivals[i] - time.perf_counter()
-        if dt > 0:
-            time.sleep(dt)
-        tickets[i] = srv.submit(pool[order[i]])
-    th.join()
-    srv.close()
-    served_wall = max(done_t) - t0
-    served = dict(solves_per_s=n_requests / served_wall, p50_ms=pct(lat, 50), p99_ms=pct(lat, 99),
-                  failed=len(fail))
+    def run_plain(arrivals):
+        lat = []
+        t0 = time.perf_counter()
+        fin = t0
+        for i in range(n_requests):
+            arr = t0 + (arrivals[i] if arrivals is not None else 0.0)
+            now = time.perf_counter()
+            if now < arr:
+                time.sleep(arr - now)
+            plain_solve(order[i])
+            fin = time.perf_counter()
+            lat.append(1e3 * (fin - arr))
+        return dict(solves_per_s=n_requests / (fin - t0), p50_ms=pct(lat, 50), p99_ms=pct(lat, 99))
 
-    # plain form: FIFO, one request at a time
-    lat2 = []
-    t0 = time.perf_counter()
-    free_at = t0
-    for i in range(n_requests):
-        arr = t0 + arrivals[i]
-        now = time.perf_counter()
-        if now < arr:
-            time.sleep(arr - now)
-        plain_solve(pool[order[i]])
-        fin = time.perf_counter()
-        lat2.append(1e3 * (fin - arr))
-        free_at = fin
-    plain_wall = free_at - t0
-    plain = dict(solves_per_s=n_requests / plain_wall, p50_ms=pct(lat2, 50), p99_ms=pct(lat2, 99))
-
-    # capacity: every request queued at once (served) / back to back (plain)
-    srv = pk.Server(max_inflight=8)
-    t0 = time.perf_counter()
-    tk = [srv.submit(pool[order[i]]) for i in range(n_requests)]
-    for t in tk:
-        srv.poll(t, timeout_ms=-1)
-    cap_served = n_requests / (time.perf_counter() - t0)
-    srv.close()
-    t0 = time.perf_counter()
-    for i in range(n_requests):
-        plain_solve(pool[order[i]])
-    cap_plain = n_requests / (time.perf_counter() - t0)
-    served["capacity_solves_per_s"] = cap_served
-    plain["capacity_solves_per_s"] = cap_plain
+    rng = np.random.default_rng(seed)
+    sweep = []
+    for load in loads:
+        rate = load / mean_svc
+        arrivals = np.cumsum(rng.exponential(1.0 / rate, size=n_requests))
+        sweep.append(dict(load_factor=load, arrival_rate_per_s=rate, served=run_served(arrivals),
+                          plain_fp32_single=run_plain(arrivals)))
+    capacity = dict(served=run_served(None)["solves_per_s"], plain_fp32_single=run_plain(None)["solves_per_s"])
+    diffs = [_pose_diff(served_res[i], plain_res[i]) for i in sorted(served_res) if i in plain_res]
+    accuracy = dict(compared=len(diffs), max_rot_rad=max(d[0] for d in diffs) if diffs else None,
+                    max_trans_m=max(d[1] for d in diffs) if diffs else None, tolerance=1e-4,
+                    against="plain FP32-label GPU solve of the same problem (same LM, max_iters each)")
     return dict(metric="served BA solves/s, p50/p99 latency", requests=n_requests, pool=pool_size,
-                arrival_rate_per_s=rate, load_factor=load_factor, max_iters=max_iters,
-                mean_single_stream_service_ms=1e3 * mean_svc,
-                pool_sizes=[[len(p["xyz"]), int(sum(len(x) for x in p["xyz"]))] for p in pool],
-                served=served, plain_fp32_single=plain,
-                note="solves_per_s and latencies under Poisson arrivals at load_factor x the plain "
-                     "single-stream capacity; capacity_solves_per_s with every request queued at once")
+                max_iters=max_iters, mean_single_stream_service_ms=1e3 * mean_svc,
+                pool_frames_points=[[len(p["xyz"]), int(sum(len(x) for x in p["xyz"]))] for p in pool],
+                loads=sweep, capacity_solves_per_s=capacity, accuracy=accuracy,
+                note="solves/s and latencies (submit to result) under Poisson arrivals at load_factor x the plain "
+                     "single-stream capacity; capacity with every request queued at once")
 
 
 def main():
@@ -564,13 +657,10 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-functions", action="store_true")
+    ap.add_argument("--no-secondary", action="store_true")
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(WORKLOADS),
                     help="other workloads of the paper's shapes (the driver uses the default)")
-    ap.add_argument("--oracle-sample", default=None)
     args = ap.parse_args()
-    if args.oracle_sample:
-        print(json.dumps(oracle_sample(args.oracle_sample)))
-        return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))

@@ -202,8 +202,8 @@ rkhsba_status rkhsba_profile(rkhsba_ctx* ctx, int32_t enable, double* ms, int64_
  * without allocating any device memory.  The paper has no counterpart; this
  * entry point exists for callers that cannot call cudaMalloc: code living
  * inside another runtime that owns the device memory through its own pool,
- * real-time loops that must not take allocator locks or face an allocation
- * failure mid-run, and code that may run while a stream is being captured.
+ * and real-time loops that must not take allocator locks or face an
+ * allocation failure mid-run.
  *
  * Every temporary buffer comes from one fixed 32 MiB device array inside the
  * library (each GPU that loads the library holds it until the process
@@ -212,10 +212,16 @@ rkhsba_status rkhsba_profile(rkhsba_ctx* ctx, int32_t enable, double* ms, int64_
  * grid cells <= 2^20 over all frames and over all edges' home cells;
  * larger problems return RKHSBA_EINVAL with a message and touch no memory
  * beyond the array.  The first call on a device looks up the array's device
- * address; make that first call before any stream capture on that device.
- * All calls share the array and reuse its contents (what must start at zero
- * is cleared in every call); calls whose GPU work overlaps (other streams or
- * other host threads) race on it, so the caller serialises them.
+ * address (cudaGetSymbolAddress); make that first call before any stream
+ * capture on that device.  All calls share the array and reuse its contents
+ * (what must start at zero is cleared in every call); calls whose GPU work
+ * overlaps (other streams or other host threads) race on it, so the caller
+ * serialises them.
+ *
+ * The call waits on its stream twice (the host lays out the grids from the
+ * frames' bounding boxes, then reads the results back), so it cannot run on
+ * a stream that is being captured: it returns RKHSBA_EINVAL there without
+ * touching the stream.
  *
  *   n_frames, n_points, edges, params  as for rkhsba_create
  *   d_xyz, d_sem, d_rgb   DEVICE inputs laid out as for rkhsba_create
@@ -230,6 +236,26 @@ rkhsba_status rkhsba_eval_static(int32_t n_frames, const int64_t* n_points, cons
                                  const int32_t* edges, const rkhsba_params* params,
                                  const double* poses, double* loss, double* grad, double* H_full,
                                  void* cuda_stream);
+
+/*
+ * rkhsba_selftest_lookback_timeout -- failure-detection self-test of the
+ * bounded device waits (the paper has no counterpart).  The radix sort of
+ * the grid build and of the query binning passes tile counts between blocks
+ * by decoupled look-back; every wait on another block's record polls at most
+ * a fixed number of times, then raises an error word that the calling entry
+ * point reports as RKHSBA_ETIMEOUT (the kernel returns, the context stays
+ * usable).  This call makes such a wait run out on purpose: one pass over two
+ * tiles of keys whose only block takes the second tile while the first
+ * tile's record is never published.
+ *
+ *   spin_limit        polls before the wait gives up, 1 .. 2^20 (else EINVAL)
+ *   writes_in_bounds  HOST out (may be NULL): 1 when the guard words on both
+ *                     sides of the output arrays are untouched
+ * Returns RKHSBA_ETIMEOUT when the wait gave up (the expected outcome),
+ * RKHSBA_OK if it did not, ECUDA on a runtime error.  Allocates and frees its
+ * own small buffers; synchronises the device.
+ */
+rkhsba_status rkhsba_selftest_lookback_timeout(int32_t spin_limit, int32_t* writes_in_bounds);
 
 /* ------------------------------------------------------------------------
  * Function-space distance and cosine (Sec. III-A, Eq. dist_rkhs).

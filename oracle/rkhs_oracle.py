@@ -18,7 +18,7 @@ Everything here is slow, obvious numpy in float64, written from the paper
   * Levenberg-Marquardt on the IRLS problem, accepted while the
     original cost F increases                                           Sec. V-A (Ceres), Sec. V-C
 
-Readings of points the paper leaves open (each also listed in the design doc):
+Readings of points the paper leaves open:
   * sigma = 1 unless given; the sparse sum keeps pairs with |d|^2 < r_c^2,
     r_c = cutoff_mult * ell (strict, float64), without renormalisation.
   * c_ij = <l_i, l_j> * exp(-|c_i - c_j|^2 / (2 ell_c^2)) when colours are

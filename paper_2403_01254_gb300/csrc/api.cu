@@ -6,6 +6,7 @@
 // arguments, sizes buffers and issues kernels; every step of the objective,
 // its derivatives and the solve runs on the device.
 #include "context.cuh"
+#include "layout.cuh"
 #include "rkhsba.h"
 
 #include <algorithm>
@@ -53,21 +54,6 @@ rkhsba_status alloc(rkhsba_ctx* ctx, T** out, long long count) {
     return RKHSBA_OK;
 }
 
-// label row padding: the pair kernel is instantiated for these widths only
-int sem_pad_for(int dim, bool bf16) {
-    if (dim <= 0) return 0;
-    static const int pads_f32[] = {4, 8, 12, 16, 20, 24, 32};
-    static const int pads_bf16[] = {8, 16, 24, 32};
-    if (bf16) {
-        for (int pd : pads_bf16)
-            if (dim <= pd) return pd;
-        return 0;
-    }
-    for (int pd : pads_f32)
-        if (dim <= pd) return pd;
-    return 0;
-}
-
 rkhsba_status normalize_params(rkhsba_ctx* ctx, const rkhsba_params* in) {
     if (!in) return fail(ctx, RKHSBA_EINVAL, "params is NULL");
     rkhsba_params p = *in;
@@ -88,23 +74,8 @@ rkhsba_status normalize_params(rkhsba_ctx* ctx, const rkhsba_params* in) {
     if (!(p.sem_min >= 0.0) || !std::isfinite(p.sem_min))
         return fail(ctx, RKHSBA_EINVAL, "params.sem_min must be finite and >= 0");
     ctx->p = p;
-    const double rc = p.cutoff_mult * p.ell;
-    GridParams& g = ctx->gp;
-    g.h = rc * (1.0 + 1.0 / 1024.0);
-    g.h_inv = 1.0 / g.h;
-    g.hf = (float)g.h;
-    g.hf_inv = (float)g.h_inv;
-    g.hf_lo = (float)(g.h - (double)g.hf);
-    g.rc2 = (float)(rc * rc);
-    const double log2e = 1.4426950408889634;
-    g.kg = (float)(-log2e / (2.0 * p.ell * p.ell));
-    g.color = 0;
-    g.kc = 0.f;
-    g.sem_dim = p.sem_dim;
-    g.sem_bf16 = p.sem_bf16 ? 1 : 0;
-    g.sem_pad = sem_pad_for(p.sem_dim, g.sem_bf16);
-    g.top_k = p.top_k;
-    g.sem_min = (p.sem_min > 0.0 && p.sem_dim > 0) ? (float)p.sem_min : -__builtin_huge_valf();
+    ctx->gp = grid_params_for(p);
+    const GridParams& g = ctx->gp;
     if (p.sem_dim > 0 && g.sem_pad == 0) return fail(ctx, RKHSBA_EINVAL, "unsupported sem_dim");
     return RKHSBA_OK;
 }
@@ -160,14 +131,6 @@ void grid_fill(rkhsba_ctx* c, bool* keys_in_alt) {
     *keys_in_alt = alt;
 }
 
-double bound_exp_scale(double bound, float* scale) {
-    if (!(bound > 0.0) || !std::isfinite(bound)) bound = 1.0;
-    int e = 61 - (int)std::ceil(std::log2(bound));
-    e = std::max(-120, std::min(120, e));
-    *scale = std::ldexp(1.0f, e);
-    return std::ldexp(1.0, -e);
-}
-
 // Freed context memory stays in the device's default pool for the next
 // context instead of going back to the driver (set once per device).
 void keep_pool_warm(int dev) {
@@ -201,11 +164,7 @@ rkhsba_status build(rkhsba_ctx* c, const double* xyz, const float* sem, const fl
     const bool has_sem = c->p.sem_dim > 0;
     if (has_sem != (sem != nullptr))
         return fail(c, RKHSBA_EINVAL, "sem must be given exactly when params.sem_dim > 0");
-    c->gp.color = (rgb != nullptr && c->p.ell_color > 0.0) ? 1 : 0;
-    if (c->gp.color) {
-        const double log2e = 1.4426950408889634;
-        c->gp.kc = (float)(-log2e / (2.0 * c->p.ell_color * c->p.ell_color));
-    }
+    grid_params_color(c->gp, rgb != nullptr && c->p.ell_color > 0.0, c->p.ell_color);
     const float* rgb_used = c->gp.color ? rgb : nullptr;
 
     // raw inputs
@@ -251,33 +210,10 @@ rkhsba_status build(rkhsba_ctx* c, const double* xyz, const float* sem, const fl
 
     // grid layout per frame (dense, one-cell margin)
     c->frames_h.assign(K, FrameDev{});
-    long long coff = 0;
-    for (int m = 0; m < K; ++m) {
-        FrameDev& F = c->frames_h[m];
-        F.pt_off = c->pt_off[m];
-        F.n_pts = (int)(c->pt_off[m + 1] - c->pt_off[m]);
-        long long cells = 1;
-        for (int k = 0; k < 3; ++k) {
-            if (F.n_pts > 0) {
-                F.lo[k] = cmin[3 * m + k] - 1;
-                long long d = (long long)cmax[3 * m + k] - cmin[3 * m + k] + 3;
-                if (d > (1LL << 20)) return fail(c, RKHSBA_EINVAL, "frame extent exceeds 2^20 grid cells per axis");
-                F.dim[k] = (int)d;
-            } else {
-                F.lo[k] = 0;
-                F.dim[k] = 1;
-            }
-            cells *= F.dim[k];
-        }
-        if (cells > (1LL << 30)) return fail(c, RKHSBA_EINVAL, "frame grid larger than 2^30 cells");
-        F.cell_off = coff;
-        coff += cells;
-        float nrm;
-        std::memcpy(&nrm, &semn[m], sizeof(float));
-        F.sem_norm_max = has_sem ? nrm : 1.0f;
-    }
-    c->C_total = coff;
-    if (c->C_total >= (1LL << 31) - 2) return fail(c, RKHSBA_EINVAL, "total grid cells exceed 2^31");
+    if (const char* msg = layout_frames(c->frames_h.data(), K, c->pt_off.data(), cmin.data(), cmax.data(),
+                                        semn.data(), has_sem, 1LL << 20, 1LL << 30, (1LL << 31) - 2,
+                                        &c->C_total))
+        return fail(c, RKHSBA_EINVAL, std::string(msg) + " (2^20 per axis, 2^30 per frame, 2^31 in all)");
     RK_TRY(alloc(c, &c->d_frames, K));
     RK_CUDA(c, cudaMemcpyAsync(c->d_frames, c->frames_h.data(), sizeof(FrameDev) * K,
                                cudaMemcpyHostToDevice, st));
@@ -301,17 +237,10 @@ rkhsba_status build(rkhsba_ctx* c, const double* xyz, const float* sem, const fl
     RK_TRY(alloc(c, &c->d_run, N));
     RK_TRY(alloc(c, &c->d_total, 4));
 
-    // per-edge sizes: bins = cells of frame a's grid, queries = points of frame b
-    c->total_bins = 0;
-    c->Q_total = 0;
-    for (int e = 0; e < E; ++e) {
-        EdgeDev& Ed = c->edges_h[e];
-        const FrameDev& Fa = c->frames_h[Ed.a];
-        Ed.bin_off = c->total_bins;
-        Ed.q_off = c->Q_total;
-        c->total_bins += (long long)Fa.dim[0] * Fa.dim[1] * Fa.dim[2];
-        c->Q_total += c->frames_h[Ed.b].n_pts;
-    }
+    // per-edge sizes (bins = cells of frame a's grid, queries = points of
+    // frame b) and fixed-point scales
+    const double rc = c->p.cutoff_mult * c->p.ell;
+    layout_edges(c->edges_h.data(), E, c->frames_h.data(), c->gp, rc, &c->total_bins, &c->Q_total);
     if (c->total_bins >= (1LL << 31) - 2) return fail(c, RKHSBA_EINVAL, "total home cells exceed 2^31");
     if (c->Q_total >= (1LL << 31) - 64) return fail(c, RKHSBA_EINVAL, "more than 2^31 queries over all edges");
     c->qbits = 1;
@@ -324,38 +253,12 @@ rkhsba_status build(rkhsba_ctx* c, const double* xyz, const float* sem, const fl
     grid_fill(c, &alt);
     RK_CUDA(c, cudaGetLastError());
 
-    // fixed-point scales per edge and moment class
-    const double rc = c->p.cutoff_mult * c->p.ell;
-    for (int e = 0; e < E; ++e) {
-        EdgeDev& Ed = c->edges_h[e];
-        const FrameDev& Fa = c->frames_h[Ed.a];
-        const FrameDev& Fb = c->frames_h[Ed.b];
-        double smax = (double)Fa.sem_norm_max * (double)Fb.sem_norm_max * (1.0 + 1e-6) + 1e-30;
-        double Wb = (double)std::max(Fa.n_pts, 1) * (double)std::max(Fb.n_pts, 1) * smax;
-        double R2 = 0.0;
-        for (int k = 0; k < 3; ++k) {
-            double lo = Fa.lo[k] * c->gp.h, hi = (Fa.lo[k] + Fa.dim[k]) * c->gp.h;
-            double mm = std::max(std::fabs(lo), std::fabs(hi));
-            R2 += mm * mm;
-        }
-        double R = std::sqrt(R2) + c->gp.h;
-        double bounds[MC_N] = {Wb, Wb * rc, Wb * R, Wb * R * R, Wb * rc * R, Wb * rc * rc, 1.0, 1.0};
-        for (int k = 0; k < MC_N; ++k) Ed.inv_scale[k] = bound_exp_scale(bounds[k], &Ed.scale[k]);
-        Ed.scale[MC_CNT] = 1.0f;
-        Ed.inv_scale[MC_CNT] = 1.0;
-    }
     RK_TRY(alloc(c, &c->d_edges, E));
     RK_CUDA(c, cudaMemcpyAsync(c->d_edges, c->edges_h.data(), sizeof(EdgeDev) * E,
                                cudaMemcpyHostToDevice, st));
     // incidence lists (frame -> edges), edge order kept
-    std::vector<int> inc_off(K + 1, 0), inc_list;
-    for (int m = 0; m < K; ++m) {
-        for (int e = 0; e < E; ++e) {
-            if (c->edges_h[e].a == m) inc_list.push_back(2 * e);
-            if (c->edges_h[e].b == m) inc_list.push_back(2 * e + 1);
-        }
-        inc_off[m + 1] = (int)inc_list.size();
-    }
+    std::vector<int> inc_off(K + 1, 0), inc_list(2 * (size_t)E + 1, 0);
+    inc_list.resize(incidence_lists(c->edges_h.data(), E, K, inc_off.data(), inc_list.data()));
     RK_TRY(alloc(c, &c->d_inc_off, K + 1));
     RK_TRY(alloc(c, &c->d_inc_list, (long long)inc_list.size()));
     RK_CUDA(c, cudaMemcpyAsync(c->d_inc_off, inc_off.data(), sizeof(int) * (K + 1), cudaMemcpyHostToDevice, st));

@@ -1,24 +1,28 @@
 // rkhsba_eval_static: one evaluation with no device allocation.
 //
 // Some callers cannot call cudaMalloc at all: code that runs inside another
-// runtime which owns every device byte through its own pool, plug-ins and
+// runtime which owns every device byte through its own pool, and plug-ins or
 // real-time loops that must not take the allocator's locks or risk an
-// allocation failure mid-run, and code that may be called while a CUDA graph
-// is being captured on the stream.  For them this entry point evaluates a
-// small problem with the same kernels as rkhsba_eval, but every temporary
-// buffer is carved out of one file-scope device array, g_scratch, of fixed
-// size.  The caller passes device pointers to the points and labels and host
-// buffers for the results.
+// allocation failure mid-run.  For them this entry point evaluates a small
+// problem with the same kernels as rkhsba_eval, but every temporary buffer is
+// carved out of one file-scope device array, g_scratch, of fixed size.  The
+// caller passes device pointers to the points and labels and host buffers
+// for the results.  The host-side layout (grids, edge offsets, fixed-point
+// scales, incidence lists) comes from the same helpers as the context path
+// (layout.cuh).
 //
 // g_scratch is held by every GPU that loads the library, for as long as the
 // library stays loaded.  Its device address is obtained once per device with
 // cudaGetSymbolAddress (in host code the symbol names a host-side stand-in,
 // not device memory); that happens in the first call on each device, so the
 // first call on a device must not be made while a stream is being captured.
-// Every call uses the same array: two calls whose work overlaps on the GPU
-// (different streams, or different host threads) overwrite each other's
-// temporaries, so calls must be serialised by the caller.
+// The call waits on its stream (bounding boxes, results), so it refuses a
+// stream under capture.  Every call uses the same array: two calls whose work
+// overlaps on the GPU (different streams, or different host threads)
+// overwrite each other's temporaries, so calls must be serialised by the
+// caller.
 #include "common.cuh"
+#include "layout.cuh"
 #include "rkhsba.h"
 
 #include <cmath>
@@ -85,28 +89,6 @@ struct Carve {
     }
 };
 
-int pad_for(int dim, bool bf16) {
-    if (dim <= 0) return 0;
-    static const int f32[] = {4, 8, 12, 16, 20, 24, 32};
-    static const int b16[] = {8, 16, 24, 32};
-    if (bf16) {
-        for (int p : b16)
-            if (dim <= p) return p;
-        return 0;
-    }
-    for (int p : f32)
-        if (dim <= p) return p;
-    return 0;
-}
-
-double scale_for(double bound, float* scale) {
-    if (!(bound > 0.0) || !std::isfinite(bound)) bound = 1.0;
-    int e = 61 - (int)std::ceil(std::log2(bound));
-    e = e < -120 ? -120 : (e > 120 ? 120 : e);
-    *scale = std::ldexp(1.0f, e);
-    return std::ldexp(1.0, -e);
-}
-
 #define SCK(call)                                                                              \
     do {                                                                                       \
         cudaError_t _e = (call);                                                               \
@@ -160,32 +142,28 @@ extern "C" rkhsba_status rkhsba_eval_static(int32_t n_frames, const int64_t* n_p
                 if (!(std::fabs(s - (i == j ? 1.0 : 0.0)) <= 1e-9)) return fail(RKHSBA_EINVAL, "non-orthonormal pose");
             }
 
-    GridParams gp{};
-    const double rc = p.cutoff_mult * p.ell;
-    gp.h = rc * (1.0 + 1.0 / 1024.0);
-    gp.h_inv = 1.0 / gp.h;
-    gp.hf = (float)gp.h;
-    gp.hf_inv = (float)gp.h_inv;
-    gp.hf_lo = (float)(gp.h - (double)gp.hf);
-    gp.rc2 = (float)(rc * rc);
-    const double log2e = 1.4426950408889634;
-    gp.kg = (float)(-log2e / (2.0 * p.ell * p.ell));
-    gp.color = (d_rgb != nullptr && p.ell_color > 0.0) ? 1 : 0;
-    gp.kc = gp.color ? (float)(-log2e / (2.0 * p.ell_color * p.ell_color)) : 0.f;
-    gp.sem_dim = p.sem_dim;
-    gp.sem_bf16 = p.sem_bf16 ? 1 : 0;
-    gp.sem_pad = pad_for(p.sem_dim, gp.sem_bf16);
-    if (p.sem_dim > 0 && gp.sem_pad == 0) return fail(RKHSBA_EINVAL, "unsupported sem_dim");
     if (p.top_k < 0 || p.top_k > TOPK_MAX) return fail(RKHSBA_EINVAL, "params.top_k must be in [0, 8]");
     if (!(p.sem_min >= 0.0) || !std::isfinite(p.sem_min))
         return fail(RKHSBA_EINVAL, "params.sem_min must be finite and >= 0");
-    gp.top_k = p.top_k;
-    gp.sem_min = (p.sem_min > 0.0 && p.sem_dim > 0) ? (float)p.sem_min : -__builtin_huge_valf();
+    const double rc = p.cutoff_mult * p.ell;
+    GridParams gp = grid_params_for(p);
+    grid_params_color(gp, d_rgb != nullptr && p.ell_color > 0.0, p.ell_color);
+    if (p.sem_dim > 0 && gp.sem_pad == 0) return fail(RKHSBA_EINVAL, "unsupported sem_dim");
+
+    // the call waits on its stream for the bounding boxes and the results;
+    // on a stream under capture those waits would fail and end the caller's
+    // capture, so such a stream is refused before anything is issued on it
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    {
+        cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+        SCK(cudaStreamIsCapturing(st, &cap));
+        if (cap != cudaStreamCaptureStatusNone)
+            return fail(RKHSBA_EINVAL, "rkhsba_eval_static waits on its stream and cannot run on a stream under capture");
+    }
 
     unsigned char* base = nullptr;
     rkhsba_status st0 = scratch_base(&base);
     if (st0 != RKHSBA_OK) return st0;
-    cudaStream_t st = (cudaStream_t)cuda_stream;
     int dev = 0, num_sms = 1;
     SCK(cudaGetDevice(&dev));
     SCK(cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev));
@@ -224,70 +202,20 @@ extern "C" rkhsba_status rkhsba_eval_static(int32_t n_frames, const int64_t* n_p
 
     // ---- grid layout, edges, fixed-point scales (host) ----
     FrameDev fh[MAX_K];
-    std::memset(fh, 0, sizeof(fh));
     long long C = 0;
-    for (int m = 0; m < K; ++m) {
-        FrameDev& F = fh[m];
-        F.pt_off = pt_off[m];
-        F.n_pts = (int)(pt_off[m + 1] - pt_off[m]);
-        long long cells = 1;
-        for (int k = 0; k < 3; ++k) {
-            if (F.n_pts > 0) {
-                F.lo[k] = cmin[3 * m + k] - 1;
-                const long long d = (long long)cmax[3 * m + k] - cmin[3 * m + k] + 3;
-                if (d > MAX_CELLS) return fail(RKHSBA_EINVAL, "rkhsba_eval_static: grid larger than 2^20 cells");
-                F.dim[k] = (int)d;
-            } else {
-                F.lo[k] = 0;
-                F.dim[k] = 1;
-            }
-            cells *= F.dim[k];
-            if (cells > MAX_CELLS) return fail(RKHSBA_EINVAL, "rkhsba_eval_static: grid larger than 2^20 cells");
-        }
-        F.cell_off = C;
-        C += cells;
-        float nrm;
-        std::memcpy(&nrm, &semn[m], sizeof(float));
-        F.sem_norm_max = p.sem_dim > 0 ? nrm : 1.0f;
-    }
-    if (C > MAX_CELLS) return fail(RKHSBA_EINVAL, "rkhsba_eval_static: more than 2^20 grid cells");
+    if (const char* msg = layout_frames(fh, K, pt_off, cmin, cmax, semn, p.sem_dim > 0, MAX_CELLS, MAX_CELLS,
+                                        MAX_CELLS + 1, &C))
+        return fail(RKHSBA_EINVAL, std::string("rkhsba_eval_static: ") + msg + " (2^20 grid cells at most)");
     long long bins = 0, Q = 0;
-    for (int e = 0; e < E; ++e) {
-        const FrameDev& Fa = fh[eh[e].a];
-        const FrameDev& Fb = fh[eh[e].b];
-        eh[e].bin_off = bins;
-        eh[e].q_off = Q;
-        bins += (long long)Fa.dim[0] * Fa.dim[1] * Fa.dim[2];
-        Q += Fb.n_pts;
-        const double smax = (double)Fa.sem_norm_max * (double)Fb.sem_norm_max * (1.0 + 1e-6) + 1e-30;
-        const double Wb = (double)(Fa.n_pts > 0 ? Fa.n_pts : 1) * (double)(Fb.n_pts > 0 ? Fb.n_pts : 1) * smax;
-        double R2 = 0.0;
-        for (int k = 0; k < 3; ++k) {
-            const double lo = Fa.lo[k] * gp.h, hi = (Fa.lo[k] + Fa.dim[k]) * gp.h;
-            const double mm = std::fabs(lo) > std::fabs(hi) ? std::fabs(lo) : std::fabs(hi);
-            R2 += mm * mm;
-        }
-        const double R = std::sqrt(R2) + gp.h;
-        const double bounds[MC_N] = {Wb, Wb * rc, Wb * R, Wb * R * R, Wb * rc * R, Wb * rc * rc, 1.0, 1.0};
-        for (int k = 0; k < MC_N; ++k) eh[e].inv_scale[k] = scale_for(bounds[k], &eh[e].scale[k]);
-        eh[e].scale[MC_CNT] = 1.0f;
-        eh[e].inv_scale[MC_CNT] = 1.0;
-    }
+    layout_edges(eh, E, fh, gp, rc, &bins, &Q);
     if (bins > MAX_BINS) return fail(RKHSBA_EINVAL, "rkhsba_eval_static: more than 2^20 home cells over all edges");
     if (Q > MAX_Q) return fail(RKHSBA_EINVAL, "rkhsba_eval_static: more than 131072 queries over all edges");
     int qbits = 1;
     while ((1LL << qbits) <= bins) ++qbits;
     int cbits = 0;
     while ((1LL << cbits) < C) ++cbits;
-    int inc_off[MAX_K + 1], inc_list[2 * MAX_E], ninc = 0;
-    inc_off[0] = 0;
-    for (int m = 0; m < K; ++m) {
-        for (int e = 0; e < E; ++e) {
-            if (eh[e].a == m) inc_list[ninc++] = 2 * e;
-            if (eh[e].b == m) inc_list[ninc++] = 2 * e + 1;
-        }
-        inc_off[m + 1] = ninc;
-    }
+    int inc_off[MAX_K + 1], inc_list[2 * MAX_E];
+    const int ninc = incidence_lists(eh, E, K, inc_off, inc_list);
 
     // ---- large arrays ----
     const int sp = gp.sem_pad;

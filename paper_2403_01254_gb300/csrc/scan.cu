@@ -15,6 +15,8 @@
 // word and the kernel finishes with what it has.
 #include "common.cuh"
 
+#include <vector>
+
 namespace rk {
 
 namespace {
@@ -26,7 +28,7 @@ constexpr int MAX_PASS = 4;
 constexpr unsigned long long ST_AGG = 1ull << 62;      // count = this tile's
 constexpr unsigned long long ST_PRE = 2ull << 62;      // count = tiles 0..t inclusive
 constexpr unsigned long long ST_CNT = (1ull << 62) - 1ull;
-constexpr int SPIN_LIMIT = 1 << 22;
+constexpr int SPIN_LIMIT = 1 << 22;         // polls of one look-back wait before it gives up
 
 __global__ void __launch_bounds__(RAD_T) k_radix_counts(const uint32_t* __restrict__ keys, long long n,
                                                         int npass, unsigned long long* __restrict__ counts) {
@@ -70,7 +72,8 @@ __global__ void __launch_bounds__(RAD_T) k_onesweep(const uint32_t* __restrict__
                                                     uint32_t* __restrict__ kout, int* __restrict__ vout,
                                                     long long n, int shift,
                                                     const unsigned long long* __restrict__ counts,
-                                                    unsigned long long* status, int* tile_ctr, int* err) {
+                                                    unsigned long long* status, int* tile_ctr, int* err,
+                                                    int spin_limit) {
     __shared__ int s_tile;
     __shared__ int run[256];
     __shared__ int wcnt[RAD_WARPS][256];
@@ -136,7 +139,7 @@ __global__ void __launch_bounds__(RAD_T) k_onesweep(const uint32_t* __restrict__
             unsigned long long v = *sp;
             int spins = 0;
             while ((v >> 62) == 0ull) {
-                if (++spins > SPIN_LIMIT) {   // give up: the prefix stays short, writes stay in bounds
+                if (++spins > spin_limit) {   // give up: the prefix stays short, writes stay in bounds
                     atomicOr(err, 1);
                     gave_up = true;
                     break;
@@ -189,7 +192,7 @@ void radix_sort_u32(uint32_t* keys, int* vals, uint32_t* keys_alt, int* vals_alt
     int* vo = vals_alt;
     for (int p = 0; p < npass; ++p) {
         k_onesweep<<<nb, RAD_T, 0, st>>>(ki, vi, ko, vo, n, 8 * p, counts + 256 * p,
-                                         status + (size_t)256 * nb * p, ctr + p, err);
+                                         status + (size_t)256 * nb * p, ctr + p, err, SPIN_LIMIT);
         count_launch();
         uint32_t* tk = ki; ki = ko; ko = tk;
         int* tv = vi; vi = vo; vo = tv;
@@ -198,3 +201,88 @@ void radix_sort_u32(uint32_t* keys, int* vals, uint32_t* keys_alt, int* vals_alt
 }
 
 }  // namespace rk
+
+// Failure-detection self-test of the look-back's bounded wait (declared in
+// include/rkhsba.h).  Two tiles of keys; tile_ctr starts at 1, so the single
+// launched block takes tile 1 while the record of tile 0 is never published.
+// Every thread of the block then polls a record that stays zero, gives up
+// after spin_limit polls, raises the error word and finishes with a short
+// prefix (zero): each output index is the digit's base from the global counts
+// plus the key's rank inside tile 1, below n, so all writes land inside the
+// output arrays.  Guard words on both sides of the outputs are checked.
+extern "C" rkhsba_status rkhsba_selftest_lookback_timeout(int32_t spin_limit, int32_t* writes_in_bounds) {
+    using namespace rk;
+    if (writes_in_bounds) *writes_in_bounds = 0;
+    if (spin_limit < 1 || spin_limit > (1 << 20)) {
+        set_thread_error("rkhsba_selftest_lookback_timeout: spin_limit must be in [1, 2^20]");
+        return RKHSBA_EINVAL;
+    }
+    const long long n = 2LL * RAD_TILE;
+    const long long G = 256;                        // guard words on each side of the outputs
+    uint32_t* kin = nullptr;
+    uint32_t* kout = nullptr;
+    int* vin = nullptr;
+    int* vout = nullptr;
+    unsigned long long* status = nullptr;
+    unsigned long long* counts = nullptr;
+    int* ctl = nullptr;                              // [0] tile counter, [1] error word
+    auto release = [&] {
+        cudaFree(kin); cudaFree(kout); cudaFree(vin); cudaFree(vout);
+        cudaFree(status); cudaFree(counts); cudaFree(ctl);
+    };
+    auto cuda_fail = [&](cudaError_t e) {
+        release();
+        cudaGetLastError();
+        set_thread_error(cudaGetErrorString(e));
+        return RKHSBA_ECUDA;
+    };
+    cudaError_t e = cudaSuccess;
+    if ((e = cudaMalloc(&kin, sizeof(uint32_t) * n)) != cudaSuccess) return cuda_fail(e);
+    if ((e = cudaMalloc(&vin, sizeof(int) * n)) != cudaSuccess) return cuda_fail(e);
+    if ((e = cudaMalloc(&kout, sizeof(uint32_t) * (n + 2 * G))) != cudaSuccess) return cuda_fail(e);
+    if ((e = cudaMalloc(&vout, sizeof(int) * (n + 2 * G))) != cudaSuccess) return cuda_fail(e);
+    if ((e = cudaMalloc(&status, sizeof(unsigned long long) * 2 * 256)) != cudaSuccess) return cuda_fail(e);
+    if ((e = cudaMalloc(&counts, sizeof(unsigned long long) * 256)) != cudaSuccess) return cuda_fail(e);
+    if ((e = cudaMalloc(&ctl, sizeof(int) * 2)) != cudaSuccess) return cuda_fail(e);
+    std::vector<uint32_t> hk(n);
+    std::vector<int> hv(n);
+    for (long long i = 0; i < n; ++i) {
+        hk[i] = (uint32_t)((unsigned long long)(i + 1) * 2654435761ull);
+        hv[i] = (int)i;
+    }
+    const int ctl0[2] = {1, 0};
+    if ((e = cudaMemcpy(kin, hk.data(), sizeof(uint32_t) * n, cudaMemcpyHostToDevice)) != cudaSuccess) return cuda_fail(e);
+    if ((e = cudaMemcpy(vin, hv.data(), sizeof(int) * n, cudaMemcpyHostToDevice)) != cudaSuccess) return cuda_fail(e);
+    if ((e = cudaMemset(kout, 0xAB, sizeof(uint32_t) * (n + 2 * G))) != cudaSuccess) return cuda_fail(e);
+    if ((e = cudaMemset(vout, 0xAB, sizeof(int) * (n + 2 * G))) != cudaSuccess) return cuda_fail(e);
+    if ((e = cudaMemset(status, 0, sizeof(unsigned long long) * 2 * 256)) != cudaSuccess) return cuda_fail(e);
+    if ((e = cudaMemset(counts, 0, sizeof(unsigned long long) * 256)) != cudaSuccess) return cuda_fail(e);
+    if ((e = cudaMemcpy(ctl, ctl0, sizeof(ctl0), cudaMemcpyHostToDevice)) != cudaSuccess) return cuda_fail(e);
+    k_radix_counts<<<2, RAD_T>>>(kin, n, 1, counts);
+    count_launch();
+    k_onesweep<<<1, RAD_T>>>(kin, vin, kout + G, vout + G, n, 0, counts, status, ctl, ctl + 1, spin_limit);
+    count_launch();
+    if ((e = cudaDeviceSynchronize()) != cudaSuccess) return cuda_fail(e);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e);
+    int ctl1[2] = {0, 0};
+    std::vector<uint32_t> gk(n + 2 * G);
+    std::vector<int> gv(n + 2 * G);
+    if ((e = cudaMemcpy(ctl1, ctl, sizeof(ctl1), cudaMemcpyDeviceToHost)) != cudaSuccess) return cuda_fail(e);
+    if ((e = cudaMemcpy(gk.data(), kout, sizeof(uint32_t) * (n + 2 * G), cudaMemcpyDeviceToHost)) != cudaSuccess)
+        return cuda_fail(e);
+    if ((e = cudaMemcpy(gv.data(), vout, sizeof(int) * (n + 2 * G), cudaMemcpyDeviceToHost)) != cudaSuccess)
+        return cuda_fail(e);
+    release();
+    bool guards = true;
+    for (long long i = 0; i < G; ++i) {
+        guards = guards && gk[i] == 0xABABABABu && gk[n + G + i] == 0xABABABABu;
+        guards = guards && gv[i] == (int)0xABABABABu && gv[n + G + i] == (int)0xABABABABu;
+    }
+    if (writes_in_bounds) *writes_in_bounds = guards ? 1 : 0;
+    if (ctl1[1]) {
+        set_thread_error("a bounded wait of the radix sort's look-back gave up (self-test)");
+        return RKHSBA_ETIMEOUT;
+    }
+    set_thread_error("");
+    return RKHSBA_OK;
+}

@@ -23,7 +23,8 @@ EXPORTS = [
     "rkhsba_edge_pairs", "rkhsba_info", "rkhsba_last_error", "rkhsba_launch_count",
     "rkhsba_profile", "rkhsba_server_create", "rkhsba_server_destroy", "rkhsba_submit",
     "rkhsba_poll", "rkhsba_cancel", "rkhsba_server_stats", "rkhsba_inner_products",
-    "rkhsba_rotation_search", "rkhsba_solve_ell_decay",
+    "rkhsba_rotation_search", "rkhsba_solve_ell_decay", "rkhsba_eval_static",
+    "rkhsba_selftest_lookback_timeout",
 ]
 
 
@@ -119,6 +120,7 @@ def load(build_if_missing=True):
                                    P(C.c_double), P(C.c_int32)],
         "rkhsba_solve_ell_decay": [vp, P(EllSchedule), P(C.c_double), P(C.c_double), P(C.c_double),
                                    P(EllInfo)],
+        "rkhsba_selftest_lookback_timeout": [C.c_int32, P(C.c_int32)],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -319,6 +321,16 @@ def rkhsba_solve_ell_decay(ctx, poses, K, decay=0.1, ell_min=0.0, max_outer=10):
                                     status=STATUS_NAMES[info.status], ell_final=info.ell_final,
                                     final_loss=info.final_loss, iters=int(info.iters),
                                     pair_terms=int(info.pair_terms))
+
+
+def rkhsba_selftest_lookback_timeout(spin_limit=1000):
+    """Make one bounded look-back wait of the radix sort run out (failure
+    detection self-test).  Returns (status name, writes_in_bounds)."""
+    ok = C.c_int32(0)
+    st = load().rkhsba_selftest_lookback_timeout(int(spin_limit), C.byref(ok))
+    if st not in (OK, ETIMEOUT):
+        _check(st)
+    return STATUS_NAMES[st], bool(ok.value)
 
 
 def rkhsba_launch_count():

@@ -293,34 +293,45 @@ def _street_primitives(rng, x_range=(-70.0, 70.0), half_width=8.0):
 
 
 def _cast(origins, dirs, boxes, poles, rmin, rmax):
-    """Nearest hit distance and class per ray against ground/boxes/poles."""
+    """Nearest hit distance and class per ray against ground/boxes/poles.
+    Rays share one origin per scan; a box or pole farther than rmax from it
+    cannot give a hit in range and is skipped (the hit set, its distances and
+    classes do not change)."""
     n = len(dirs)
     best = np.full(n, np.inf)
     cls = np.full(n, -1, dtype=np.int64)
     o = origins
+    o0 = np.asarray(o[0], dtype=np.float64)
     # ground plane z = 0 (class 0 road)
     with np.errstate(divide="ignore", invalid="ignore"):
         t = -o[:, 2] / dirs[:, 2]
+        inv = 1.0 / dirs
     ok = (dirs[:, 2] < 0) & (t > 0) & (t < best)
     best[ok] = t[ok]
     cls[ok] = 0
-    # axis-aligned boxes (slab method)
+    # axis-aligned boxes (slab method); fmax/fmin skip the NaN of 0 * inf
     for lo, hi, c in boxes:
         lo = np.asarray(lo)
         hi = np.asarray(hi)
-        with np.errstate(divide="ignore", invalid="ignore"):
-            inv = 1.0 / dirs
-            t1 = (lo - o) * inv
-            t2 = (hi - o) * inv
-        tmin = np.nanmax(np.minimum(t1, t2), axis=1)
-        tmax = np.nanmin(np.maximum(t1, t2), axis=1)
+        gap = np.maximum(np.maximum(lo - o0, o0 - hi), 0.0)
+        if float(np.sqrt(gap @ gap)) > rmax:
+            continue
+        with np.errstate(invalid="ignore"):
+            t1 = (lo - o0) * inv
+            t2 = (hi - o0) * inv
+        a = np.minimum(t1, t2)
+        b = np.maximum(t1, t2)
+        tmin = np.fmax(np.fmax(a[:, 0], a[:, 1]), a[:, 2])
+        tmax = np.fmin(np.fmin(b[:, 0], b[:, 1]), b[:, 2])
         ok = (tmax >= tmin) & (tmin > 0) & (tmin < best)
         best[ok] = tmin[ok]
         cls[ok] = c
     # vertical cylinders
     for px, py, r, h, c in poles:
-        dx = o[:, 0] - px
-        dy = o[:, 1] - py
+        if math.hypot(o0[0] - px, o0[1] - py) - r > rmax:
+            continue
+        dx = o0[0] - px
+        dy = o0[1] - py
         a = dirs[:, 0] ** 2 + dirs[:, 1] ** 2
         b = 2 * (dx * dirs[:, 0] + dy * dirs[:, 1])
         cc = dx * dx + dy * dy - r * r

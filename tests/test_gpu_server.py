@@ -134,3 +134,29 @@ def test_shutdown_with_requests_in_flight(pk):
     t0 = time.time()
     srv.close()
     assert time.time() - t0 < 60
+
+
+def test_served_bf16_results_match_the_oracle(pk):
+    """Served results meet the pose tolerance against the FP64 oracle's LM on
+    the same inputs (labels rounded to BF16 by the generator, so the device's
+    BF16 rows hold them exactly), after the same number of LM iterations."""
+    import oracle as O
+    probs = []
+    for k, (K, n) in enumerate([(2, 3000), (3, 2000)]):
+        p = scenes.lidar_street_problem(seed=950 + k, n_frames=K, n_points=n, max_deg=3.0, max_trans=0.1,
+                                        sem_bf16=1)
+        p["params"] = dict(p["params"], max_iters=10)
+        probs.append(p)
+    srv = pk.Server(max_inflight=2)
+    try:
+        tickets = [srv.submit(p) for p in probs]
+        res = [srv.poll(t, timeout_ms=-1) for t in tickets]
+    finally:
+        srv.close()
+    for p, (T, info) in zip(probs, res):
+        assert info["state"] == "finished"
+        ref = O.lm_solve(p, params=dict(max_iters=10))
+        assert info["iters"] == ref["iters"]
+        dr = max(O.pose_error(a, b)[0] for a, b in zip(T, ref["poses"]))
+        dt = max(O.pose_error(a, b)[1] for a, b in zip(T, ref["poses"]))
+        assert dr <= 1e-4 and dt <= 1e-4, (dr, dt)
