@@ -262,11 +262,13 @@ def _flat_inputs(prob):
         edges=np.asarray(prob["edges"], np.int32))
 
 
-def measure_device(pk, rb, prob, steps, warmup, dev, stream, flush, world=1, clocks_index=None):
+def measure_device(pk, rb, prob, steps, warmup, dev, stream, flush, world=1, clocks_index=None, autotune=False):
     """Time `steps` bench steps of the resident problem with CUDA events on
     the library's stream (L2 flushed between steps, outside the events);
-    phase times from the library's own events.  Returns pair-terms per step,
-    summed step time, phase times, launch count and clock samples."""
+    phase times from the library's own events.  With autotune the library's
+    autotuner first times every pair-stage setting on this problem and the
+    fastest is used.  Returns pair-terms per step, summed step time, phase
+    times, launch count, clock samples and the tuning."""
     import torch
     f = _flat_inputs(prob)
     P = f["P"]
@@ -277,8 +279,18 @@ def measure_device(pk, rb, prob, steps, warmup, dev, stream, flush, world=1, clo
     rgb_d = torch.from_numpy(f["rgb"]).to(dev) if f["color"] else None
     poses_d = torch.from_numpy(f["poses0"]).to(dev)
     torch.cuda.synchronize()
+    tuning = None
+    if autotune:
+        best, table = rb.rkhsba_autotune(f["n_points"], xyz_d.data_ptr(), sem_d.data_ptr(),
+                                         rgb_d.data_ptr() if f["color"] else None, f["edges"], params,
+                                         f["poses0"], stream.cuda_stream, reps=2, on_device=True)
+        params.cell_scale = best["cell_scale"]
+        tuning = dict(chosen=best, table=table, timed="one evaluation (binning + pair stage + assembly), "
+                                                      "mean of 2 after 1 untimed, CUDA events")
     ctx = pk.rkhsba_create_device(f["n_points"], xyz_d.data_ptr(), sem_d.data_ptr(),
                                   rgb_d.data_ptr() if f["color"] else None, f["edges"], params, stream.cuda_stream)
+    if tuning:
+        rb.rkhsba_set_tuning(ctx, tuning["chosen"]["unit_queries"], tuning["chosen"]["ctas_per_sm"])
 
     def step():
         rb.rkhsba_rebuild(ctx)
@@ -322,7 +334,7 @@ def measure_device(pk, rb, prob, steps, warmup, dev, stream, flush, world=1, clo
         rb.rkhsba_destroy(ctx)
     ms = sum(a.elapsed_time(b) for a, b in ev)
     return dict(pairs_per_step=int(pairs_per_step), ms=ms, prof=prof, launches=int(n_launch), clocks=clk,
-                flat=f)
+                flat=f, tuning=tuning, params=params)
 
 
 def roofline_of(name, m, steps, dev, sm_max):
@@ -351,7 +363,7 @@ def roofline_of(name, m, steps, dev, sm_max):
                 phases_ms_per_step={k: v[0] / steps for k, v in m["prof"].items()})
 
 
-def measure_e2e(pk, rb, f, stream, n_steps):
+def measure_e2e(pk, rb, f, stream, n_steps, tuning=None):
     """Same metric through the public C ABI from pinned HOST buffers: each
     step is rkhsba_create (H2D of points and labels, grid build) +
     rkhsba_solve with max_iters 1 (two evaluations, D2H of the poses) +
@@ -370,13 +382,16 @@ def measure_e2e(pk, rb, f, stream, n_steps):
     rgb_p = pinned(f["rgb"], torch.float32)
     pos_p = pinned(f["poses0"], torch.float64)
     params1 = pk.make_params(P["ell"], P["cutoff_mult"], P["sigma"], P.get("ell_color", 0.0), f["sem_dim"],
-                             P.get("sem_bf16", 0), max_iters=1)
+                             P.get("sem_bf16", 0), max_iters=1,
+                             cell_scale=tuning["cell_scale"] if tuning else 1.0)
     pairs, secs = 0, 0.0
     for k in range(n_steps + 2):
         pos_p[:] = f["poses0"]
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         c2 = rb.rkhsba_create_flat(f["n_points"], xyz_p, sem_p, rgb_p, f["edges"], params1, stream.cuda_stream)
+        if tuning:
+            rb.rkhsba_set_tuning(c2, tuning["unit_queries"], tuning["ctas_per_sm"])
         T, info = rb.rkhsba_solve(c2, pos_p, f["K"])
         rb.rkhsba_destroy(c2)
         dt = time.perf_counter() - t0
@@ -387,7 +402,8 @@ def measure_e2e(pk, rb, f, stream, n_steps):
            f["edges"].nbytes + f["n_points"].nbytes)
     return dict(value=pairs / secs, unit=UNIT, h2d_bytes_per_step=int(h2d),
                 d2h_bytes_per_step=int(f["poses0"].nbytes + 64), steps=n_steps,
-                step="create (H2D + grids) + solve with max_iters 1 + destroy")
+                step="create (H2D + grids) + solve with max_iters 1 + destroy" +
+                     (", with the autotuned setting" if tuning else ""))
 
 
 def ours(args, rank, world, local_rank):
@@ -407,7 +423,8 @@ def ours(args, rank, world, local_rank):
     pk.load()
     stream = torch.cuda.Stream(device=dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
-    m = measure_device(pk, rb, prob, args.steps, args.warmup, dev, stream, flush, world, clocks_index=local_rank)
+    m = measure_device(pk, rb, prob, args.steps, args.warmup, dev, stream, flush, world, clocks_index=local_rank,
+                       autotune=not args.no_autotune)
     value, ms_max = replica_throughput(m["ms"], m["pairs_per_step"], args.steps, world, dev)
     clk = m["clocks"]
     sm_max = (clk or {}).get("sm_max_mhz") or 2070.0
@@ -416,7 +433,8 @@ def ours(args, rank, world, local_rank):
 
     e2e = None
     if not args.no_e2e:
-        e2e = measure_e2e(pk, rb, f, stream, max(3, min(args.steps, 20)))
+        e2e = measure_e2e(pk, rb, f, stream, max(3, min(args.steps, 20)),
+                          m["tuning"]["chosen"] if m["tuning"] else None)
 
     secondary = None
     if rank == 0 and world == 1 and not args.no_secondary and args.workload == WORKLOAD:
@@ -424,11 +442,12 @@ def ours(args, rank, world, local_rank):
         for name in SECONDARY:
             p2 = workload(name)
             steps2 = 50
-            m2 = measure_device(pk, rb, p2, steps2, 5, dev, stream, flush)
+            m2 = measure_device(pk, rb, p2, steps2, 5, dev, stream, flush, autotune=not args.no_autotune)
             secondary[name] = dict(
                 value=m2["pairs_per_step"] * steps2 / (m2["ms"] / 1e3), unit=UNIT, steps=steps2,
                 ms_per_step=m2["ms"] / steps2, pair_terms_per_step=m2["pairs_per_step"],
-                roofline=roofline_of(name, m2, steps2, dev, sm_max))
+                roofline=roofline_of(name, m2, steps2, dev, sm_max),
+                tuning=m2["tuning"]["chosen"] if m2["tuning"] else None)
     serve = None
     if rank == 0 and world == 1 and not args.no_serving and args.workload == WORKLOAD:
         serve = serving(pk)
@@ -446,7 +465,9 @@ def ours(args, rank, world, local_rank):
                                 pair_terms_per_step=int(m["pairs_per_step"]),
                                 l2="256 MiB buffer written between steps, outside the timed events",
                                 step="grid build + evaluation + one LM iteration (2 evaluations)",
-                                parallelism="replicas" if world > 1 else "single GPU"),
+                                parallelism="replicas" if world > 1 else "single GPU",
+                                tuning=m["tuning"]["chosen"] if m["tuning"] else "default (untuned)"),
+                    autotune=m["tuning"],
                     roofline=roofline, cpu_baseline=cpu_base, e2e=e2e, gpu_launches=m["launches"],
                     clocks=clk, secondary=secondary, serving=serve, functions=funcs)
         print(json.dumps(line), flush=True)
@@ -542,11 +563,14 @@ def serving(pk, seed=1634, n_requests=200, pool_size=50, max_iters=30, loads=(0.
     """Served BA solves: a Poisson stream of n_requests requests (2-10 frames x
     5k-100k LiDAR points, log-uniform, 19-class labels) drawn in turn from
     pool_size generated problems, at several loads (x the measured plain
-    single-stream capacity).  Served form: the request server (continuous
-    batching, BF16 labels on the device, up to 8 in flight).  Plain form: one
-    request at a time through rkhsba_create + rkhsba_solve with FP32 labels.
-    Accuracy: the served poses of every pool problem against the plain FP32
-    poses of the same problem (both run max_iters LM iterations at most)."""
+    single-stream capacity).  Served form: the request server in batched
+    mode (continuous batching, one pair launch per round over every in-flight
+    request, autotuned pair stage, BF16 labels on the device, up to 8 in
+    flight); at load 1 and at capacity also the server with per-request
+    streams.  Plain form: one request at a time through rkhsba_create +
+    rkhsba_solve with FP32 labels.  Accuracy: the served (batched) poses of
+    every pool problem against the plain FP32 poses of the same problem (both
+    run max_iters LM iterations at most)."""
     import threading
 
     import scenes
@@ -581,8 +605,8 @@ def serving(pk, seed=1634, n_requests=200, pool_size=50, max_iters=30, loads=(0.
         svc.append(time.perf_counter() - t0)
     mean_svc = sum(svc[order[i]] for i in range(n_requests)) / n_requests
 
-    def run_served(arrivals):
-        srv = pk.Server(max_inflight=8)
+    def run_served(arrivals, **kw):
+        srv = pk.Server(max_inflight=8, **kw)
         lat, done_t = [None] * n_requests, [None] * n_requests
         tickets = [None] * n_requests
         fail = []
@@ -596,7 +620,7 @@ def serving(pk, seed=1634, n_requests=200, pool_size=50, max_iters=30, loads=(0.
                 lat[i] = r[1]["latency_ms"]
                 if r[1]["state"] != "finished":
                     fail.append(r[1])
-                else:
+                elif kw.get("mode", "batched") == "batched":
                     served_res.setdefault(order[i], r[0])
 
         th = threading.Thread(target=poller)
@@ -629,12 +653,18 @@ def serving(pk, seed=1634, n_requests=200, pool_size=50, max_iters=30, loads=(0.
 
     rng = np.random.default_rng(seed)
     sweep = []
+    batched = dict(mode="batched", autotune=True)
     for load in loads:
         rate = load / mean_svc
         arrivals = np.cumsum(rng.exponential(1.0 / rate, size=n_requests))
-        sweep.append(dict(load_factor=load, arrival_rate_per_s=rate, served=run_served(arrivals),
-                          plain_fp32_single=run_plain(arrivals)))
-    capacity = dict(served=run_served(None)["solves_per_s"], plain_fp32_single=run_plain(None)["solves_per_s"])
+        ent = dict(load_factor=load, arrival_rate_per_s=rate, served=run_served(arrivals, **batched),
+                   plain_fp32_single=run_plain(arrivals))
+        if load == 1.0:
+            ent["served_per_request_streams"] = run_served(arrivals, mode="per_request")
+        sweep.append(ent)
+    capacity = dict(served=run_served(None, **batched)["solves_per_s"],
+                    served_per_request_streams=run_served(None, mode="per_request")["solves_per_s"],
+                    plain_fp32_single=run_plain(None)["solves_per_s"])
     diffs = [_pose_diff(served_res[i], plain_res[i]) for i in sorted(served_res) if i in plain_res]
     accuracy = dict(compared=len(diffs), max_rot_rad=max(d[0] for d in diffs) if diffs else None,
                     max_trans_m=max(d[1] for d in diffs) if diffs else None, tolerance=1e-4,
@@ -658,6 +688,7 @@ def main():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-functions", action="store_true")
     ap.add_argument("--no-secondary", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true", help="measure the default pair-stage setting")
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(WORKLOADS),
                     help="other workloads of the paper's shapes (the driver uses the default)")
     args = ap.parse_args()

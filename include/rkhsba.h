@@ -79,6 +79,11 @@ typedef struct {
     double tol_rel_f;    /* stop when an accepted step gains less than this relative F (1e-12) */
     double sem_min;      /* > 0: drop pairs whose semantic kernel <l_i, l_j> is below
                             sem_min (the semantic pruning of Sec. VII); 0: off */
+    double cell_scale;   /* grid cell edge h = cell_scale * r_c * (1 + 2^-10), 1..4
+                            (default 1).  Larger cells put more queries in a unit
+                            and more candidates in the 27-cell stencil; results
+                            do not depend on it beyond FP32 rounding (the
+                            autotuner picks it per workload) */
 } rkhsba_params;
 
 typedef struct {
@@ -331,6 +336,50 @@ rkhsba_status rkhsba_solve_ell_decay(rkhsba_ctx* ctx, const rkhsba_ell_schedule*
                                      double* ell_levels, double* dD_levels, rkhsba_ell_info* info);
 
 /* ------------------------------------------------------------------------
+ * Pair-kernel tuning and the autotuner (the paper has no counterpart; these
+ * pick launch shapes of the sparse double sum of Sec. III-B per workload).
+ *
+ * Three knobs change the speed of the pair stage but not its results beyond
+ * FP32 rounding (pair sets and the exact fixed-point sums do not change):
+ *   cell_scale    grid cell edge in units of r_c (params.cell_scale, fixed
+ *                 at rkhsba_create: the grids are built for it)
+ *   unit_queries  queries of one home cell handed to a warp at a time (1..32)
+ *   ctas_per_sm   resident CTAs per SM of the persistent pair launch
+ *                 (0: as many as fit)
+ * ------------------------------------------------------------------------ */
+typedef struct {
+    double cell_scale;
+    int32_t unit_queries;
+    int32_t ctas_per_sm;
+    double ms;             /* autotuner: mean time of one evaluation with these settings */
+} rkhsba_tuning;
+
+/* Set the runtime knobs of a context (captured LM graphs are rebuilt). */
+rkhsba_status rkhsba_set_tuning(rkhsba_ctx* ctx, int32_t unit_queries, int32_t ctas_per_sm);
+rkhsba_status rkhsba_get_tuning(const rkhsba_ctx* ctx, rkhsba_tuning* out);
+
+/*
+ * rkhsba_autotune -- time the evaluation of one problem under every
+ * candidate setting (cell_scale 1, 1.25, 1.5 x unit_queries 16, 32 x
+ * ctas_per_sm 1, all) and report the fastest.  For each cell size a
+ * temporary context is built from the inputs (arguments as for
+ * rkhsba_create, or as for rkhsba_create_device when inputs_on_device is 1);
+ * each setting is run once untimed, then `reps` (1..100) evaluations at
+ * `poses` ([K*16] HOST) are timed with CUDA events on cuda_stream.
+ *   best      HOST out: the fastest setting and its mean time (ms)
+ *   table     HOST out [table_cap] (may be NULL when table_cap is 0): every
+ *             setting tried, in order; *n_table receives the count (12)
+ * Creating a context with params.cell_scale = best.cell_scale and calling
+ * rkhsba_set_tuning(ctx, best.unit_queries, best.ctas_per_sm) applies it.
+ * Synchronous; holds one temporary context at a time.
+ */
+rkhsba_status rkhsba_autotune(int32_t n_frames, const int64_t* n_points, const double* xyz, const float* sem,
+                              const float* rgb, int32_t n_edges, const int32_t* edges,
+                              const rkhsba_params* params, int32_t inputs_on_device, const double* poses,
+                              void* cuda_stream, int32_t reps, rkhsba_tuning* best, rkhsba_tuning* table,
+                              int32_t table_cap, int32_t* n_table);
+
+/* ------------------------------------------------------------------------
  * Request server: continuous batching of BA solves on one GPU.
  *
  * Requests (each a problem as for rkhsba_create plus initial poses) are
@@ -338,11 +387,17 @@ rkhsba_status rkhsba_solve_ell_decay(rkhsba_ctx* ctx, const rkhsba_ell_schedule*
  * the device-memory budget allows (the problem's buffers are estimated from
  * its sizes before admission and charged at their real size after).  Every
  * admitted problem keeps its points and grids resident and runs the
- * rkhsba_solve loop (Sec. V-A, V-C) on its own stream, a few LM iterations
- * per issue, so the GPU work of different requests overlaps; a finished
- * request frees its slot and memory and the next one is admitted at once.
+ * rkhsba_solve loop (Sec. V-A, V-C).  In batched mode (the default) the
+ * server advances all admitted problems together, one LM iteration per
+ * round: each problem's damped solve and query binning on its own stream,
+ * then one persistent pair launch over the units of every problem (each
+ * adding into its own accumulators), then each problem's assembly and
+ * accept/reject on its own stream; in per-request mode every problem runs
+ * whole iterations on its own stream, a few per issue.  Either way the GPU
+ * work of different requests overlaps; a finished request frees its slot and
+ * memory and the next one is admitted at once.
  * Results do not depend on what else is running: a request solved alone and
- * in a mix gives the same poses bit for bit.
+ * in a mix, in either mode, gives the same poses bit for bit.
  *
  * Threads: rkhsba_submit / rkhsba_poll / rkhsba_cancel / rkhsba_server_stats
  * may be called from any host threads; the server's own threads make all
@@ -357,6 +412,14 @@ typedef struct {
     int64_t memory_budget;     /* bytes of device memory for admitted requests
                                   (0: half of the free memory at creation) */
     double request_timeout_ms; /* watchdog per request from admission (0: none) */
+    int32_t mode;              /* 0 (default): batched rounds -- every round runs one LM
+                                  iteration of every admitted request, with ONE
+                                  persistent pair launch over the units of all of
+                                  them that share a label layout; 1: per-request
+                                  streams, iters_per_issue whole iterations per issue */
+    int32_t autotune;          /* 1: the first request of each label layout is timed
+                                  under the autotuner's settings (rkhsba_autotune) and
+                                  the fastest is used for it and later ones; 0: off */
 } rkhsba_server_config;
 
 typedef struct {

@@ -73,6 +73,9 @@ rkhsba_status normalize_params(rkhsba_ctx* ctx, const rkhsba_params* in) {
     if (p.top_k < 0 || p.top_k > TOPK_MAX) return fail(ctx, RKHSBA_EINVAL, "params.top_k must be in [0, 8]");
     if (!(p.sem_min >= 0.0) || !std::isfinite(p.sem_min))
         return fail(ctx, RKHSBA_EINVAL, "params.sem_min must be finite and >= 0");
+    if (p.cell_scale == 0.0) p.cell_scale = 1.0;
+    if (!(p.cell_scale >= 1.0 && p.cell_scale <= 4.0))
+        return fail(ctx, RKHSBA_EINVAL, "params.cell_scale must be in [1, 4]");
     ctx->p = p;
     ctx->gp = grid_params_for(p);
     const GridParams& g = ctx->gp;
@@ -312,27 +315,41 @@ void run_binning(rkhsba_ctx* c, const double* poses, const int* done) {
     c->q_sorted_key = alt ? c->d_qkey_alt : c->d_qkey;
     const int* qv = alt ? c->d_qval_alt : c->d_qval;
     launch_query_gather(c->q_sorted_key, qv, c->d_qrec, c->Q_total, c->d_slots, c->d_bin_first, done, st);
-    launch_units(c->q_sorted_key, c->d_bin_first, c->Q_total, c->d_unit_start, c->d_ucount, done, st);
+    launch_units(c->q_sorted_key, c->d_bin_first, c->Q_total, c->tune_uq, c->d_unit_start, c->d_ucount, done, st);
 }
 
-// One evaluation at the device poses `poses`; results into the cand buffers.
-void run_eval(rkhsba_ctx* c, const double* poses, const int* done) {
-    cudaStream_t st = c->stream;
+// One evaluation at the device poses `poses`, results into the cand
+// buffers, in three parts: binning (queries keyed, sorted and cut into
+// units; accumulators cleared), the pair stage, and the FP64 assembly.
+void eval_pre(rkhsba_ctx* c, const double* poses, const int* done) {
     c->phase_begin(1);
     run_binning(c, poses, done);
-    cudaMemsetAsync(c->d_acc, 0, sizeof(long long) * c->E * ACC_N, st);
+    cudaMemsetAsync(c->d_acc, 0, sizeof(long long) * c->E * ACC_N, c->stream);
     c->phase_end();
+}
+
+void eval_pairs(rkhsba_ctx* c, const int* done) {
     c->phase_begin(2);
-    launch_pairs(c->d_unit_start, c->d_ucount, c->d_ucount + 1, c->q_sorted_key, c->d_slots, c->Q_total,
-                 c->d_edges, c->E, c->d_frames, c->d_cell_start, c->d_pts4, c->d_sem, c->d_col4, c->gp,
-                 c->d_acc, done, c->num_sms, st);
+    launch_pairs(PairLaunch{c->d_unit_start, c->d_ucount, c->d_ucount + 1, done, c->num_sms, c->tune_ctas,
+                            c->stream},
+                 c->pair_args());
     c->phase_end();
+}
+
+void eval_post(rkhsba_ctx* c, const int* done) {
+    cudaStream_t st = c->stream;
     c->phase_begin(3);
     launch_edge_assemble(c->d_edges, c->E, c->d_xf, c->d_acc, c->p.sigma * c->p.sigma, c->d_eout, done, st);
     cudaMemsetAsync(c->d_H_cand, 0, sizeof(double) * 36LL * c->K * c->K, st);
     launch_frame_assemble(c->d_edges, c->E, c->K, c->d_inc_off, c->d_inc_list, c->d_eout, c->d_H_cand,
                           c->d_b_cand, c->d_F_cand, c->d_n_cand, done, st);
     c->phase_end();
+}
+
+void run_eval(rkhsba_ctx* c, const double* poses, const int* done) {
+    eval_pre(c, poses, done);
+    eval_pairs(c, done);
+    eval_post(c, done);
 }
 
 rkhsba_status check_poses(rkhsba_ctx* c, const double* poses) {
@@ -377,18 +394,57 @@ void lm_initial(rkhsba_ctx* c) {
     c->need_initial = false;
 }
 
-void lm_iteration(rkhsba_ctx* c) {
+// One LM iteration in two halves around the pair stage: the damped solve
+// and the binning at the candidate poses; then the assembly and the
+// accept/reject of the candidate.
+void lm_iter_pre(rkhsba_ctx* c) {
     const int* done = &c->d_state->done;
     c->phase_begin(4);
     launch_lm_solve(c->K, c->d_H_cur, c->d_b_cur, c->d_poses_cur, c->d_poses_cand, c->d_state,
                     c->d_lm_ws, c->stream);
     c->phase_end();
-    run_eval(c, c->d_poses_cand, done);
+    eval_pre(c, c->d_poses_cand, done);
+}
+
+void lm_iter_post(rkhsba_ctx* c) {
+    const int* done = &c->d_state->done;
+    eval_post(c, done);
     c->phase_begin(4);
     launch_lm_accept(c->K, c->d_state, c->d_F_cand, c->d_n_cand, c->d_poses_cur, c->d_poses_cand,
                      c->d_b_cur, c->d_b_cand, c->stream);
     launch_copy_if_accepted(c->d_state, c->d_H_cur, c->d_H_cand, 36LL * c->K * c->K, c->stream);
     c->phase_end();
+}
+
+void lm_iteration(rkhsba_ctx* c) {
+    lm_iter_pre(c);
+    eval_pairs(c, &c->d_state->done);
+    lm_iter_post(c);
+}
+
+// Captures fn (kernels on the context stream) into *exec once; false when
+// capture is not possible (the caller then launches fn directly).
+template <typename Fn>
+bool capture_graph(rkhsba_ctx* c, cudaGraphExec_t* exec, long long* kernels, Fn fn) {
+    cudaGraph_t g = nullptr;
+    const long long before = t_launches;
+    bool ok = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+    if (ok) {
+        fn();
+        ok = cudaStreamEndCapture(c->stream, &g) == cudaSuccess && g != nullptr;
+    }
+    if (ok) ok = cudaGraphInstantiate(exec, g, 0) == cudaSuccess;
+    if (g) cudaGraphDestroy(g);
+    const long long n = t_launches - before;   // captured, not run
+    g_launches.fetch_sub(n);
+    t_launches = before;
+    if (!ok) {
+        cudaGetLastError();
+        *exec = nullptr;
+        return false;
+    }
+    *kernels = n;
+    return true;
 }
 
 // n LM iterations.  After the first evaluation has run (kernel attributes and
@@ -403,26 +459,11 @@ void lm_iterate(rkhsba_ctx* c, int n) {
         return;
     }
     if (!c->iter_graph) {
-        cudaGraph_t g = nullptr;
-        const long long before = t_launches;
-        bool ok = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
-        if (ok) {
-            lm_iteration(c);
-            ok = cudaStreamEndCapture(c->stream, &g) == cudaSuccess && g != nullptr;
-        }
-        if (ok) ok = cudaGraphInstantiate(&c->iter_graph, g, 0) == cudaSuccess;
-        if (g) cudaGraphDestroy(g);
-        const long long kernels = t_launches - before;   // captured, not run
-        g_launches.fetch_sub(kernels);
-        t_launches = before;
-        if (!ok) {
-            cudaGetLastError();
-            c->iter_graph = nullptr;
+        if (!capture_graph(c, &c->iter_graph, &c->iter_launches, [&] { lm_iteration(c); })) {
             c->use_graph = false;
             for (int i = 0; i < n; ++i) lm_iteration(c);
             return;
         }
-        c->iter_launches = kernels;
     }
     for (int i = 0; i < n; ++i) {
         cudaGraphLaunch(c->iter_graph, c->stream);
@@ -475,6 +516,41 @@ rkhsba_status ctx_begin_solve(rkhsba_ctx* c, const double* host_poses) {
     return RKHSBA_OK;
 }
 void ctx_iterate(rkhsba_ctx* c, int n) { lm_iterate(c, n); }
+
+// The two halves of one LM iteration for the batched server, each replayed
+// from a CUDA graph captured on first use; the pair stage between them runs
+// in the server's batched launch.
+void ctx_iter_pre(rkhsba_ctx* c) {
+    if (c->use_graph && !c->prof) {
+        if (c->pre_graph || capture_graph(c, &c->pre_graph, &c->pre_launches, [&] { lm_iter_pre(c); })) {
+            cudaGraphLaunch(c->pre_graph, c->stream);
+            count_launch(c->pre_launches);
+            return;
+        }
+    }
+    lm_iter_pre(c);
+}
+void ctx_iter_post(rkhsba_ctx* c) {
+    if (c->use_graph && !c->prof) {
+        if (c->post_graph || capture_graph(c, &c->post_graph, &c->post_launches, [&] { lm_iter_post(c); })) {
+            cudaGraphLaunch(c->post_graph, c->stream);
+            count_launch(c->post_launches);
+            return;
+        }
+    }
+    lm_iter_post(c);
+}
+PairJob ctx_pair_job(const rkhsba_ctx* c) {
+    PairJob j{};
+    j.unit_start = c->d_unit_start;
+    j.n_units = c->d_ucount;
+    j.done = &c->d_state->done;
+    j.a = c->pair_args();
+    return j;
+}
+GridParams ctx_layout(const rkhsba_ctx* c) { return c->gp; }
+int ctx_num_sms(const rkhsba_ctx* c) { return c->num_sms; }
+int ctx_tune_ctas(const rkhsba_ctx* c) { return c->tune_ctas; }
 cudaStream_t ctx_stream(const rkhsba_ctx* c) { return c->stream; }
 const void* ctx_state_dev(const rkhsba_ctx* c) { return c->d_state; }
 const double* ctx_poses_dev(const rkhsba_ctx* c) { return c->d_poses_cur; }
@@ -640,7 +716,7 @@ rkhsba_status rkhsba_edge_pairs(rkhsba_ctx* c, const double* poses, int32_t edge
     cudaMemsetAsync(c->d_ucount + 1, 0, sizeof(int), st);
     launch_emit_pairs(c->d_unit_start, c->d_ucount, c->d_ucount + 1, c->q_sorted_key, c->d_slots, c->Q_total,
                       c->d_edges, c->E, c->d_frames, c->d_cell_start, c->d_pts4, c->gp, edge, c->d_perm_local,
-                      capacity, di, dj, dn, c->num_sms, st);
+                      capacity, c->tune_uq, di, dj, dn, c->num_sms, st);
     unsigned long long n = 0;
     cudaMemcpyAsync(&n, dn, sizeof(n), cudaMemcpyDeviceToHost, st);
     cudaError_t es = cudaStreamSynchronize(st);
@@ -700,6 +776,93 @@ const char* rkhsba_last_error(const rkhsba_ctx* c) {
 }
 
 int64_t rkhsba_launch_count(void) { return g_launches.load(); }
+
+rkhsba_status rkhsba_set_tuning(rkhsba_ctx* c, int32_t unit_queries, int32_t ctas_per_sm) {
+    if (!c) return fail(nullptr, RKHSBA_EINVAL, "ctx is NULL");
+    if (unit_queries < 1 || unit_queries > UNIT_Q) return fail(c, RKHSBA_EINVAL, "unit_queries must be in [1, 32]");
+    if (ctas_per_sm < 0 || ctas_per_sm > 32) return fail(c, RKHSBA_EINVAL, "ctas_per_sm must be in [0, 32]");
+    c->tune_uq = unit_queries;
+    c->tune_ctas = ctas_per_sm;
+    c->drop_graphs();
+    return RKHSBA_OK;
+}
+
+rkhsba_status rkhsba_get_tuning(const rkhsba_ctx* c, rkhsba_tuning* out) {
+    if (!c || !out) return fail(nullptr, RKHSBA_EINVAL, "NULL argument");
+    out->cell_scale = c->p.cell_scale;
+    out->unit_queries = c->tune_uq;
+    out->ctas_per_sm = c->tune_ctas;
+    out->ms = 0.0;
+    return RKHSBA_OK;
+}
+
+// The autotuner: for every candidate cell size a context is built over the
+// caller's inputs (grid build at that cell size), and for every unit size
+// and CTA count the evaluation at `poses` (binning, pair stage, FP64
+// assembly) is timed with CUDA events on the stream after one untimed run.
+// The fastest candidate wins (the first on ties).
+rkhsba_status rkhsba_autotune(int32_t n_frames, const int64_t* n_points, const double* xyz, const float* sem,
+                              const float* rgb, int32_t n_edges, const int32_t* edges,
+                              const rkhsba_params* params, int32_t inputs_on_device, const double* poses,
+                              void* cuda_stream, int32_t reps, rkhsba_tuning* best, rkhsba_tuning* table,
+                              int32_t table_cap, int32_t* n_table) {
+    if (!params || !poses || !best) return fail(nullptr, RKHSBA_EINVAL, "NULL argument");
+    if (reps < 1 || reps > 100) return fail(nullptr, RKHSBA_EINVAL, "reps must be in [1, 100]");
+    if (table_cap < 0 || (table_cap > 0 && !table)) return fail(nullptr, RKHSBA_EINVAL, "bad table");
+    static const double scales[] = {1.0, 1.25, 1.5};
+    static const int uqs[] = {16, 32};
+    static const int ctas[] = {1, 0};
+    int n = 0;
+    best->ms = -1.0;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        cudaGetLastError();
+        return fail(nullptr, RKHSBA_ECUDA, "event creation failed");
+    }
+    rkhsba_status st = RKHSBA_OK;
+    for (double sc : scales) {
+        rkhsba_params p = *params;
+        p.cell_scale = sc;
+        rkhsba_ctx* c = nullptr;
+        st = create_impl(&c, n_frames, n_points, xyz, sem, rgb, n_edges, edges, &p, cuda_stream,
+                         inputs_on_device != 0);
+        if (st != RKHSBA_OK) break;
+        st = check_poses(c, poses);
+        if (st == RKHSBA_OK) {
+            cudaMemcpyAsync(c->d_poses_cand, poses, sizeof(double) * 16 * c->K, cudaMemcpyHostToDevice, c->stream);
+            for (int uq : uqs)
+                for (int ct : ctas) {
+                    c->tune_uq = uq;
+                    c->tune_ctas = ct;
+                    run_eval(c, c->d_poses_cand, nullptr);
+                    cudaEventRecord(e0, c->stream);
+                    for (int r = 0; r < reps; ++r) run_eval(c, c->d_poses_cand, nullptr);
+                    cudaEventRecord(e1, c->stream);
+                    float ms = 0.f;
+                    if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+                        st = fail(c, RKHSBA_ECUDA, "autotune timing failed");
+                        break;
+                    }
+                    rkhsba_tuning t{sc, uq, ct, (double)ms / reps};
+                    if (n < table_cap) table[n] = t;
+                    ++n;
+                    if (best->ms < 0.0 || t.ms < best->ms) *best = t;
+                }
+        }
+        if (st != RKHSBA_OK) {
+            std::string msg = c->err;
+            delete c;
+            t_err = msg;
+            break;
+        }
+        delete c;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (n_table) *n_table = n;
+    return st;
+}
 
 }  // extern "C"
 

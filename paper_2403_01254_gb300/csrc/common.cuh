@@ -101,6 +101,46 @@ struct GridParams {
 
 constexpr int TOPK_MAX = 8;   // largest top_k of the neighbour-limited variant
 
+// What the pair kernel reads of one problem for one evaluation: the sorted
+// queries of every edge, the problem's grids and labels, and its per-edge
+// fixed-point accumulators.
+struct PairArgs {
+    const uint32_t* qkey;     // sorted home-cell keys of the queries
+    const float4* slots;      // sorted query records (offset from the home centre, point index)
+    long long Q;              // queries over all edges
+    const EdgeDev* edges;
+    const FrameDev* frames;
+    const int* cell_start;
+    const float4* pts4;       // points, cell-local, sorted by (frame, cell)
+    const void* sem_sorted;   // label rows in the same order (FP32 or BF16), or NULL
+    const float4* col4;       // colours in the same order, or NULL
+    long long* acc;           // [E][ACC_N] fixed-point moments
+    int E;
+    int uq;                   // queries per unit (1..32)
+    GridParams gp;
+};
+
+// One problem of a batched pair launch: its unit list and LM state flag
+// (a job whose solve is done contributes no units).
+struct PairJob {
+    const int* unit_start;
+    const int* n_units;
+    const int* done;
+    PairArgs a;
+};
+constexpr int MAX_PAIR_JOBS = 64;   // problems in one batched pair launch
+
+// Launch state of a single-problem pair launch.
+struct PairLaunch {
+    const int* unit_start;
+    const int* n_units;
+    int* unit_counter;        // zeroed by the caller
+    const int* done;          // LM state flag or NULL
+    int num_sms;
+    int ctas_per_sm;          // 0: as many as fit
+    cudaStream_t stream;
+};
+
 struct LMState {
     double lambda;
     double F_cur, F_cand;
@@ -144,17 +184,19 @@ void launch_query_keys(const EdgeDev* edges, int E, const FrameDev* frames, cons
 void launch_query_gather(const uint32_t* qkey_sorted, const int* qval_sorted, const float4* qrec,
                          long long Q, float4* slots, int* bin_first, const int* done,
                          cudaStream_t st);
-void launch_units(const uint32_t* qkey_sorted, const int* bin_first, long long Q, int* unit_start,
+void launch_units(const uint32_t* qkey_sorted, const int* bin_first, long long Q, int uq, int* unit_start,
                   int* n_units, const int* done, cudaStream_t st);
-void launch_pairs(const int* unit_start, const int* n_units, int* unit_counter,
-                  const uint32_t* qkey, const float4* slots, long long Q, const EdgeDev* edges, int E,
-                  const FrameDev* frames, const int* cell_start, const float4* pts4,
-                  const void* sem_sorted, const float4* col4, GridParams gp, long long* acc,
-                  const int* done, int num_sms, cudaStream_t st);
+void launch_pairs(const PairLaunch& L, const PairArgs& A);
+// One persistent launch over the units of n_jobs problems (device array
+// `jobs`) that share the label layout, colour use and variant of `layout`;
+// false when the layout has no batched kernel (top_k variant) or n_jobs is
+// out of range.  *counter must be zero.
+bool launch_pairs_multi(const PairJob* jobs, int n_jobs, const GridParams& layout, int* counter, int num_sms,
+                        int ctas_per_sm, cudaStream_t st);
 void launch_emit_pairs(const int* unit_start, const int* n_units, int* unit_counter,
                        const uint32_t* qkey, const float4* slots, long long Q, const EdgeDev* edges,
                        int E, const FrameDev* frames, const int* cell_start, const float4* pts4,
-                       GridParams gp, int edge_sel, const int* perm_local, long long capacity,
+                       GridParams gp, int edge_sel, const int* perm_local, long long capacity, int uq,
                        int* i_out, int* j_out, unsigned long long* n_out, int num_sms,
                        cudaStream_t st);
 
@@ -189,4 +231,11 @@ const double* ctx_poses_dev(const rkhsba_ctx* c);
 size_t ctx_bytes(const rkhsba_ctx* c);
 int ctx_max_iters(const rkhsba_ctx* c);
 int ctx_state_bytes();
+// batched serving: the LM iteration split around the pair stage
+void ctx_iter_pre(rkhsba_ctx* c);
+void ctx_iter_post(rkhsba_ctx* c);
+PairJob ctx_pair_job(const rkhsba_ctx* c);
+GridParams ctx_layout(const rkhsba_ctx* c);
+int ctx_num_sms(const rkhsba_ctx* c);
+int ctx_tune_ctas(const rkhsba_ctx* c);
 }  // namespace rk

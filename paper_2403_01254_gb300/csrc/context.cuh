@@ -98,6 +98,39 @@ struct rkhsba_ctx {
     cudaGraphExec_t iter_graph = nullptr;   // one LM iteration, replayed
     bool use_graph = true;
     long long iter_launches = 0;            // kernels in one iteration
+    cudaGraphExec_t pre_graph = nullptr;    // LM solve + binning of one iteration (batched serving)
+    cudaGraphExec_t post_graph = nullptr;   // assembly + accept of one iteration (batched serving)
+    long long pre_launches = 0, post_launches = 0;
+
+    // pair-kernel tuning (rkhsba_set_tuning / the autotuner)
+    int tune_uq = 32;                       // queries per unit
+    int tune_ctas = 0;                      // CTAs per SM of the pair launch (0: as many as fit)
+
+    // drop captured graphs (their kernels' arguments changed)
+    void drop_graphs() {
+        if (iter_graph) cudaGraphExecDestroy(iter_graph);
+        if (pre_graph) cudaGraphExecDestroy(pre_graph);
+        if (post_graph) cudaGraphExecDestroy(post_graph);
+        iter_graph = pre_graph = post_graph = nullptr;
+    }
+
+    rk::PairArgs pair_args() const {
+        rk::PairArgs a{};
+        a.qkey = q_sorted_key;
+        a.slots = d_slots;
+        a.Q = Q_total;
+        a.edges = d_edges;
+        a.frames = d_frames;
+        a.cell_start = d_cell_start;
+        a.pts4 = d_pts4;
+        a.sem_sorted = d_sem;
+        a.col4 = d_col4;
+        a.acc = d_acc;
+        a.E = E;
+        a.uq = tune_uq;
+        a.gp = gp;
+        return a;
+    }
 
     // phase profiler (CUDA events on the context stream)
     static constexpr int NPH = 5;
@@ -140,6 +173,8 @@ struct rkhsba_ctx {
         if (stream) cudaStreamSynchronize(stream);
         for (auto e : ev_pool) cudaEventDestroy(e);
         if (iter_graph) cudaGraphExecDestroy(iter_graph);
+        if (pre_graph) cudaGraphExecDestroy(pre_graph);
+        if (post_graph) cudaGraphExecDestroy(post_graph);
         if (own_stream && stream) cudaStreamDestroy(stream);
     }
 };

@@ -30,13 +30,14 @@ inline int sem_pad_for(int dim, bool bf16) {
 }
 
 // Kernel constants of Eq. kernel for validated parameters: cell size
-// h = r_c (1 + 2^-10) (the 27-cell stencil covers every pair closer than
-// r_c), r_c^2, the exponent scale -log2(e) / (2 ell^2), the label variants.
+// h = cell_scale r_c (1 + 2^-10) (cell_scale >= 1, so the 27-cell stencil
+// covers every pair closer than r_c), r_c^2, the exponent scale
+// -log2(e) / (2 ell^2), the label variants.
 // The colour factor is set by grid_params_color once the inputs are known.
 inline GridParams grid_params_for(const rkhsba_params& p) {
     GridParams g{};
     const double rc = p.cutoff_mult * p.ell;
-    g.h = rc * (1.0 + 1.0 / 1024.0);
+    g.h = (p.cell_scale >= 1.0 ? p.cell_scale : 1.0) * rc * (1.0 + 1.0 / 1024.0);
     g.h_inv = 1.0 / g.h;
     g.hf = (float)g.h;
     g.hf_inv = (float)g.h_inv;

@@ -145,6 +145,8 @@ extern "C" rkhsba_status rkhsba_eval_static(int32_t n_frames, const int64_t* n_p
     if (p.top_k < 0 || p.top_k > TOPK_MAX) return fail(RKHSBA_EINVAL, "params.top_k must be in [0, 8]");
     if (!(p.sem_min >= 0.0) || !std::isfinite(p.sem_min))
         return fail(RKHSBA_EINVAL, "params.sem_min must be finite and >= 0");
+    if (p.cell_scale == 0.0) p.cell_scale = 1.0;
+    if (!(p.cell_scale >= 1.0 && p.cell_scale <= 4.0)) return fail(RKHSBA_EINVAL, "params.cell_scale must be in [1, 4]");
     const double rc = p.cutoff_mult * p.ell;
     GridParams gp = grid_params_for(p);
     grid_params_color(gp, d_rgb != nullptr && p.ell_color > 0.0, p.ell_color);
@@ -274,9 +276,24 @@ extern "C" rkhsba_status rkhsba_eval_static(int32_t n_frames, const int64_t* n_p
     radix_sort_u32(d_qkey, d_qval, d_qkey_alt, d_qval_alt, Q, qbits, d_hist, d_ws, d_err + 1, st, &qalt);
     const uint32_t* qk = qalt ? d_qkey_alt : d_qkey;
     launch_query_gather(qk, qalt ? d_qval_alt : d_qval, d_qrec, Q, d_slots, d_bin_first, nullptr, st);
-    launch_units(qk, d_bin_first, Q, d_units, d_ucount, nullptr, st);
-    launch_pairs(d_units, d_ucount, d_ucount + 1, qk, d_slots, Q, d_edges, E, d_frames, d_cell_start, d_pts4,
-                 d_sem_sorted, d_col4, gp, d_acc, nullptr, num_sms, st);
+    launch_units(qk, d_bin_first, Q, UNIT_Q, d_units, d_ucount, nullptr, st);
+    {
+        PairArgs a{};
+        a.qkey = qk;
+        a.slots = d_slots;
+        a.Q = Q;
+        a.edges = d_edges;
+        a.frames = d_frames;
+        a.cell_start = d_cell_start;
+        a.pts4 = d_pts4;
+        a.sem_sorted = d_sem_sorted;
+        a.col4 = d_col4;
+        a.acc = d_acc;
+        a.E = E;
+        a.uq = UNIT_Q;
+        a.gp = gp;
+        launch_pairs(PairLaunch{d_units, d_ucount, d_ucount + 1, nullptr, num_sms, 0, st}, a);
+    }
     launch_edge_assemble(d_edges, E, d_xf, d_acc, p.sigma * p.sigma, d_eout, nullptr, st);
     SCK(cudaMemsetAsync(d_H, 0, sizeof(double) * 36LL * K * K, st));
     launch_frame_assemble(d_edges, E, K, d_inc_off, d_inc_list, d_eout, d_H, d_b, d_F, d_n, nullptr, st);

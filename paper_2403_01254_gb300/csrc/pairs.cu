@@ -179,10 +179,11 @@ __global__ void k_query_gather(const uint32_t* __restrict__ key, const int* __re
     }
 }
 
-// a unit starts at the first query of a home cell and every UNIT_Q queries
-// after; one atomic per block reserves the block's slots in the unit list
+// a unit starts at the first query of a home cell and every uq queries
+// after (uq <= 32); one atomic per block reserves the block's slots in the
+// unit list
 __global__ void __launch_bounds__(256) k_units(const uint32_t* __restrict__ key, const int* __restrict__ bin_first,
-                                               long long Q, int* __restrict__ unit_start,
+                                               long long Q, int uq, int* __restrict__ unit_start,
                                                int* __restrict__ n_units, const int* done) {
     if (done && *done) return;
     __shared__ int s_cnt[8];
@@ -193,7 +194,7 @@ __global__ void __launch_bounds__(256) k_units(const uint32_t* __restrict__ key,
         bool st = false;
         if (k < Q) {
             const uint32_t kk = key[k];
-            st = kk != NO_KEY && ((k - bin_first[kk]) % UNIT_Q) == 0;
+            st = kk != NO_KEY && ((k - bin_first[kk]) % uq) == 0;
         }
         const unsigned m = __ballot_sync(FULL, st);
         if (lane == 0) s_cnt[warp] = __popc(m);
@@ -450,13 +451,13 @@ __device__ __forceinline__ int stream_point(const Rows& R, int v, int& dx, int& 
 // Unit header shared by the pair and the pair-list kernels: home cell of the
 // unit starting at sorted query k0, and the number of its queries (<= UQ).
 __device__ __forceinline__ int unit_queries(const uint32_t* __restrict__ qkey, long long Q, int k0,
-                                            uint32_t key0, int lane) {
-    // units start every UQ queries of a home cell, so a unit holds at most UQ
-    // of them even when the cell continues past k0 + UQ
+                                            uint32_t key0, int lane, int uq) {
+    // units start every uq queries of a home cell, so a unit holds at most uq
+    // of them even when the cell continues past k0 + uq
     const long long k1 = (long long)k0 + lane;
     const bool m1 = k1 < Q && qkey[k1] == key0;
     const int n = __popc(__ballot_sync(FULL, m1));
-    return n < UQ ? n : UQ;
+    return n < uq ? n : uq;
 }
 
 // One step of the moment reduce-scatter: lanes whose bit `o` is clear keep
@@ -582,20 +583,25 @@ __device__ __forceinline__ void label_gram_bf16(const unsigned* __restrict__ sem
         }
 }
 
+// One unit (<= A.uq queries of one frame-a home cell, starting at sorted
+// query k0) of the pair sum: stage the queries, stream the candidates of the
+// 27-cell stencil, test, walk and fold, and add the unit's moments to its
+// edge.  wb is the warp's shared-memory block.
 template <int DP, bool BF16, bool COLOR>
-__global__ void __launch_bounds__(PAIR_T, (BF16 && DP > 0) ? 2 : RK_PAIR_MINB)
-k_pairs(const int* __restrict__ unit_start, const int* __restrict__ n_units, int* unit_counter,
-        const uint32_t* __restrict__ qkey, const float4* __restrict__ slots, long long Q,
-        const EdgeDev* __restrict__ edges, int E, const FrameDev* __restrict__ frames,
-        const int* __restrict__ cell_start, const float4* __restrict__ pts4,
-        const void* __restrict__ sem_sorted, const float4* __restrict__ col4, GridParams gp,
-        long long* __restrict__ acc, const int* done) {
-    if (done && *done) return;
-    extern __shared__ float4 smem4[];
+__device__ __forceinline__ void pair_unit(const PairArgs& A, int k0, float* wb, int lane) {
+    const uint32_t* __restrict__ qkey = A.qkey;
+    const float4* __restrict__ slots = A.slots;
+    const long long Q = A.Q;
+    const EdgeDev* __restrict__ edges = A.edges;
+    const int E = A.E;
+    const FrameDev* __restrict__ frames = A.frames;
+    const int* __restrict__ cell_start = A.cell_start;
+    const float4* __restrict__ pts4 = A.pts4;
+    const void* __restrict__ sem_sorted = A.sem_sorted;
+    const float4* __restrict__ col4 = A.col4;
+    long long* __restrict__ acc = A.acc;
+    const GridParams& gp = A.gp;
     constexpr int SW = SemRow<DP, BF16>::WORDS;
-    const int lane = threadIdx.x & 31;
-    const int warp = threadIdx.x >> 5;
-    float* wb = reinterpret_cast<float*>(smem4) + warp * warp_smem_words<DP, BF16, COLOR>();
     float4* smw = reinterpret_cast<float4*>(wb);                      // [UQ] walk records
     float* smt = wb + 4 * UQ;                                         // [UQ/2][8] test records
     float4* scq = reinterpret_cast<float4*>(wb + 8 * UQ);             // [UQ] query colours
@@ -608,262 +614,325 @@ k_pairs(const int* __restrict__ unit_start, const int* __restrict__ n_units, int
     const ulonglong2* walk2 = reinterpret_cast<const ulonglong2*>(smw);
     const ulonglong2* test2 = reinterpret_cast<const ulonglong2*>(smt);
     const u64 H2 = f2(0.5f, 0.5f);
-    const int nu = *n_units;
-    for (;;) {
-        int u = 0;
-        if (lane == 0) u = atomicAdd(unit_counter, 1);
-        u = __shfl_sync(FULL, u, 0);
-        if (u >= nu) break;
-        const int k0 = unit_start[u];
-        const uint32_t key0 = qkey[k0];
-        const int qcount = unit_queries(qkey, Q, k0, key0, lane);
-        const int e = find_edge_bin(edges, E, key0);
-        const FrameDev& Fa = frames[edges[e].a];
-        const int dx0 = Fa.dim[0], dy0 = Fa.dim[1], dz0 = Fa.dim[2];
-        const int cell = (int)(key0 - edges[e].bin_off);
-        const int hx = cell % dx0, hy = (cell / dx0) % dy0, hz = cell / (dx0 * dy0);
-        __syncwarp();
-        // bounding box of the unit's queries (home-centre coordinates)
-        float blo0 = __int_as_float(0x7f800000), blo1 = blo0, blo2 = blo0;
-        float bhi0 = -blo0, bhi1 = -blo0, bhi2 = -blo0;
-        {
-            const int q = lane;
-            float* tq = smt + 8 * (q >> 1) + (q & 1);
-            if (q < qcount) {
-                const float4 r = slots[(long long)k0 + q];
-                blo0 = bhi0 = r.x;
-                blo1 = bhi1 = r.y;
-                blo2 = bhi2 = r.z;
-                const int s = __float_as_int(r.w);
-                const float mx = -2.f * r.x, my = -2.f * r.y, mz = -2.f * r.z;
-                smw[q] = make_float4(mx, my, mz, mx);
-                tq[0] = mx;
-                tq[2] = my;
-                tq[4] = mz;
-                tq[6] = fmaf(r.x, r.x, fmaf(r.y, r.y, r.z * r.z));
-                if (COLOR) scq[q] = __ldg(col4 + s);
-                SemRow<DP, BF16>::stage(ssq + q * SW, sem_sorted, s);
-            } else if (q == qcount && (q & 1)) {
-                // odd count: the partner slot of the last pair never passes
-                tq[0] = 0.f;
-                tq[2] = 0.f;
-                tq[4] = 0.f;
-                tq[6] = __int_as_float(0x7f800000);
-            }
+    const uint32_t key0 = qkey[k0];
+    const int qcount = unit_queries(qkey, Q, k0, key0, lane, A.uq);
+    const int e = find_edge_bin(edges, E, key0);
+    const FrameDev& Fa = frames[edges[e].a];
+    const int dx0 = Fa.dim[0], dy0 = Fa.dim[1], dz0 = Fa.dim[2];
+    const int cell = (int)(key0 - edges[e].bin_off);
+    const int hx = cell % dx0, hy = (cell / dx0) % dy0, hz = cell / (dx0 * dy0);
+    __syncwarp();
+    // bounding box of the unit's queries (home-centre coordinates)
+    float blo0 = __int_as_float(0x7f800000), blo1 = blo0, blo2 = blo0;
+    float bhi0 = -blo0, bhi1 = -blo0, bhi2 = -blo0;
+    {
+        const int q = lane;
+        float* tq = smt + 8 * (q >> 1) + (q & 1);
+        if (q < qcount) {
+            const float4 r = slots[(long long)k0 + q];
+            blo0 = bhi0 = r.x;
+            blo1 = bhi1 = r.y;
+            blo2 = bhi2 = r.z;
+            const int s = __float_as_int(r.w);
+            const float mx = -2.f * r.x, my = -2.f * r.y, mz = -2.f * r.z;
+            smw[q] = make_float4(mx, my, mz, mx);
+            tq[0] = mx;
+            tq[2] = my;
+            tq[4] = mz;
+            tq[6] = fmaf(r.x, r.x, fmaf(r.y, r.y, r.z * r.z));
+            if (COLOR) scq[q] = __ldg(col4 + s);
+            SemRow<DP, BF16>::stage(ssq + q * SW, sem_sorted, s);
+        } else if (q == qcount && (q & 1)) {
+            // odd count: the partner slot of the last pair never passes
+            tq[0] = 0.f;
+            tq[2] = 0.f;
+            tq[4] = 0.f;
+            tq[6] = __int_as_float(0x7f800000);
         }
+    }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            blo0 = fminf(blo0, __shfl_xor_sync(FULL, blo0, o));
-            blo1 = fminf(blo1, __shfl_xor_sync(FULL, blo1, o));
-            blo2 = fminf(blo2, __shfl_xor_sync(FULL, blo2, o));
-            bhi0 = fmaxf(bhi0, __shfl_xor_sync(FULL, bhi0, o));
-            bhi1 = fmaxf(bhi1, __shfl_xor_sync(FULL, bhi1, o));
-            bhi2 = fmaxf(bhi2, __shfl_xor_sync(FULL, bhi2, o));
-        }
-        const int C = build_rows(R, cell_start, Fa.cell_off, dx0, dy0, dz0, hx, hy, hz, lane);
-        const int np = (qcount + 1) >> 1;
-        // a candidate farther than r_c from the query box pairs with none of
-        // the queries; the margin keeps every candidate the exact test passes
-        const float box_thr = gp.rc2 * 1.0001f;
+    for (int o = 16; o > 0; o >>= 1) {
+        blo0 = fminf(blo0, __shfl_xor_sync(FULL, blo0, o));
+        blo1 = fminf(blo1, __shfl_xor_sync(FULL, blo1, o));
+        blo2 = fminf(blo2, __shfl_xor_sync(FULL, blo2, o));
+        bhi0 = fmaxf(bhi0, __shfl_xor_sync(FULL, bhi0, o));
+        bhi1 = fmaxf(bhi1, __shfl_xor_sync(FULL, bhi1, o));
+        bhi2 = fmaxf(bhi2, __shfl_xor_sync(FULL, bhi2, o));
+    }
+    const int C = build_rows(R, cell_start, Fa.cell_off, dx0, dy0, dz0, hx, hy, hz, lane);
+    const int np = (qcount + 1) >> 1;
+    // a candidate farther than r_c from the query box pairs with none of
+    // the queries; the margin keeps every candidate the exact test passes
+    const float box_thr = gp.rc2 * 1.0001f;
 
-        // per lane, over its candidates x with sums w0 = sum w, dc = sum w d,
-        // qc = sum w d d^T: W, D, Q and sum w0 x, sum w0 x x^T, sum x dc^T
+    // per lane, over its candidates x with sums w0 = sum w, dc = sum w d,
+    // qc = sum w d d^T: W, D, Q and sum w0 x, sum w0 x x^T, sum x dc^T
 #pragma unroll
-        for (int k = 0; k < N_ACC / 4; ++k) sacc[k] = make_float4(0.f, 0.f, 0.f, 0.f);
-        int cnt = 0;
-        int c_s = 0, qhead = 0, qlen = 0;            // stream position, ring head and fill
-        while (c_s < C || qlen > 0) {
-            // stream the 27-cell candidates through the box test into the
-            // ring until it holds a full batch (or the stream ends)
-            while (qlen < 32 && c_s < C) {
-                const int v = c_s + lane;
-                bool keep = false;
-                float4 ent = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (v < C) {
-                    int dx, dy, dz;
-                    const int i = stream_point(R, v, dx, dy, dz);
-                    const float4 p = __ldg(pts4 + i);
-                    ent.x = fmaf((float)dx, gp.hf, p.x);
-                    ent.y = fmaf((float)dy, gp.hf, p.y);
-                    ent.z = fmaf((float)dz, gp.hf, p.z);
-                    ent.w = __int_as_float(i);
-                    const float e0 = fmaxf(fmaxf(blo0 - ent.x, ent.x - bhi0), 0.f);
-                    const float e1 = fmaxf(fmaxf(blo1 - ent.y, ent.y - bhi1), 0.f);
-                    const float e2 = fmaxf(fmaxf(blo2 - ent.z, ent.z - bhi2), 0.f);
-                    keep = fmaf(e0, e0, fmaf(e1, e1, e2 * e2)) < box_thr;
-                }
-                const unsigned bal = __ballot_sync(FULL, keep);
-                if (keep) cq[(qhead + qlen + __popc(bal & ((1u << lane) - 1u))) & (CQ_N - 1)] = ent;
-                qlen += __popc(bal);
-                c_s += 32;
+    for (int k = 0; k < N_ACC / 4; ++k) sacc[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+    int cnt = 0;
+    int c_s = 0, qhead = 0, qlen = 0;            // stream position, ring head and fill
+    while (c_s < C || qlen > 0) {
+        // stream the 27-cell candidates through the box test into the
+        // ring until it holds a full batch (or the stream ends)
+        while (qlen < 32 && c_s < C) {
+            const int v = c_s + lane;
+            bool keep = false;
+            float4 ent = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (v < C) {
+                int dx, dy, dz;
+                const int i = stream_point(R, v, dx, dy, dz);
+                const float4 p = __ldg(pts4 + i);
+                ent.x = fmaf((float)dx, gp.hf, p.x);
+                ent.y = fmaf((float)dy, gp.hf, p.y);
+                ent.z = fmaf((float)dz, gp.hf, p.z);
+                ent.w = __int_as_float(i);
+                const float e0 = fmaxf(fmaxf(blo0 - ent.x, ent.x - bhi0), 0.f);
+                const float e1 = fmaxf(fmaxf(blo1 - ent.y, ent.y - bhi1), 0.f);
+                const float e2 = fmaxf(fmaxf(blo2 - ent.z, ent.z - bhi2), 0.f);
+                keep = fmaf(e0, e0, fmaf(e1, e1, e2 * e2)) < box_thr;
             }
-            __syncwarp();
-            const int nb = qlen < 32 ? qlen : 32;
-            if (nb == 0) break;                      // stream ended with the ring empty
-            const bool has = lane < nb;
-            const float4 ent = has ? cq[(qhead + lane) & (CQ_N - 1)] : make_float4(0.f, 0.f, 0.f, 0.f);
-            qhead = (qhead + nb) & (CQ_N - 1);
-            qlen -= nb;
-            __syncwarp();
-            const int i = __float_as_int(ent.w);
-            // candidate relative to the home cell centre
-            const float x0 = ent.x, x1 = ent.y, x2 = ent.z;
-            const float xx = fmaf(x0, x0, fmaf(x1, x1, x2 * x2));
-            const float thr = gp.rc2 - xx;
-            Sem<DP, BF16> cs;
-            if (DP > 0 && !BF16) cs.load(sem_sorted, i, has);
-            float4 cc = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (COLOR && has) cc = __ldg(col4 + i);
-            // cutoff test against query pairs: bit j set when |x - y_j| < r_c
-            unsigned mk = 0u;
-            {
-                const u64 X0 = f2(x0, x0), X1 = f2(x1, x1), X2 = f2(x2, x2);
-#pragma unroll 4
-                for (int pj = 0; pj < np; ++pj) {
-                    const ulonglong2 a = test2[2 * pj], b = test2[2 * pj + 1];
-                    const float2 t = f2_split(ffma2(X0, a.x, ffma2(X1, a.y, ffma2(X2, b.x, b.y))));
-                    mk |= ((t.x < thr ? 1u : 0u) | (t.y < thr ? 2u : 0u)) << (2 * pj);
-                }
-            }
-            if (!has) mk = 0u;
-            if constexpr (BF16 && DP > 0) {
-                label_gram_bf16<DP>(reinterpret_cast<const unsigned*>(sem_sorted), ssq, i, __ballot_sync(FULL, has),
-                                    lane, gram);
-                __syncwarp();
-            }
-            const float* gcol = gram + lane;                      // column of this lane's candidate
-            const u64 XA = f2(x0, x1), XB = f2(x2, x0);
-            float w0 = 0.f, dz_s = 0.f, q12 = 0.f, q22 = 0.f;
-            u64 D01 = 0ull, Q0011 = 0ull, Q0201 = 0ull;
-            // the bit walk, compiled twice: with the semantic-pruning test
-            // only when pruning is on (a uniform branch per batch).  Each
-            // iteration takes 4 of the lane's pairs as independent dependency
-            // chains (missing ones weigh zero); at 2 CTAs per SM the registers
-            // for them are there, and the ILP hides more latency than a third
-            // CTA's warps did.
-            auto walk = [&](auto prune) {
-                constexpr bool PRUNE = decltype(prune)::value;
-                auto pair_w = [&](int j, u64& E01, u64& E20, float& ez, bool& kept) -> float {
-                    const ulonglong2 m = walk2[j];
-                    E01 = ffma2(H2, m.x, XA);
-                    E20 = ffma2(H2, m.y, XB);
-                    const float2 exy = f2_split(E01);
-                    ez = f2_split(E20).x;
-                    const float dd = fmaf(exy.x, exy.x, fmaf(exy.y, exy.y, ez * ez));
-                    float arg = dd * gp.kg;
-                    if (COLOR) {
-                        const float4 qc = scq[j];
-                        const float cr = cc.x - qc.x, cg = cc.y - qc.y, cb = cc.z - qc.z;
-                        arg = fmaf(fmaf(cr, cr, fmaf(cg, cg, cb * cb)), gp.kc, arg);
-                    }
-                    float s;
-                    if constexpr (BF16 && DP > 0) s = gcol[j * GRAM_LD];
-                    else s = SemRow<DP, BF16>::dot(cs, ssq + j * SW);
-                    kept = true;
-                    if constexpr (PRUNE) kept = s >= gp.sem_min;
-                    return kept ? s * ex2_approx(arg) : 0.f;
-                };
-                auto add = [&](float w, u64 E01, u64 E20, float ez, bool kept) {
-                    const u64 WXY = fmul2(f2(w, w), E01);
-                    const float wz = w * ez;
-                    w0 += w;
-                    D01 = fadd2(D01, WXY);
-                    dz_s += wz;
-                    Q0011 = ffma2(WXY, E01, Q0011);
-                    Q0201 = ffma2(WXY, E20, Q0201);
-                    q12 = fmaf(f2_split(WXY).y, ez, q12);
-                    q22 = fmaf(wz, ez, q22);
-                    cnt += kept ? 1 : 0;
-                };
-                constexpr int U = 4;   // pairs per iteration
-                while (__any_sync(FULL, mk != 0u)) {
-                    if (mk) {
-                        int jj[U];
-                        bool hv[U];
-#pragma unroll
-                        for (int u = 0; u < U; ++u) {
-                            hv[u] = mk != 0u;
-                            jj[u] = hv[u] ? __ffs(mk) - 1 : 0;
-                            if (hv[u]) mk &= mk - 1u;
-                        }
-                        u64 Ea[U], Eb[U];
-                        float ez[U], w[U];
-                        bool kp[U];
-#pragma unroll
-                        for (int u = 0; u < U; ++u) w[u] = pair_w(jj[u], Ea[u], Eb[u], ez[u], kp[u]);
-#pragma unroll
-                        for (int u = 0; u < U; ++u) {
-                            if (!hv[u]) { w[u] = 0.f; kp[u] = false; }
-                            add(w[u], Ea[u], Eb[u], ez[u], kp[u]);
-                        }
-                    }
-                }
-            };
-            if (DP > 0 && gp.sem_min > -__int_as_float(0x7f800000)) walk(std::true_type{});
-            else walk(std::false_type{});
-            const float2 dxy = f2_split(D01), q0011 = f2_split(Q0011), q0201 = f2_split(Q0201);
-            const float x[3] = {x0, x1, x2};
-            const float dc[3] = {dxy.x, dxy.y, dz_s};
-            const float qc[6] = {q0011.x, q0201.y, q0201.x, q0011.y, q12, q22};
-            float a[N_ACC];
-#pragma unroll
-            for (int k = 0; k < N_ACC / 4; ++k) {
-                const float4 t = sacc[k];
-                a[4 * k] = t.x; a[4 * k + 1] = t.y; a[4 * k + 2] = t.z; a[4 * k + 3] = t.w;
-            }
-            a[A_W] += w0;
-#pragma unroll
-            for (int t6 = 0; t6 < 6; ++t6) a[A_Q + t6] += qc[t6];
-#pragma unroll
-            for (int mm = 0; mm < 3; ++mm) {
-                a[A_D + mm] += dc[mm];
-                const float wx = w0 * x[mm];
-                a[A_SWX + mm] += wx;
-#pragma unroll
-                for (int l = 0; l < 3; ++l) a[A_SXD + 3 * mm + l] = fmaf(x[mm], dc[l], a[A_SXD + 3 * mm + l]);
-#pragma unroll
-                for (int l = mm; l < 3; ++l) {
-                    const int t6 = mm == 0 ? l : (mm == 1 ? 2 + l : 5);
-                    a[A_SWXX + t6] = fmaf(wx, x[l], a[A_SWXX + t6]);
-                }
-            }
-#pragma unroll
-            for (int k = 0; k < N_ACC / 4; ++k) sacc[k] = make_float4(a[4 * k], a[4 * k + 1], a[4 * k + 2], a[4 * k + 3]);
+            const unsigned bal = __ballot_sync(FULL, keep);
+            if (keep) cq[(qhead + qlen + __popc(bal & ((1u << lane) - 1u))) & (CQ_N - 1)] = ent;
+            qlen += __popc(bal);
+            c_s += 32;
         }
+        __syncwarp();
+        const int nb = qlen < 32 ? qlen : 32;
+        if (nb == 0) break;                      // stream ended with the ring empty
+        const bool has = lane < nb;
+        const float4 ent = has ? cq[(qhead + lane) & (CQ_N - 1)] : make_float4(0.f, 0.f, 0.f, 0.f);
+        qhead = (qhead + nb) & (CQ_N - 1);
+        qlen -= nb;
+        __syncwarp();
+        const int i = __float_as_int(ent.w);
+        // candidate relative to the home cell centre
+        const float x0 = ent.x, x1 = ent.y, x2 = ent.z;
+        const float xx = fmaf(x0, x0, fmaf(x1, x1, x2 * x2));
+        const float thr = gp.rc2 - xx;
+        Sem<DP, BF16> cs;
+        if (DP > 0 && !BF16) cs.load(sem_sorted, i, has);
+        float4 cc = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (COLOR && has) cc = __ldg(col4 + i);
+        // cutoff test against query pairs: bit j set when |x - y_j| < r_c
+        unsigned mk = 0u;
+        {
+            const u64 X0 = f2(x0, x0), X1 = f2(x1, x1), X2 = f2(x2, x2);
+#pragma unroll 4
+            for (int pj = 0; pj < np; ++pj) {
+                const ulonglong2 a = test2[2 * pj], b = test2[2 * pj + 1];
+                const float2 t = f2_split(ffma2(X0, a.x, ffma2(X1, a.y, ffma2(X2, b.x, b.y))));
+                mk |= ((t.x < thr ? 1u : 0u) | (t.y < thr ? 2u : 0u)) << (2 * pj);
+            }
+        }
+        if (!has) mk = 0u;
+        if constexpr (BF16 && DP > 0) {
+            label_gram_bf16<DP>(reinterpret_cast<const unsigned*>(sem_sorted), ssq, i, __ballot_sync(FULL, has),
+                                lane, gram);
+            __syncwarp();
+        }
+        const float* gcol = gram + lane;                      // column of this lane's candidate
+        const u64 XA = f2(x0, x1), XB = f2(x2, x0);
+        float w0 = 0.f, dz_s = 0.f, q12 = 0.f, q22 = 0.f;
+        u64 D01 = 0ull, Q0011 = 0ull, Q0201 = 0ull;
+        // the bit walk, compiled twice: with the semantic-pruning test
+        // only when pruning is on (a uniform branch per batch).  Each
+        // iteration takes 4 of the lane's pairs as independent dependency
+        // chains (missing ones weigh zero); at 2 CTAs per SM the registers
+        // for them are there, and the ILP hides more latency than a third
+        // CTA's warps did.
+        auto walk = [&](auto prune) {
+            constexpr bool PRUNE = decltype(prune)::value;
+            auto pair_w = [&](int j, u64& E01, u64& E20, float& ez, bool& kept) -> float {
+                const ulonglong2 m = walk2[j];
+                E01 = ffma2(H2, m.x, XA);
+                E20 = ffma2(H2, m.y, XB);
+                const float2 exy = f2_split(E01);
+                ez = f2_split(E20).x;
+                const float dd = fmaf(exy.x, exy.x, fmaf(exy.y, exy.y, ez * ez));
+                float arg = dd * gp.kg;
+                if (COLOR) {
+                    const float4 qc = scq[j];
+                    const float cr = cc.x - qc.x, cg = cc.y - qc.y, cb = cc.z - qc.z;
+                    arg = fmaf(fmaf(cr, cr, fmaf(cg, cg, cb * cb)), gp.kc, arg);
+                }
+                float s;
+                if constexpr (BF16 && DP > 0) s = gcol[j * GRAM_LD];
+                else s = SemRow<DP, BF16>::dot(cs, ssq + j * SW);
+                kept = true;
+                if constexpr (PRUNE) kept = s >= gp.sem_min;
+                return kept ? s * ex2_approx(arg) : 0.f;
+            };
+            auto add = [&](float w, u64 E01, u64 E20, float ez, bool kept) {
+                const u64 WXY = fmul2(f2(w, w), E01);
+                const float wz = w * ez;
+                w0 += w;
+                D01 = fadd2(D01, WXY);
+                dz_s += wz;
+                Q0011 = ffma2(WXY, E01, Q0011);
+                Q0201 = ffma2(WXY, E20, Q0201);
+                q12 = fmaf(f2_split(WXY).y, ez, q12);
+                q22 = fmaf(wz, ez, q22);
+                cnt += kept ? 1 : 0;
+            };
+            constexpr int U = 4;   // pairs per iteration
+            while (__any_sync(FULL, mk != 0u)) {
+                if (mk) {
+                    int jj[U];
+                    bool hv[U];
+#pragma unroll
+                    for (int u = 0; u < U; ++u) {
+                        hv[u] = mk != 0u;
+                        jj[u] = hv[u] ? __ffs(mk) - 1 : 0;
+                        if (hv[u]) mk &= mk - 1u;
+                    }
+                    u64 Ea[U], Eb[U];
+                    float ez[U], w[U];
+                    bool kp[U];
+#pragma unroll
+                    for (int u = 0; u < U; ++u) w[u] = pair_w(jj[u], Ea[u], Eb[u], ez[u], kp[u]);
+#pragma unroll
+                    for (int u = 0; u < U; ++u) {
+                        if (!hv[u]) { w[u] = 0.f; kp[u] = false; }
+                        add(w[u], Ea[u], Eb[u], ez[u], kp[u]);
+                    }
+                }
+            }
+        };
+        if (DP > 0 && gp.sem_min > -__int_as_float(0x7f800000)) walk(std::true_type{});
+        else walk(std::false_type{});
+        const float2 dxy = f2_split(D01), q0011 = f2_split(Q0011), q0201 = f2_split(Q0201);
+        const float x[3] = {x0, x1, x2};
+        const float dc[3] = {dxy.x, dxy.y, dz_s};
+        const float qc[6] = {q0011.x, q0201.y, q0201.x, q0011.y, q12, q22};
         float a[N_ACC];
 #pragma unroll
         for (int k = 0; k < N_ACC / 4; ++k) {
             const float4 t = sacc[k];
             a[4 * k] = t.x; a[4 * k + 1] = t.y; a[4 * k + 2] = t.z; a[4 * k + 3] = t.w;
         }
-        const float W = a[A_W];
-        const float Dv[3] = {a[A_D], a[A_D + 1], a[A_D + 2]};
-        const float* Qm = a + A_Q;
-        const float* Swx = a + A_SWX;
-        const float* Swxx = a + A_SWXX;
-        const float* Sxd = a + A_SXD;
-        // y' = x - d:  sum w y' = sum w0 x - D;  sum w y'y'^T = sum w0 x x^T -
-        // sum (x dc^T + dc x^T) + Q;  sum w d y'^T = sum dc x^T - Q
-        float Sy[3], Myy[6], Mdy[9];
+        a[A_W] += w0;
 #pragma unroll
-        for (int mm = 0; mm < 3; ++mm) Sy[mm] = Swx[mm] - Dv[mm];
+        for (int t6 = 0; t6 < 6; ++t6) a[A_Q + t6] += qc[t6];
 #pragma unroll
-        for (int mm = 0; mm < 3; ++mm)
+        for (int mm = 0; mm < 3; ++mm) {
+            a[A_D + mm] += dc[mm];
+            const float wx = w0 * x[mm];
+            a[A_SWX + mm] += wx;
+#pragma unroll
+            for (int l = 0; l < 3; ++l) a[A_SXD + 3 * mm + l] = fmaf(x[mm], dc[l], a[A_SXD + 3 * mm + l]);
 #pragma unroll
             for (int l = mm; l < 3; ++l) {
                 const int t6 = mm == 0 ? l : (mm == 1 ? 2 + l : 5);
-                Myy[t6] = Swxx[t6] - (Sxd[3 * mm + l] + Sxd[3 * l + mm]) + Qm[t6];
+                a[A_SWXX + t6] = fmaf(wx, x[l], a[A_SWXX + t6]);
             }
+        }
 #pragma unroll
-        for (int mm = 0; mm < 3; ++mm)
+        for (int k = 0; k < N_ACC / 4; ++k) sacc[k] = make_float4(a[4 * k], a[4 * k + 1], a[4 * k + 2], a[4 * k + 3]);
+    }
+    float a[N_ACC];
 #pragma unroll
-            for (int l = 0; l < 3; ++l) {
-                const int qi = (mm <= l) ? (mm == 0 ? l : (mm == 1 ? 2 + l : 5))
-                                         : (l == 0 ? mm : (l == 1 ? 2 + mm : 5));
-                Mdy[3 * mm + l] = Sxd[3 * l + mm] - Qm[qi];
+    for (int k = 0; k < N_ACC / 4; ++k) {
+        const float4 t = sacc[k];
+        a[4 * k] = t.x; a[4 * k + 1] = t.y; a[4 * k + 2] = t.z; a[4 * k + 3] = t.w;
+    }
+    const float W = a[A_W];
+    const float Dv[3] = {a[A_D], a[A_D + 1], a[A_D + 2]};
+    const float* Qm = a + A_Q;
+    const float* Swx = a + A_SWX;
+    const float* Swxx = a + A_SWXX;
+    const float* Sxd = a + A_SXD;
+    // y' = x - d:  sum w y' = sum w0 x - D;  sum w y'y'^T = sum w0 x x^T -
+    // sum (x dc^T + dc x^T) + Q;  sum w d y'^T = sum dc x^T - Q
+    float Sy[3], Myy[6], Mdy[9];
+#pragma unroll
+    for (int mm = 0; mm < 3; ++mm) Sy[mm] = Swx[mm] - Dv[mm];
+#pragma unroll
+    for (int mm = 0; mm < 3; ++mm)
+#pragma unroll
+        for (int l = mm; l < 3; ++l) {
+            const int t6 = mm == 0 ? l : (mm == 1 ? 2 + l : 5);
+            Myy[t6] = Swxx[t6] - (Sxd[3 * mm + l] + Sxd[3 * l + mm]) + Qm[t6];
+        }
+#pragma unroll
+    for (int mm = 0; mm < 3; ++mm)
+#pragma unroll
+        for (int l = 0; l < 3; ++l) {
+            const int qi = (mm <= l) ? (mm == 0 ? l : (mm == 1 ? 2 + l : 5))
+                                     : (l == 0 ? mm : (l == 1 ? 2 + mm : 5));
+            Mdy[3 * mm + l] = Sxd[3 * l + mm] - Qm[qi];
+        }
+    store_moments(W, Dv, Sy, Myy, Mdy, Qm, cnt, Fa, hx, hy, hz, gp, edges[e].scale,
+                  acc + (long long)e * ACC_N, lane);
+
+}
+
+template <int DP, bool BF16, bool COLOR>
+__global__ void __launch_bounds__(PAIR_T, (BF16 && DP > 0) ? 2 : RK_PAIR_MINB)
+k_pairs(const int* __restrict__ unit_start, const int* __restrict__ n_units, int* unit_counter,
+        const PairArgs A, const int* done) {
+    if (done && *done) return;
+    extern __shared__ float4 smem4[];
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    float* wb = reinterpret_cast<float*>(smem4) + warp * warp_smem_words<DP, BF16, COLOR>();
+    const int nu = *n_units;
+    for (;;) {
+        int u = 0;
+        if (lane == 0) u = atomicAdd(unit_counter, 1);
+        u = __shfl_sync(FULL, u, 0);
+        if (u >= nu) break;
+        pair_unit<DP, BF16, COLOR>(A, unit_start[u], wb, lane);
+    }
+}
+
+// The pair stage of several problems in one persistent launch: the units of
+// job j are numbered after those of jobs 0..j-1 (a job whose solve is done
+// contributes none), warps take global unit numbers from one counter, find
+// the job by binary search over the prefix, and run the unit with that
+// job's arrays.  Every job adds into its own fixed-point accumulators, so a
+// problem's results do not depend on which other problems share the launch.
+template <int DP, bool BF16, bool COLOR>
+__global__ void __launch_bounds__(PAIR_T, (BF16 && DP > 0) ? 2 : RK_PAIR_MINB)
+k_pairs_multi(const PairJob* __restrict__ jobs, int n_jobs, int* unit_counter) {
+    __shared__ int s_pref[MAX_PAIR_JOBS + 1];
+    extern __shared__ float4 smem4[];
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    if (warp == 0) {
+        int carry = 0;
+        for (int base = 0; base < n_jobs; base += 32) {
+            const int j = base + lane;
+            int n = 0;
+            if (j < n_jobs) {
+                const int* dn = jobs[j].done;
+                n = (dn && *dn) ? 0 : *jobs[j].n_units;
             }
-        store_moments(W, Dv, Sy, Myy, Mdy, Qm, cnt, Fa, hx, hy, hz, gp, edges[e].scale,
-                      acc + (long long)e * ACC_N, lane);
+            int inc = n;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int v = __shfl_up_sync(FULL, inc, o);
+                if (lane >= o) inc += v;
+            }
+            if (j < n_jobs) s_pref[j] = carry + inc - n;
+            carry += __shfl_sync(FULL, inc, 31);
+        }
+        if (lane == 0) s_pref[n_jobs] = carry;
+    }
+    __syncthreads();
+    const int total = s_pref[n_jobs];
+    float* wb = reinterpret_cast<float*>(smem4) + warp * warp_smem_words<DP, BF16, COLOR>();
+    for (;;) {
+        int u = 0;
+        if (lane == 0) u = atomicAdd(unit_counter, 1);
+        u = __shfl_sync(FULL, u, 0);
+        if (u >= total) break;
+        int lo = 0, hi = n_jobs - 1;                 // last job with s_pref[j] <= u
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (s_pref[mid] <= u) lo = mid; else hi = mid - 1;
+        }
+        const PairJob* J = jobs + lo;
+        pair_unit<DP, BF16, COLOR>(J->a, J->unit_start[u - s_pref[lo]], wb, lane);
     }
 }
 
@@ -886,7 +955,7 @@ k_pairs_topk(const int* __restrict__ unit_start, const int* __restrict__ n_units
              const EdgeDev* __restrict__ edges, int E, const FrameDev* __restrict__ frames,
              const int* __restrict__ cell_start, const float4* __restrict__ pts4,
              const void* __restrict__ sem_sorted, const float4* __restrict__ col4, GridParams gp,
-             long long* __restrict__ acc, const int* done) {
+             long long* __restrict__ acc, int uq, const int* done) {
     if (done && *done) return;
     extern __shared__ float4 smem4[];
     constexpr int SW = SemRow<DP, BF16>::WORDS;
@@ -908,7 +977,7 @@ k_pairs_topk(const int* __restrict__ unit_start, const int* __restrict__ n_units
         if (u >= nu) break;
         const int k0 = unit_start[u];
         const uint32_t key0 = qkey[k0];
-        const int qcount = unit_queries(qkey, Q, k0, key0, lane);
+        const int qcount = unit_queries(qkey, Q, k0, key0, lane, uq);
         const int e = find_edge_bin(edges, E, key0);
         const FrameDev& Fa = frames[edges[e].a];
         const int dx0 = Fa.dim[0], dy0 = Fa.dim[1], dz0 = Fa.dim[2];
@@ -1055,7 +1124,7 @@ k_emit_pairs(const int* __restrict__ unit_start, const int* __restrict__ n_units
              const uint32_t* __restrict__ qkey, const float4* __restrict__ slots, long long Q,
              const EdgeDev* __restrict__ edges, int E, const FrameDev* __restrict__ frames,
              const int* __restrict__ cell_start, const float4* __restrict__ pts4, GridParams gp,
-             int edge_sel, const int* __restrict__ perm_local, long long capacity,
+             int edge_sel, const int* __restrict__ perm_local, long long capacity, int uq,
              int* __restrict__ i_out, int* __restrict__ j_out, unsigned long long* n_out) {
     __shared__ float4 s_m[PAIR_T / 32][UQ];
     __shared__ int s_j[PAIR_T / 32][UQ];
@@ -1074,7 +1143,7 @@ k_emit_pairs(const int* __restrict__ unit_start, const int* __restrict__ n_units
         const uint32_t key0 = qkey[k0];
         const int e = find_edge_bin(edges, E, key0);
         if (e != edge_sel) continue;
-        const int qcount = unit_queries(qkey, Q, k0, key0, lane);
+        const int qcount = unit_queries(qkey, Q, k0, key0, lane, uq);
         const FrameDev& Fa = frames[edges[e].a];
         const int dx0 = Fa.dim[0], dy0 = Fa.dim[1], dz0 = Fa.dim[2];
         const int cell = (int)(key0 - edges[e].bin_off);
@@ -1120,83 +1189,76 @@ inline unsigned blocks_for(long long n, int t) {
     return (unsigned)b;
 }
 
-template <int DP, bool BF16, bool COLOR>
-void run_pairs_topk(unsigned grid, cudaStream_t st, const int* unit_start, const int* n_units,
-                    int* unit_counter, const uint32_t* qkey, const float4* slots, long long Q,
-                    const EdgeDev* edges, int E, const FrameDev* frames, const int* cell_start,
-                    const float4* pts4, const void* sem, const float4* col4, GridParams gp,
-                    long long* acc, const int* done) {
-    const size_t smem = sizeof(float) * (PAIR_T / 32) * warp_smem_words_topk<DP, BF16, COLOR>();
-    static int blocks_per_sm = 0;
-    if (!blocks_per_sm) {
-        cudaFuncSetAttribute(k_pairs_topk<DP, BF16, COLOR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_pairs_topk<DP, BF16, COLOR>, PAIR_T,
-                                                      smem);
-        if (blocks_per_sm < 1) blocks_per_sm = 1;
+// Resident CTAs per SM of a pair kernel at its shared-memory size (queried
+// once per instantiation; the dynamic shared memory opt-in is set then).
+template <typename KernelT>
+int pair_blocks_per_sm(KernelT kernel, size_t smem, int* cache) {
+    if (!*cache) {
+        cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        int b = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kernel, PAIR_T, smem);
+        *cache = b < 1 ? 1 : b;
     }
-    grid *= (unsigned)blocks_per_sm;
-    k_pairs_topk<DP, BF16, COLOR><<<grid, PAIR_T, smem, st>>>(unit_start, n_units, unit_counter, qkey, slots,
-                                                              Q, edges, E, frames, cell_start, pts4, sem,
-                                                              col4, gp, acc, done);
+    return *cache;
+}
+
+inline unsigned pair_grid(int num_sms, int resident, int ctas_per_sm) {
+    const int per_sm = (ctas_per_sm > 0 && ctas_per_sm < resident) ? ctas_per_sm : resident;
+    return (unsigned)(num_sms * per_sm);
 }
 
 template <int DP, bool BF16, bool COLOR>
-void run_pairs(unsigned grid, cudaStream_t st, const int* unit_start, const int* n_units,
-               int* unit_counter, const uint32_t* qkey, const float4* slots, long long Q,
-               const EdgeDev* edges, int E, const FrameDev* frames, const int* cell_start,
-               const float4* pts4, const void* sem, const float4* col4, GridParams gp,
-               long long* acc, const int* done) {
-    const size_t smem = sizeof(float) * (PAIR_T / 32) * warp_smem_words<DP, BF16, COLOR>();
-    static int blocks_per_sm = 0;   // opt in to > 48 KB and size the persistent grid, once
-    if (!blocks_per_sm) {
-        cudaFuncSetAttribute(k_pairs<DP, BF16, COLOR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_pairs<DP, BF16, COLOR>, PAIR_T, smem);
-        if (blocks_per_sm < 1) blocks_per_sm = 1;
-    }
-    grid *= (unsigned)blocks_per_sm;
-    if (gp.top_k > 0) {
-        run_pairs_topk<DP, BF16, COLOR>(grid / (unsigned)blocks_per_sm, st, unit_start, n_units, unit_counter,
-                                        qkey, slots, Q, edges, E, frames, cell_start, pts4, sem, col4, gp, acc,
-                                        done);
+void run_pairs(const PairLaunch& L, const PairArgs& A) {
+    if (A.gp.top_k > 0) {
+        const size_t smem = sizeof(float) * (PAIR_T / 32) * warp_smem_words_topk<DP, BF16, COLOR>();
+        static int resident = 0;
+        const int r = pair_blocks_per_sm(k_pairs_topk<DP, BF16, COLOR>, smem, &resident);
+        k_pairs_topk<DP, BF16, COLOR><<<pair_grid(L.num_sms, r, L.ctas_per_sm), PAIR_T, smem, L.stream>>>(
+            L.unit_start, L.n_units, L.unit_counter, A.qkey, A.slots, A.Q, A.edges, A.E, A.frames, A.cell_start,
+            A.pts4, A.sem_sorted, A.col4, A.gp, A.acc, A.uq, L.done);
         return;
     }
-    k_pairs<DP, BF16, COLOR><<<grid, PAIR_T, smem, st>>>(unit_start, n_units, unit_counter, qkey, slots,
-                                                         Q, edges, E, frames, cell_start, pts4, sem,
-                                                         col4, gp, acc, done);
+    const size_t smem = sizeof(float) * (PAIR_T / 32) * warp_smem_words<DP, BF16, COLOR>();
+    static int resident = 0;   // opt in to > 48 KB and size the persistent grid, once
+    const int r = pair_blocks_per_sm(k_pairs<DP, BF16, COLOR>, smem, &resident);
+    k_pairs<DP, BF16, COLOR><<<pair_grid(L.num_sms, r, L.ctas_per_sm), PAIR_T, smem, L.stream>>>(
+        L.unit_start, L.n_units, L.unit_counter, A, L.done);
 }
 
-template <bool COLOR>
-bool dispatch_pairs(unsigned grid, cudaStream_t st, const int* unit_start, const int* n_units,
-                    int* unit_counter, const uint32_t* qkey, const float4* slots, long long Q,
-                    const EdgeDev* edges, int E, const FrameDev* frames, const int* cell_start,
-                    const float4* pts4, const void* sem, const float4* col4, GridParams gp,
-                    long long* acc, const int* done) {
-#define RK_P(DPV, BFV)                                                                            \
-    run_pairs<DPV, BFV, COLOR>(grid, st, unit_start, n_units, unit_counter, qkey, slots, Q, edges, \
-                               E, frames, cell_start, pts4, sem, col4, gp, acc, done);            \
-    return true
-    if (gp.sem_pad == 0) { RK_P(0, false); }
+template <int DP, bool BF16, bool COLOR>
+void run_pairs_multi(const PairJob* jobs, int n_jobs, int* counter, int num_sms, int ctas_per_sm,
+                     cudaStream_t st) {
+    const size_t smem = sizeof(float) * (PAIR_T / 32) * warp_smem_words<DP, BF16, COLOR>();
+    static int resident = 0;
+    const int r = pair_blocks_per_sm(k_pairs_multi<DP, BF16, COLOR>, smem, &resident);
+    k_pairs_multi<DP, BF16, COLOR><<<pair_grid(num_sms, r, ctas_per_sm), PAIR_T, smem, st>>>(jobs, n_jobs,
+                                                                                            counter);
+}
+
+// Calls F.template operator()<DP, BF16>() for the label layout of gp
+// (padded width, FP32 or BF16 rows); false for a layout without kernels.
+template <typename F>
+bool with_label_layout(const GridParams& gp, const F& f) {
+    if (gp.sem_pad == 0) { f.template operator()<0, false>(); return true; }
     if (gp.sem_bf16) {
         switch (gp.sem_pad) {
-            case 8: RK_P(8, true);
-            case 16: RK_P(16, true);
-            case 24: RK_P(24, true);
-            case 32: RK_P(32, true);
+            case 8: f.template operator()<8, true>(); return true;
+            case 16: f.template operator()<16, true>(); return true;
+            case 24: f.template operator()<24, true>(); return true;
+            case 32: f.template operator()<32, true>(); return true;
             default: return false;
         }
     }
     switch (gp.sem_pad) {
-        case 4: RK_P(4, false);
-        case 8: RK_P(8, false);
-        case 12: RK_P(12, false);
-        case 16: RK_P(16, false);
-        case 20: RK_P(20, false);
-        case 24: RK_P(24, false);
-        case 32: RK_P(32, false);
+        case 4: f.template operator()<4, false>(); return true;
+        case 8: f.template operator()<8, false>(); return true;
+        case 12: f.template operator()<12, false>(); return true;
+        case 16: f.template operator()<16, false>(); return true;
+        case 20: f.template operator()<20, false>(); return true;
+        case 24: f.template operator()<24, false>(); return true;
+        case 32: f.template operator()<32, false>(); return true;
         default: return false;
     }
-#undef RK_P
 }
 }  // namespace
 
@@ -1224,37 +1286,63 @@ void launch_query_gather(const uint32_t* qkey_sorted, const int* qval_sorted, co
     count_launch();
 }
 
-void launch_units(const uint32_t* qkey_sorted, const int* bin_first, long long Q, int* unit_start,
+void launch_units(const uint32_t* qkey_sorted, const int* bin_first, long long Q, int uq, int* unit_start,
                   int* n_units, const int* done, cudaStream_t st) {
     if (Q <= 0) return;
-    k_units<<<blocks_for(Q, 256), 256, 0, st>>>(qkey_sorted, bin_first, Q, unit_start, n_units, done);
+    if (uq < 1 || uq > UQ) uq = UQ;
+    k_units<<<blocks_for(Q, 256), 256, 0, st>>>(qkey_sorted, bin_first, Q, uq, unit_start, n_units, done);
     count_launch();
 }
 
-void launch_pairs(const int* unit_start, const int* n_units, int* unit_counter,
-                  const uint32_t* qkey, const float4* slots, long long Q, const EdgeDev* edges, int E,
-                  const FrameDev* frames, const int* cell_start, const float4* pts4,
-                  const void* sem_sorted, const float4* col4, GridParams gp, long long* acc,
-                  const int* done, int num_sms, cudaStream_t st) {
-    if (Q <= 0) return;
-    const unsigned grid = (unsigned)num_sms;   // times the resident blocks per SM
-    const bool ok = gp.color
-        ? dispatch_pairs<true>(grid, st, unit_start, n_units, unit_counter, qkey, slots, Q, edges, E, frames,
-                               cell_start, pts4, sem_sorted, col4, gp, acc, done)
-        : dispatch_pairs<false>(grid, st, unit_start, n_units, unit_counter, qkey, slots, Q, edges, E, frames,
-                                cell_start, pts4, sem_sorted, col4, gp, acc, done);
+namespace {
+struct SingleLaunch {
+    const PairLaunch& L;
+    const PairArgs& A;
+    template <int DP, bool BF16>
+    void operator()() const {
+        if (A.gp.color) run_pairs<DP, BF16, true>(L, A);
+        else run_pairs<DP, BF16, false>(L, A);
+    }
+};
+struct MultiLaunch {
+    const PairJob* jobs;
+    int n_jobs;
+    bool color;
+    int* counter;
+    int num_sms, ctas_per_sm;
+    cudaStream_t st;
+    template <int DP, bool BF16>
+    void operator()() const {
+        if (color) run_pairs_multi<DP, BF16, true>(jobs, n_jobs, counter, num_sms, ctas_per_sm, st);
+        else run_pairs_multi<DP, BF16, false>(jobs, n_jobs, counter, num_sms, ctas_per_sm, st);
+    }
+};
+}  // namespace
+
+void launch_pairs(const PairLaunch& L, const PairArgs& A) {
+    if (A.Q <= 0) return;
+    if (with_label_layout(A.gp, SingleLaunch{L, A})) count_launch();
+}
+
+bool launch_pairs_multi(const PairJob* jobs, int n_jobs, const GridParams& layout, int* counter, int num_sms,
+                        int ctas_per_sm, cudaStream_t st) {
+    if (n_jobs <= 0 || n_jobs > MAX_PAIR_JOBS || layout.top_k > 0) return false;
+    const bool ok = with_label_layout(layout, MultiLaunch{jobs, n_jobs, layout.color != 0, counter, num_sms,
+                                                          ctas_per_sm, st});
     if (ok) count_launch();
+    return ok;
 }
 
 void launch_emit_pairs(const int* unit_start, const int* n_units, int* unit_counter,
                        const uint32_t* qkey, const float4* slots, long long Q, const EdgeDev* edges,
                        int E, const FrameDev* frames, const int* cell_start, const float4* pts4,
-                       GridParams gp, int edge_sel, const int* perm_local, long long capacity,
+                       GridParams gp, int edge_sel, const int* perm_local, long long capacity, int uq,
                        int* i_out, int* j_out, unsigned long long* n_out, int num_sms,
                        cudaStream_t st) {
     if (Q <= 0) return;
+    if (uq < 1 || uq > UQ) uq = UQ;
     k_emit_pairs<<<num_sms * 2, PAIR_T, 0, st>>>(unit_start, n_units, unit_counter, qkey, slots, Q, edges, E,
-                                                 frames, cell_start, pts4, gp, edge_sel, perm_local, capacity,
+                                                 frames, cell_start, pts4, gp, edge_sel, perm_local, capacity, uq,
                                                  i_out, j_out, n_out);
     count_launch();
 }

@@ -2,16 +2,29 @@
 //
 // Two host threads drive the device.  The admission thread takes queued
 // requests while an in-flight slot is free and the device-memory budget has
-// room, builds each problem (upload + grid step) on the slot's stream and
-// hands it to the stepping thread.  The stepping thread advances every
-// admitted problem by a few LM iterations at a time (the loop of
-// rkhsba_solve: solve, evaluate, accept; Sec. V-A, V-C), checks completion
-// with an event per issue, and finishes requests whose LM state says done:
-// poses copied out, context destroyed, slot and memory released, waiting
-// pollers and the admission thread woken.  Problems on different streams run
-// concurrently on the GPU.  Because every evaluation is exact in its
-// reductions (fixed point) and stable in its sorts, a request's result does
-// not depend on which other requests share the GPU.
+// room, builds each problem (upload + grid step + the evaluation at the
+// initial poses) on the slot's stream and hands it to the stepping thread.
+//
+// The stepping thread advances every admitted problem by one LM iteration
+// per round (the loop of rkhsba_solve: solve, evaluate, accept; Sec. V-A,
+// V-C).  In the default batched mode a round is: each problem's damped solve
+// and query binning on its own stream (a replayed CUDA graph), then ONE
+// persistent pair launch over the units of all problems that share a label
+// layout (the sum of Eq. inner_product_actual_ba over every edge of every
+// admitted problem, each problem adding into its own fixed-point
+// accumulators), then each problem's FP64 assembly and accept/reject on its
+// own stream (a second graph).  In the per-request mode each problem runs
+// whole iterations on its own stream, a few per issue.  Requests whose LM
+// state says done are finished after the round: poses copied out, context
+// destroyed, slot and memory released, pollers and the admission thread
+// woken.  Because every evaluation is exact in its reductions (fixed point)
+// and stable in its sorts, a request's result does not depend on which other
+// requests share the GPU, nor on the mode.
+//
+// With autotuning on, the first request of each label layout is timed under
+// the autotuner's candidate settings (rkhsba_autotune) before it is built,
+// and the fastest setting is used for it and every later request of that
+// layout.
 #include "common.cuh"
 #include "rkhsba.h"
 
@@ -48,7 +61,8 @@ struct Req {
     std::atomic<bool> cancel{false};
     rkhsba_ctx* ctx = nullptr;
     int slot = -1;
-    cudaEvent_t ev = nullptr;
+    cudaEvent_t ev = nullptr;        // end of the last issued work
+    cudaEvent_t ev_pre = nullptr;    // end of the round's first half (batched mode)
     bool started = false;
     int issued = 0;
     Clock::time_point t_submit, t_admit, t_done;
@@ -114,8 +128,24 @@ struct rkhsba_server {
     std::thread admit_thr, step_thr;
     int device = 0;
 
+    // batched mode
+    cudaStream_t round_stream = nullptr;
+    cudaEvent_t ev_mid = nullptr;
+    PairJob* d_jobs = nullptr;          // [max_inflight] jobs of the round's batched launches
+    int* d_counters = nullptr;          // [max_inflight] unit counters, one per launch
+    std::vector<PairJob> h_jobs;
+    int num_sms = 1;
+
+    // autotuning: per label layout (sem_pad, bf16, colour) the chosen setting
+    struct Tuned { int key; rkhsba_tuning t; };
+    std::vector<Tuned> tuned;
+    std::mutex tune_mu;
+
     void admit_loop();
     void step_loop();
+    void step_loop_batched();
+    void issue_round(const std::vector<Req*>& batch);
+    bool tuning_for(Req* r, rkhsba_tuning* t);
     void finish(Req* r, int state, int status);   // called without mu held
 };
 
@@ -147,6 +177,10 @@ void rkhsba_server::finish(Req* r, int state, int status) {
     if (r->ev) {
         cudaEventDestroy(r->ev);
         r->ev = nullptr;
+    }
+    if (r->ev_pre) {
+        cudaEventDestroy(r->ev_pre);
+        r->ev_pre = nullptr;
     }
     {
         std::lock_guard<std::mutex> lk(mu);
@@ -203,14 +237,22 @@ void rkhsba_server::admit_loop() {
             r->t_admit = Clock::now();
         }
         rkhsba_ctx* ctx = nullptr;
+        rkhsba_tuning tune{};
+        const bool tuned_ok = cfg.autotune && tuning_for(r, &tune);
+        if (tuned_ok) r->p.cell_scale = tune.cell_scale;
         rkhsba_status s = rkhsba_create(&ctx, r->K, r->n.data(), r->xyz.data(), r->sem.empty() ? nullptr : r->sem.data(),
                                         r->rgb.empty() ? nullptr : r->rgb.data(), r->E, r->edges.data(), &r->p,
                                         (void*)streams[slot]);
+        if (s == RKHSBA_OK && tuned_ok) s = rkhsba_set_tuning(ctx, tune.unit_queries, tune.ctas_per_sm);
         if (s == RKHSBA_OK) s = ctx_begin_solve(ctx, r->poses0.data());
-        cudaEvent_t ev = nullptr;
-        if (s == RKHSBA_OK && cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) s = RKHSBA_ECUDA;
+        cudaEvent_t ev = nullptr, ev_pre = nullptr;
+        if (s == RKHSBA_OK && (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess ||
+                               cudaEventCreateWithFlags(&ev_pre, cudaEventDisableTiming) != cudaSuccess))
+            s = RKHSBA_ECUDA;
         if (s != RKHSBA_OK) {
             r->ctx = ctx;
+            r->ev = ev;
+            r->ev_pre = ev_pre;
             {
                 std::lock_guard<std::mutex> lk(mu);
                 mem_in_use -= std::min(mem_in_use, r->est);
@@ -223,6 +265,7 @@ void rkhsba_server::admit_loop() {
             std::lock_guard<std::mutex> lk(mu);
             r->ctx = ctx;
             r->ev = ev;
+            r->ev_pre = ev_pre;
             const size_t real = ctx_bytes(ctx);
             mem_in_use = mem_in_use - std::min(mem_in_use, r->est) + real;
             r->bytes = real;
@@ -290,6 +333,130 @@ void rkhsba_server::step_loop() {
     }
 }
 
+// Label layout of a request (the template class of its pair kernel).
+static int layout_key(const rkhsba_params& p, bool has_rgb) {
+    const int pad = p.sem_dim > 0 ? (p.sem_dim + 3) / 4 : 0;
+    return pad * 4 + (p.sem_bf16 ? 2 : 0) + ((has_rgb && p.ell_color > 0.0) ? 1 : 0);
+}
+
+bool rkhsba_server::tuning_for(Req* r, rkhsba_tuning* t) {
+    const int key = layout_key(r->p, !r->rgb.empty());
+    {
+        std::lock_guard<std::mutex> lk(tune_mu);
+        for (const Tuned& x : tuned)
+            if (x.key == key) {
+                *t = x.t;
+                return true;
+            }
+    }
+    rkhsba_tuning best{};
+    const rkhsba_status s = rkhsba_autotune(r->K, r->n.data(), r->xyz.data(), r->sem.empty() ? nullptr : r->sem.data(),
+                                            r->rgb.empty() ? nullptr : r->rgb.data(), r->E, r->edges.data(), &r->p, 0,
+                                            r->poses0.data(), (void*)streams[r->slot], 2, &best, nullptr, 0, nullptr);
+    if (s != RKHSBA_OK) return false;
+    std::lock_guard<std::mutex> lk(tune_mu);
+    tuned.push_back({key, best});
+    *t = best;
+    return true;
+}
+
+// One LM iteration of every request in `batch`: first halves on their own
+// streams, one batched pair launch per label layout on the round stream
+// (after every first half of its members), second halves on their own
+// streams after the launches.  Requests with the neighbour-limited variant
+// (its own kernel) run whole iterations on their streams.
+void rkhsba_server::issue_round(const std::vector<Req*>& batch) {
+    struct Group { int key; GridParams layout; int ctas; std::vector<Req*> reqs; };
+    std::vector<Group> groups;
+    for (Req* r : batch) {
+        const GridParams g = ctx_layout(r->ctx);
+        if (g.top_k > 0) {
+            ctx_iterate(r->ctx, 1);
+            cudaEventRecord(r->ev, ctx_stream(r->ctx));
+            continue;
+        }
+        const int key = g.sem_pad * 4 + (g.sem_bf16 ? 2 : 0) + (g.color ? 1 : 0);
+        Group* grp = nullptr;
+        for (Group& x : groups)
+            if (x.key == key && (int)x.reqs.size() < MAX_PAIR_JOBS) grp = &x;
+        if (!grp) {
+            groups.push_back({key, g, ctx_tune_ctas(r->ctx), {}});
+            grp = &groups.back();
+        }
+        grp->reqs.push_back(r);
+    }
+    if (groups.empty()) return;
+    int off = 0, gi = 0;
+    for (Group& grp : groups) {
+        const int n = (int)grp.reqs.size();
+        for (int k = 0; k < n; ++k) {
+            Req* r = grp.reqs[k];
+            ctx_iter_pre(r->ctx);
+            cudaEventRecord(r->ev_pre, ctx_stream(r->ctx));
+            cudaStreamWaitEvent(round_stream, r->ev_pre, 0);
+            h_jobs[off + k] = ctx_pair_job(r->ctx);
+        }
+        cudaMemcpyAsync(d_jobs + off, h_jobs.data() + off, sizeof(PairJob) * n, cudaMemcpyHostToDevice, round_stream);
+        cudaMemsetAsync(d_counters + gi, 0, sizeof(int), round_stream);
+        launch_pairs_multi(d_jobs + off, n, grp.layout, d_counters + gi, num_sms, grp.ctas, round_stream);
+        off += n;
+        ++gi;
+    }
+    cudaEventRecord(ev_mid, round_stream);
+    for (Group& grp : groups)
+        for (Req* r : grp.reqs) {
+            cudaStream_t rs = ctx_stream(r->ctx);
+            cudaStreamWaitEvent(rs, ev_mid, 0);
+            ctx_iter_post(r->ctx);
+            cudaEventRecord(r->ev, rs);
+        }
+}
+
+void rkhsba_server::step_loop_batched() {
+    cudaSetDevice(device);
+    std::vector<Req*> snap, batch;
+    for (;;) {
+        {
+            std::unique_lock<std::mutex> lk(mu);
+            if (stop) return;
+            if (running.empty()) cv_step.wait_for(lk, std::chrono::milliseconds(5));
+            if (stop) return;
+            snap = running;
+        }
+        batch.clear();
+        for (Req* r : snap) {
+            // no work of a request is in flight between rounds
+            if (r->cancel) {
+                finish(r, RQ_CANCELLED, RKHSBA_OK);
+                continue;
+            }
+            if (cfg.request_timeout_ms > 0 && ms_between(r->t_admit, Clock::now()) > cfg.request_timeout_ms) {
+                finish(r, RQ_FAILED, RKHSBA_ETIMEOUT);
+                continue;
+            }
+            batch.push_back(r);
+        }
+        if (batch.empty()) continue;
+        issue_round(batch);
+        for (Req* r : batch) {
+            r->started = true;
+            if (cudaEventSynchronize(r->ev) != cudaSuccess) {
+                finish(r, RQ_FAILED, RKHSBA_ECUDA);
+                continue;
+            }
+            ++r->issued;
+            LMState s{};
+            cudaStream_t rs = ctx_stream(r->ctx);
+            if (cudaMemcpyAsync(&s, ctx_state_dev(r->ctx), sizeof(LMState), cudaMemcpyDeviceToHost, rs) != cudaSuccess ||
+                cudaStreamSynchronize(rs) != cudaSuccess) {
+                finish(r, RQ_FAILED, RKHSBA_ECUDA);
+                continue;
+            }
+            if (s.done || r->issued >= ctx_max_iters(r->ctx)) finish(r, RQ_DONE, RKHSBA_OK);
+        }
+    }
+}
+
 extern "C" {
 
 rkhsba_status rkhsba_server_create(rkhsba_server** out, const rkhsba_server_config* cfg) {
@@ -299,6 +466,12 @@ rkhsba_status rkhsba_server_create(rkhsba_server** out, const rkhsba_server_conf
     if (cfg) s->cfg = *cfg;
     if (s->cfg.max_inflight <= 0) s->cfg.max_inflight = 8;
     if (s->cfg.iters_per_issue <= 0) s->cfg.iters_per_issue = 4;
+    if (s->cfg.max_inflight > 256) s->cfg.max_inflight = 256;
+    if (s->cfg.mode < 0 || s->cfg.mode > 1) {
+        delete s;
+        set_thread_error("rkhsba_server_create: mode must be 0 (batched) or 1 (per request)");
+        return RKHSBA_EINVAL;
+    }
     if (cudaGetDevice(&s->device) != cudaSuccess) {
         delete s;
         set_thread_error("no CUDA device");
@@ -324,8 +497,27 @@ rkhsba_status rkhsba_server_create(rkhsba_server** out, const rkhsba_server_conf
         s->streams.push_back(st);
         s->free_slots.push_back(s->cfg.max_inflight - 1 - i);
     }
+    if (s->cfg.mode == 0) {
+        cudaDeviceGetAttribute(&s->num_sms, cudaDevAttrMultiProcessorCount, s->device);
+        s->h_jobs.assign(s->cfg.max_inflight, PairJob{});
+        if (cudaStreamCreateWithFlags(&s->round_stream, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&s->ev_mid, cudaEventDisableTiming) != cudaSuccess ||
+            cudaMalloc(&s->d_jobs, sizeof(PairJob) * s->cfg.max_inflight) != cudaSuccess ||
+            cudaMalloc(&s->d_counters, sizeof(int) * s->cfg.max_inflight) != cudaSuccess) {
+            cudaGetLastError();
+            for (auto x : s->streams) cudaStreamDestroy(x);
+            if (s->round_stream) cudaStreamDestroy(s->round_stream);
+            if (s->ev_mid) cudaEventDestroy(s->ev_mid);
+            cudaFree(s->d_jobs);
+            cudaFree(s->d_counters);
+            delete s;
+            set_thread_error("batched-mode resources could not be created");
+            return RKHSBA_ECUDA;
+        }
+    }
     s->admit_thr = std::thread([s] { s->admit_loop(); });
-    s->step_thr = std::thread([s] { s->step_loop(); });
+    if (s->cfg.mode == 0) s->step_thr = std::thread([s] { s->step_loop_batched(); });
+    else s->step_thr = std::thread([s] { s->step_loop(); });
     *out = s;
     return RKHSBA_OK;
 }
@@ -350,6 +542,13 @@ void rkhsba_server_destroy(rkhsba_server* s) {
         cudaStreamSynchronize(st);
         cudaStreamDestroy(st);
     }
+    if (s->round_stream) {
+        cudaStreamSynchronize(s->round_stream);
+        cudaStreamDestroy(s->round_stream);
+    }
+    if (s->ev_mid) cudaEventDestroy(s->ev_mid);
+    cudaFree(s->d_jobs);
+    cudaFree(s->d_counters);
     for (auto& kv : s->all) delete kv.second;
     delete s;
 }

@@ -24,7 +24,7 @@ EXPORTS = [
     "rkhsba_profile", "rkhsba_server_create", "rkhsba_server_destroy", "rkhsba_submit",
     "rkhsba_poll", "rkhsba_cancel", "rkhsba_server_stats", "rkhsba_inner_products",
     "rkhsba_rotation_search", "rkhsba_solve_ell_decay", "rkhsba_eval_static",
-    "rkhsba_selftest_lookback_timeout",
+    "rkhsba_selftest_lookback_timeout", "rkhsba_set_tuning", "rkhsba_get_tuning", "rkhsba_autotune",
 ]
 
 
@@ -38,7 +38,8 @@ class Params(C.Structure):
     _fields_ = [("ell", C.c_double), ("cutoff_mult", C.c_double), ("sigma", C.c_double),
                 ("ell_color", C.c_double), ("sem_dim", C.c_int32), ("sem_bf16", C.c_int32),
                 ("max_iters", C.c_int32), ("top_k", C.c_int32), ("lambda0", C.c_double),
-                ("tol_step", C.c_double), ("tol_rel_f", C.c_double), ("sem_min", C.c_double)]
+                ("tol_step", C.c_double), ("tol_rel_f", C.c_double), ("sem_min", C.c_double),
+                ("cell_scale", C.c_double)]
 
 
 class SolveInfo(C.Structure):
@@ -48,7 +49,13 @@ class SolveInfo(C.Structure):
 
 class ServerConfig(C.Structure):
     _fields_ = [("max_inflight", C.c_int32), ("iters_per_issue", C.c_int32),
-                ("memory_budget", C.c_int64), ("request_timeout_ms", C.c_double)]
+                ("memory_budget", C.c_int64), ("request_timeout_ms", C.c_double),
+                ("mode", C.c_int32), ("autotune", C.c_int32)]
+
+
+class Tuning(C.Structure):
+    _fields_ = [("cell_scale", C.c_double), ("unit_queries", C.c_int32), ("ctas_per_sm", C.c_int32),
+                ("ms", C.c_double)]
 
 
 class RequestInfo(C.Structure):
@@ -121,6 +128,10 @@ def load(build_if_missing=True):
         "rkhsba_solve_ell_decay": [vp, P(EllSchedule), P(C.c_double), P(C.c_double), P(C.c_double),
                                    P(EllInfo)],
         "rkhsba_selftest_lookback_timeout": [C.c_int32, P(C.c_int32)],
+        "rkhsba_set_tuning": [vp, C.c_int32, C.c_int32],
+        "rkhsba_get_tuning": [vp, P(Tuning)],
+        "rkhsba_autotune": [C.c_int32, P(C.c_int64), vp, vp, vp, C.c_int32, P(C.c_int32), P(Params), C.c_int32,
+                            P(C.c_double), vp, C.c_int32, P(Tuning), P(Tuning), C.c_int32, P(C.c_int32)],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -146,10 +157,10 @@ def _check(status, ctx=None):
 
 
 def make_params(ell, cutoff_mult=3.0, sigma=1.0, ell_color=0.0, sem_dim=0, sem_bf16=0, max_iters=100,
-                lambda0=1e-4, tol_step=1e-10, tol_rel_f=1e-12, top_k=0, sem_min=0.0):
+                lambda0=1e-4, tol_step=1e-10, tol_rel_f=1e-12, top_k=0, sem_min=0.0, cell_scale=1.0):
     return Params(float(ell), float(cutoff_mult), float(sigma), float(ell_color), int(sem_dim),
                   int(bool(sem_bf16)), int(max_iters), int(top_k), float(lambda0), float(tol_step),
-                  float(tol_rel_f), float(sem_min))
+                  float(tol_rel_f), float(sem_min), float(cell_scale))
 
 
 # ---------------------------------------------------------------- C-ABI ----
@@ -333,6 +344,43 @@ def rkhsba_selftest_lookback_timeout(spin_limit=1000):
     return STATUS_NAMES[st], bool(ok.value)
 
 
+def _tuning_dict(t):
+    return dict(cell_scale=t.cell_scale, unit_queries=t.unit_queries, ctas_per_sm=t.ctas_per_sm, ms=t.ms)
+
+
+def rkhsba_set_tuning(ctx, unit_queries=32, ctas_per_sm=0):
+    _check(load().rkhsba_set_tuning(ctx, int(unit_queries), int(ctas_per_sm)), ctx)
+
+
+def rkhsba_get_tuning(ctx):
+    t = Tuning()
+    _check(load().rkhsba_get_tuning(ctx, C.byref(t)), ctx)
+    return _tuning_dict(t)
+
+
+def rkhsba_autotune(n_points, xyz, sem, rgb, edges, params, poses, stream=None, reps=2, on_device=False):
+    """Time the evaluation under every candidate (cell_scale, unit_queries,
+    ctas_per_sm); returns (best, table) as dicts.  xyz / sem / rgb: flat host
+    arrays (float64 [N,3], float32 [N,D], float32 [N,3] or None), or device
+    pointers (ints) with on_device=True."""
+    lib = load()
+    n = np.ascontiguousarray(n_points, dtype=np.int64)
+    K = len(n)
+    e = np.ascontiguousarray(np.asarray(edges, np.int32).reshape(-1))
+    T = np.ascontiguousarray(poses, dtype=np.float64).reshape(K * 16)
+    if on_device:
+        px, ps, pr = xyz, sem, rgb
+    else:
+        px, ps, pr = (None if a is None else a.ctypes.data for a in (xyz, sem, rgb))
+    best = Tuning()
+    table = (Tuning * 16)()
+    nt = C.c_int32()
+    _check(lib.rkhsba_autotune(K, _ptr(n, C.c_int64), px, ps, pr, len(e) // 2, _ptr(e, C.c_int32),
+                               C.byref(params), int(bool(on_device)), _ptr(T, C.c_double), stream, int(reps),
+                               C.byref(best), table, 16, C.byref(nt)))
+    return _tuning_dict(best), [_tuning_dict(table[i]) for i in range(min(nt.value, 16))]
+
+
 def rkhsba_launch_count():
     return int(load().rkhsba_launch_count())
 
@@ -343,13 +391,13 @@ class Problem:
 
     def __init__(self, xyz, sem=None, rgb=None, edges=None, ell=0.1, cutoff_mult=3.0, sigma=1.0,
                  ell_color=0.0, sem_bf16=False, max_iters=100, lambda0=1e-4, tol_step=1e-10,
-                 tol_rel_f=1e-12, top_k=0, sem_min=0.0, stream=None):
+                 tol_rel_f=1e-12, top_k=0, sem_min=0.0, cell_scale=1.0, stream=None):
         self.K = len(xyz)
         self.edges = np.asarray(edges, np.int32).reshape(-1, 2)
         self.E = len(self.edges)
         sem_dim = 0 if sem is None else int(np.asarray(sem[0]).shape[-1])
         self.params = make_params(ell, cutoff_mult, sigma, ell_color, sem_dim, sem_bf16, max_iters,
-                                  lambda0, tol_step, tol_rel_f, top_k, sem_min)
+                                  lambda0, tol_step, tol_rel_f, top_k, sem_min, cell_scale)
         self.ctx = rkhsba_create(xyz, sem, rgb, self.edges, self.params, stream)
 
     @classmethod
@@ -357,7 +405,7 @@ class Problem:
         p = dict(prob["params"])
         p.update(over)
         keep = {k: p[k] for k in ("ell", "cutoff_mult", "sigma", "ell_color", "sem_bf16", "max_iters",
-                                  "lambda0", "tol_step", "tol_rel_f", "top_k", "sem_min") if k in p}
+                                  "lambda0", "tol_step", "tol_rel_f", "top_k", "sem_min", "cell_scale") if k in p}
         return cls(prob["xyz"], prob.get("sem"), prob.get("rgb"), prob["edges"], **keep)
 
     def eval(self, poses, want_H=True, want_blocks=False):
@@ -380,6 +428,12 @@ class Problem:
 
     def info(self):
         return rkhsba_info(self.ctx)
+
+    def set_tuning(self, unit_queries=32, ctas_per_sm=0):
+        rkhsba_set_tuning(self.ctx, unit_queries, ctas_per_sm)
+
+    def tuning(self):
+        return rkhsba_get_tuning(self.ctx)
 
     def close(self):
         if getattr(self, "ctx", None):
@@ -424,10 +478,13 @@ def rkhsba_eval_static(n_points, d_xyz, d_sem, d_rgb, edges, params, poses, stre
 class Server:
     """Continuous-batching request server (rkhsba_server_* in the C ABI)."""
 
-    def __init__(self, max_inflight=8, iters_per_issue=4, memory_budget=0, request_timeout_ms=0.0):
+    MODES = {"batched": 0, "per_request": 1}
+
+    def __init__(self, max_inflight=8, iters_per_issue=4, memory_budget=0, request_timeout_ms=0.0,
+                 mode="batched", autotune=False):
         lib = load()
         cfg = ServerConfig(int(max_inflight), int(iters_per_issue), int(memory_budget),
-                           float(request_timeout_ms))
+                           float(request_timeout_ms), self.MODES[mode], int(bool(autotune)))
         h = C.c_void_p()
         _check(lib.rkhsba_server_create(C.byref(h), C.byref(cfg)))
         self.h = h.value
@@ -445,7 +502,7 @@ class Server:
                              p.get("ell_color", 0.0), sem_dim, p.get("sem_bf16", 0),
                              p.get("max_iters", 100), p.get("lambda0", 1e-4),
                              p.get("tol_step", 1e-10), p.get("tol_rel_f", 1e-12), p.get("top_k", 0),
-                             p.get("sem_min", 0.0))
+                             p.get("sem_min", 0.0), p.get("cell_scale", 1.0))
         n = np.array([len(x) for x in prob["xyz"]], np.int64)
         xyz = np.ascontiguousarray(np.concatenate([np.asarray(x, np.float64).reshape(-1, 3)
                                                    for x in prob["xyz"]]))
@@ -506,8 +563,9 @@ class Server:
             pass
 
 
-def rkhsba_server_create(max_inflight=8, iters_per_issue=4, memory_budget=0, request_timeout_ms=0.0):
-    return Server(max_inflight, iters_per_issue, memory_budget, request_timeout_ms)
+def rkhsba_server_create(max_inflight=8, iters_per_issue=4, memory_budget=0, request_timeout_ms=0.0,
+                         mode="batched", autotune=False):
+    return Server(max_inflight, iters_per_issue, memory_budget, request_timeout_ms, mode, autotune)
 
 
 def rkhsba_server_destroy(server):

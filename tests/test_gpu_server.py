@@ -37,7 +37,11 @@ def _problems():
     return out
 
 
-def test_results_same_alone_in_mix_and_direct(pk):
+@pytest.mark.parametrize("mode", ["batched", "per_request"])
+def test_results_same_alone_in_mix_and_direct(pk, mode):
+    """Batched mode runs one pair launch over the units of every in-flight
+    request per round; per-request mode runs each request on its own stream.
+    Either way every request's poses equal those of rkhsba_solve bit for bit."""
     probs = _problems()
     direct = []
     for p in probs:
@@ -46,7 +50,7 @@ def test_results_same_alone_in_mix_and_direct(pk):
             direct.append(g.solve(p["poses0"]))
         finally:
             g.close()
-    srv = pk.Server(max_inflight=4)
+    srv = pk.Server(max_inflight=4, mode=mode)
     try:
         alone = []
         for p in probs:
@@ -159,4 +163,37 @@ def test_served_bf16_results_match_the_oracle(pk):
         assert info["iters"] == ref["iters"]
         dr = max(O.pose_error(a, b)[0] for a, b in zip(T, ref["poses"]))
         dt = max(O.pose_error(a, b)[1] for a, b in zip(T, ref["poses"]))
+        assert dr <= 1e-4 and dt <= 1e-4, (dr, dt)
+
+
+def test_batched_rounds_with_autotuning(pk):
+    """With autotuning the first request of a label layout picks the setting
+    (cell size, unit size, CTAs per SM) used for every request of that
+    layout; each served result then equals rkhsba_solve under that setting
+    bit for bit, and the setting keeps the poses within tolerance of the
+    untuned solve."""
+    probs = _problems()[:4]
+    srv = pk.Server(max_inflight=4, autotune=True)
+    try:
+        tickets = [srv.submit(p) for p in probs]
+        res = [srv.poll(t, timeout_ms=-1) for t in tickets]
+    finally:
+        srv.close()
+    from paper_2403_01254_gb300 import rkhsba as rb
+    p0 = probs[0]
+    f = dict(n=np.array([len(x) for x in p0["xyz"]], np.int64),
+             xyz=np.ascontiguousarray(np.concatenate(p0["xyz"])),
+             sem=np.ascontiguousarray(np.concatenate(p0["sem"]).astype(np.float32)))
+    params = pk.make_params(p0["params"]["ell"], sem_dim=p0["sem"][0].shape[1], max_iters=25)
+    best, table = rb.rkhsba_autotune(f["n"], f["xyz"], f["sem"], None, p0["edges"], params, p0["poses0"])
+    assert len(table) == 12 and best["ms"] == min(t["ms"] for t in table)
+    for p, (T, info) in zip(probs, res):
+        assert info["state"] == "finished"
+        g = pk.Problem.from_scene(p)
+        try:
+            T0, _ = g.solve(p["poses0"])
+        finally:
+            g.close()
+        dr = max(np.arccos(np.clip((np.trace(np.linalg.inv(a) @ b) - 2) / 2, -1, 1)) for a, b in zip(T, T0))
+        dt = max(np.linalg.norm((np.linalg.inv(a) @ b)[:3, 3]) for a, b in zip(T, T0))
         assert dr <= 1e-4 and dt <= 1e-4, (dr, dt)

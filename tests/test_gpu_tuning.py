@@ -1,0 +1,104 @@
+"""Pair-kernel tuning knobs and the autotuner.
+
+The knobs (grid cell size, queries per unit, CTAs per SM) change how the pair
+sum is cut into work, never which pairs it holds: under every setting the
+evaluation matches the FP64 oracle within the parity tolerances and the pair
+set is bit-exact outside the cutoff band.  The autotuner times every setting
+on the caller's problem and returns the fastest; applying it reproduces a
+context built with that setting bit for bit.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+import scenes
+
+pytestmark = pytest.mark.gpu
+
+LOSS_TOL, GRAD_TOL, H_TOL = 1e-5, 1e-4, 1e-4
+
+
+@pytest.fixture(scope="module")
+def pk():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2403_01254_gb300 as pk
+    pk.load()
+    return pk
+
+
+def _reln(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(b), 1e-300))
+
+
+@pytest.mark.parametrize("cell_scale", [1.0, 1.25, 1.5, 2.0])
+@pytest.mark.parametrize("uq,ctas", [(32, 0), (16, 1), (7, 0)])
+def test_every_setting_matches_the_oracle(pk, cell_scale, uq, ctas):
+    prob = scenes.lidar_street_problem(seed=71, n_frames=3, n_points=4000, sem_bf16=int(uq == 16))
+    T = prob["poses0"]
+    ref = O.evaluate(prob, T)
+    g = pk.Problem.from_scene(prob, cell_scale=cell_scale)
+    try:
+        g.set_tuning(uq, ctas)
+        assert g.tuning()["unit_queries"] == uq and g.tuning()["cell_scale"] == cell_scale
+        out = g.eval(T, want_H=True, want_blocks=True)
+        T2, info = g.solve(T)
+    finally:
+        g.close()
+    assert np.abs(out["edge_pairs"] - ref["edge_pairs"]).sum() <= 3
+    assert abs(out["loss"] - ref["loss"]) <= LOSS_TOL * abs(ref["loss"])
+    assert _reln(out["grad"], ref["grad"]) <= GRAD_TOL
+    assert _reln(out["H"], ref["H"]) <= H_TOL
+    assert np.all(np.isfinite(T2)) and info["iters"] >= 1
+
+
+def test_pair_set_with_large_cells(pk):
+    prob = scenes.tiny_problem(seed=72, n_frames=2, n=500, extent=1.2, ell=0.12)
+    T = prob["poses0"]
+    g = pk.Problem.from_scene(prob, cell_scale=1.75)
+    try:
+        g.set_tuning(9, 1)
+        gi, gj, n = g.edge_pairs(T, 0)
+    finally:
+        g.close()
+    ri, rj = O.edge_pairs(prob, T, 0)
+    assert set(zip(gi.tolist(), gj.tolist())) == set(zip(ri.tolist(), rj.tolist()))
+
+
+def test_autotune_picks_the_fastest_and_applies(pk):
+    from paper_2403_01254_gb300 import rkhsba as rb
+    prob = scenes.lidar_street_problem(seed=73, n_frames=4, n_points=6000)
+    n = np.array([len(x) for x in prob["xyz"]], np.int64)
+    xyz = np.ascontiguousarray(np.concatenate(prob["xyz"]))
+    sem = np.ascontiguousarray(np.concatenate(prob["sem"]).astype(np.float32))
+    params = pk.make_params(0.3, sem_dim=sem.shape[1])
+    best, table = rb.rkhsba_autotune(n, xyz, sem, None, prob["edges"], params, prob["poses0"], reps=2)
+    assert len(table) == 12
+    assert {t["cell_scale"] for t in table} == {1.0, 1.25, 1.5}
+    assert {t["unit_queries"] for t in table} == {16, 32}
+    assert all(t["ms"] > 0 for t in table)
+    assert best["ms"] == min(t["ms"] for t in table)
+    # the chosen setting, applied two ways, gives the same evaluation bit for bit
+    outs = []
+    for _ in range(2):
+        g = pk.Problem.from_scene(prob, cell_scale=best["cell_scale"])
+        try:
+            g.set_tuning(best["unit_queries"], best["ctas_per_sm"])
+            outs.append(g.eval(prob["poses0"]))
+        finally:
+            g.close()
+    assert outs[0]["loss"] == outs[1]["loss"] and np.array_equal(outs[0]["grad"], outs[1]["grad"])
+
+
+def test_tuning_rejects_bad_values(pk):
+    prob = scenes.tiny_problem(seed=74, n_frames=2, n=50)
+    g = pk.Problem.from_scene(prob)
+    try:
+        for uq, ct in ((0, 0), (33, 0), (8, -1)):
+            with pytest.raises(pk.RkhsbaError):
+                g.set_tuning(uq, ct)
+    finally:
+        g.close()
+    with pytest.raises(pk.RkhsbaError):
+        pk.Problem.from_scene(prob, cell_scale=0.5)
