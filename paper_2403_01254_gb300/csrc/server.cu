@@ -33,6 +33,7 @@
 #include <chrono>
 #include <cmath>
 #include <condition_variable>
+#include <cstring>
 #include <deque>
 #include <mutex>
 #include <string>
@@ -64,6 +65,8 @@ struct Req {
     cudaEvent_t ev = nullptr;        // end of the last issued work
     cudaEvent_t ev_pre = nullptr;    // end of the round's first half (batched mode)
     bool started = false;
+    bool inflight = false;           // batched mode: an issued iteration has not completed
+    LMState* mirror = nullptr;       // batched mode: pinned copy of the LM state after each iteration
     int issued = 0;
     Clock::time_point t_submit, t_admit, t_done;
     rkhsba_solve_info info{};
@@ -128,12 +131,17 @@ struct rkhsba_server {
     std::thread admit_thr, step_thr;
     int device = 0;
 
-    // batched mode
-    cudaStream_t round_stream = nullptr;
-    cudaEvent_t ev_mid = nullptr;
-    PairJob* d_jobs = nullptr;          // [max_inflight] jobs of the round's batched launches
-    int* d_counters = nullptr;          // [max_inflight] unit counters, one per launch
+    // batched mode: rounds go round-robin over a few round streams, each with
+    // its own slice of job records and unit counters, so the batched launch
+    // of one round does not wait for that of another
+    static constexpr int N_ROUND = 4;
+    cudaStream_t round_stream[N_ROUND] = {};
+    cudaEvent_t ev_mid[N_ROUND] = {};
+    PairJob* d_jobs = nullptr;          // [N_ROUND][max_inflight] job records
+    int* d_counters = nullptr;          // [N_ROUND][max_inflight] unit counters
+    LMState* h_mirror = nullptr;        // [max_inflight] pinned LM-state copies, one per slot
     std::vector<PairJob> h_jobs;
+    int next_round = 0;
     int num_sms = 1;
 
     // autotuning: per label layout (sem_pad, bf16, colour) the chosen setting
@@ -261,6 +269,10 @@ void rkhsba_server::admit_loop() {
             finish(r, RQ_FAILED, s);
             continue;
         }
+        if (h_mirror) {
+            r->mirror = h_mirror + slot;
+            r->mirror->done = 0;
+        }
         {
             std::lock_guard<std::mutex> lk(mu);
             r->ctx = ctx;
@@ -360,19 +372,23 @@ bool rkhsba_server::tuning_for(Req* r, rkhsba_tuning* t) {
     return true;
 }
 
-// One LM iteration of every request in `batch`: first halves on their own
-// streams, one batched pair launch per label layout on the round stream
-// (after every first half of its members), second halves on their own
-// streams after the launches.  Requests with the neighbour-limited variant
-// (its own kernel) run whole iterations on their streams.
+// One LM iteration of every request in `batch` (requests whose previous
+// iteration has completed): first halves on their own streams, then on the
+// next round stream one batched pair launch per label layout (after the
+// first halves of its members), then second halves on their own streams
+// after the launches, each followed by a copy of the LM state to the
+// request's pinned mirror.  Requests with the neighbour-limited variant (its
+// own kernel) run whole iterations on their streams.
 void rkhsba_server::issue_round(const std::vector<Req*>& batch) {
     struct Group { int key; GridParams layout; int ctas; std::vector<Req*> reqs; };
     std::vector<Group> groups;
     for (Req* r : batch) {
         const GridParams g = ctx_layout(r->ctx);
         if (g.top_k > 0) {
+            cudaStream_t rs = ctx_stream(r->ctx);
             ctx_iterate(r->ctx, 1);
-            cudaEventRecord(r->ev, ctx_stream(r->ctx));
+            cudaMemcpyAsync(r->mirror, ctx_state_dev(r->ctx), sizeof(LMState), cudaMemcpyDeviceToHost, rs);
+            cudaEventRecord(r->ev, rs);
             continue;
         }
         const int key = g.sem_pad * 4 + (g.sem_bf16 ? 2 : 0) + (g.color ? 1 : 0);
@@ -386,6 +402,11 @@ void rkhsba_server::issue_round(const std::vector<Req*>& batch) {
         grp->reqs.push_back(r);
     }
     if (groups.empty()) return;
+    const int ri = next_round;
+    next_round = (next_round + 1) % N_ROUND;
+    cudaStream_t rst = round_stream[ri];
+    PairJob* jobs = d_jobs + (size_t)ri * cfg.max_inflight;
+    int* counters = d_counters + (size_t)ri * cfg.max_inflight;
     int off = 0, gi = 0;
     for (Group& grp : groups) {
         const int n = (int)grp.reqs.size();
@@ -393,25 +414,32 @@ void rkhsba_server::issue_round(const std::vector<Req*>& batch) {
             Req* r = grp.reqs[k];
             ctx_iter_pre(r->ctx);
             cudaEventRecord(r->ev_pre, ctx_stream(r->ctx));
-            cudaStreamWaitEvent(round_stream, r->ev_pre, 0);
+            cudaStreamWaitEvent(rst, r->ev_pre, 0);
             h_jobs[off + k] = ctx_pair_job(r->ctx);
         }
-        cudaMemcpyAsync(d_jobs + off, h_jobs.data() + off, sizeof(PairJob) * n, cudaMemcpyHostToDevice, round_stream);
-        cudaMemsetAsync(d_counters + gi, 0, sizeof(int), round_stream);
-        launch_pairs_multi(d_jobs + off, n, grp.layout, d_counters + gi, num_sms, grp.ctas, round_stream);
+        cudaMemcpyAsync(jobs + off, h_jobs.data() + off, sizeof(PairJob) * n, cudaMemcpyHostToDevice, rst);
+        cudaMemsetAsync(counters + gi, 0, sizeof(int), rst);
+        launch_pairs_multi(jobs + off, n, grp.layout, counters + gi, num_sms, grp.ctas, rst);
         off += n;
         ++gi;
     }
-    cudaEventRecord(ev_mid, round_stream);
+    cudaEventRecord(ev_mid[ri], rst);
     for (Group& grp : groups)
         for (Req* r : grp.reqs) {
             cudaStream_t rs = ctx_stream(r->ctx);
-            cudaStreamWaitEvent(rs, ev_mid, 0);
+            cudaStreamWaitEvent(rs, ev_mid[ri], 0);
             ctx_iter_post(r->ctx);
+            cudaMemcpyAsync(r->mirror, ctx_state_dev(r->ctx), sizeof(LMState), cudaMemcpyDeviceToHost, rs);
             cudaEventRecord(r->ev, rs);
         }
 }
 
+// Rolling rounds: every pass collects the requests whose last iteration
+// has completed (an event query, no waiting), ends those whose LM state (its
+// pinned mirror) says done or that hit max_iters, applies cancellations and
+// the watchdog, and issues one round over the rest.  Requests that are still
+// running join a later round, so small problems are not held back by large
+// ones, and problems that become ready together share one pair launch.
 void rkhsba_server::step_loop_batched() {
     cudaSetDevice(device);
     std::vector<Req*> snap, batch;
@@ -425,7 +453,20 @@ void rkhsba_server::step_loop_batched() {
         }
         batch.clear();
         for (Req* r : snap) {
-            // no work of a request is in flight between rounds
+            if (r->inflight) {
+                const cudaError_t q = cudaEventQuery(r->ev);
+                if (q == cudaErrorNotReady) continue;
+                r->inflight = false;
+                if (q != cudaSuccess) {
+                    finish(r, RQ_FAILED, RKHSBA_ECUDA);
+                    continue;
+                }
+                ++r->issued;
+                if (r->mirror->done || r->issued >= ctx_max_iters(r->ctx)) {
+                    finish(r, RQ_DONE, RKHSBA_OK);
+                    continue;
+                }
+            }
             if (r->cancel) {
                 finish(r, RQ_CANCELLED, RKHSBA_OK);
                 continue;
@@ -436,23 +477,14 @@ void rkhsba_server::step_loop_batched() {
             }
             batch.push_back(r);
         }
-        if (batch.empty()) continue;
+        if (batch.empty()) {
+            std::this_thread::sleep_for(std::chrono::microseconds(20));
+            continue;
+        }
         issue_round(batch);
         for (Req* r : batch) {
             r->started = true;
-            if (cudaEventSynchronize(r->ev) != cudaSuccess) {
-                finish(r, RQ_FAILED, RKHSBA_ECUDA);
-                continue;
-            }
-            ++r->issued;
-            LMState s{};
-            cudaStream_t rs = ctx_stream(r->ctx);
-            if (cudaMemcpyAsync(&s, ctx_state_dev(r->ctx), sizeof(LMState), cudaMemcpyDeviceToHost, rs) != cudaSuccess ||
-                cudaStreamSynchronize(rs) != cudaSuccess) {
-                finish(r, RQ_FAILED, RKHSBA_ECUDA);
-                continue;
-            }
-            if (s.done || r->issued >= ctx_max_iters(r->ctx)) finish(r, RQ_DONE, RKHSBA_OK);
+            r->inflight = true;
         }
     }
 }
@@ -500,20 +532,28 @@ rkhsba_status rkhsba_server_create(rkhsba_server** out, const rkhsba_server_conf
     if (s->cfg.mode == 0) {
         cudaDeviceGetAttribute(&s->num_sms, cudaDevAttrMultiProcessorCount, s->device);
         s->h_jobs.assign(s->cfg.max_inflight, PairJob{});
-        if (cudaStreamCreateWithFlags(&s->round_stream, cudaStreamNonBlocking) != cudaSuccess ||
-            cudaEventCreateWithFlags(&s->ev_mid, cudaEventDisableTiming) != cudaSuccess ||
-            cudaMalloc(&s->d_jobs, sizeof(PairJob) * s->cfg.max_inflight) != cudaSuccess ||
-            cudaMalloc(&s->d_counters, sizeof(int) * s->cfg.max_inflight) != cudaSuccess) {
+        bool ok = true;
+        for (int i = 0; i < rkhsba_server::N_ROUND && ok; ++i)
+            ok = cudaStreamCreateWithFlags(&s->round_stream[i], cudaStreamNonBlocking) == cudaSuccess &&
+                 cudaEventCreateWithFlags(&s->ev_mid[i], cudaEventDisableTiming) == cudaSuccess;
+        ok = ok && cudaMalloc(&s->d_jobs, sizeof(PairJob) * s->cfg.max_inflight * rkhsba_server::N_ROUND) == cudaSuccess &&
+             cudaMalloc(&s->d_counters, sizeof(int) * s->cfg.max_inflight * rkhsba_server::N_ROUND) == cudaSuccess &&
+             cudaMallocHost(&s->h_mirror, sizeof(LMState) * s->cfg.max_inflight) == cudaSuccess;
+        if (!ok) {
             cudaGetLastError();
             for (auto x : s->streams) cudaStreamDestroy(x);
-            if (s->round_stream) cudaStreamDestroy(s->round_stream);
-            if (s->ev_mid) cudaEventDestroy(s->ev_mid);
+            for (int i = 0; i < rkhsba_server::N_ROUND; ++i) {
+                if (s->round_stream[i]) cudaStreamDestroy(s->round_stream[i]);
+                if (s->ev_mid[i]) cudaEventDestroy(s->ev_mid[i]);
+            }
             cudaFree(s->d_jobs);
             cudaFree(s->d_counters);
+            if (s->h_mirror) cudaFreeHost(s->h_mirror);
             delete s;
             set_thread_error("batched-mode resources could not be created");
             return RKHSBA_ECUDA;
         }
+        std::memset(s->h_mirror, 0, sizeof(LMState) * s->cfg.max_inflight);
     }
     s->admit_thr = std::thread([s] { s->admit_loop(); });
     if (s->cfg.mode == 0) s->step_thr = std::thread([s] { s->step_loop_batched(); });
@@ -542,13 +582,16 @@ void rkhsba_server_destroy(rkhsba_server* s) {
         cudaStreamSynchronize(st);
         cudaStreamDestroy(st);
     }
-    if (s->round_stream) {
-        cudaStreamSynchronize(s->round_stream);
-        cudaStreamDestroy(s->round_stream);
+    for (int i = 0; i < rkhsba_server::N_ROUND; ++i) {
+        if (s->round_stream[i]) {
+            cudaStreamSynchronize(s->round_stream[i]);
+            cudaStreamDestroy(s->round_stream[i]);
+        }
+        if (s->ev_mid[i]) cudaEventDestroy(s->ev_mid[i]);
     }
-    if (s->ev_mid) cudaEventDestroy(s->ev_mid);
     cudaFree(s->d_jobs);
     cudaFree(s->d_counters);
+    if (s->h_mirror) cudaFreeHost(s->h_mirror);
     for (auto& kv : s->all) delete kv.second;
     delete s;
 }
