@@ -131,17 +131,21 @@ struct rkhsba_server {
     std::thread admit_thr, step_thr;
     int device = 0;
 
-    // batched mode: rounds go round-robin over a few round streams, each with
-    // its own slice of job records and unit counters, so the batched launch
-    // of one round does not wait for that of another
-    static constexpr int N_ROUND = 4;
-    cudaStream_t round_stream[N_ROUND] = {};
-    cudaEvent_t ev_mid[N_ROUND] = {};
-    PairJob* d_jobs = nullptr;          // [N_ROUND][max_inflight] job records
-    int* d_counters = nullptr;          // [N_ROUND][max_inflight] unit counters
-    LMState* h_mirror = nullptr;        // [max_inflight] pinned LM-state copies, one per slot
-    std::vector<PairJob> h_jobs;
-    int next_round = 0;
+    // batched mode: each round takes a free round slot -- a stream, pinned
+    // host and device job records, unit counters and an event marking the
+    // end of its batched launches -- so the launches of different rounds do
+    // not wait for each other and no copy waits on the host.  A round holds
+    // at least one request and a request is in at most one pending round, so
+    // max_inflight + 1 slots always leave one free.
+    struct RoundSlot {
+        cudaStream_t stream = nullptr;
+        cudaEvent_t ev_mid = nullptr;
+        PairJob* h_jobs = nullptr;      // pinned [max_inflight]
+        PairJob* d_jobs = nullptr;      // [max_inflight]
+        int* d_counters = nullptr;      // [max_inflight]
+    };
+    std::vector<RoundSlot> rounds;
+    LMState* h_mirror = nullptr;        // [max_inflight] pinned LM-state copies, one per request slot
     int num_sms = 1;
 
     // autotuning: per label layout (sem_pad, bf16, colour) the chosen setting
@@ -149,6 +153,21 @@ struct rkhsba_server {
     std::vector<Tuned> tuned;
     std::mutex tune_mu;
 
+    void release_rounds() {
+        for (auto& x : rounds) {
+            if (x.stream) {
+                cudaStreamSynchronize(x.stream);
+                cudaStreamDestroy(x.stream);
+            }
+            if (x.ev_mid) cudaEventDestroy(x.ev_mid);
+            if (x.h_jobs) cudaFreeHost(x.h_jobs);
+            cudaFree(x.d_jobs);
+            cudaFree(x.d_counters);
+        }
+        rounds.clear();
+        if (h_mirror) cudaFreeHost(h_mirror);
+        h_mirror = nullptr;
+    }
     void admit_loop();
     void step_loop();
     void step_loop_batched();
@@ -402,11 +421,20 @@ void rkhsba_server::issue_round(const std::vector<Req*>& batch) {
         grp->reqs.push_back(r);
     }
     if (groups.empty()) return;
-    const int ri = next_round;
-    next_round = (next_round + 1) % N_ROUND;
-    cudaStream_t rst = round_stream[ri];
-    PairJob* jobs = d_jobs + (size_t)ri * cfg.max_inflight;
-    int* counters = d_counters + (size_t)ri * cfg.max_inflight;
+    RoundSlot* rs_free = nullptr;
+    for (RoundSlot& x : rounds)
+        if (cudaEventQuery(x.ev_mid) == cudaSuccess) {
+            rs_free = &x;
+            break;
+        }
+    if (!rs_free) {                      // not reached (see RoundSlot); wait for the first slot
+        cudaEventSynchronize(rounds[0].ev_mid);
+        rs_free = &rounds[0];
+    }
+    cudaStream_t rst = rs_free->stream;
+    PairJob* jobs = rs_free->d_jobs;
+    PairJob* hjobs = rs_free->h_jobs;
+    int* counters = rs_free->d_counters;
     int off = 0, gi = 0;
     for (Group& grp : groups) {
         const int n = (int)grp.reqs.size();
@@ -415,19 +443,19 @@ void rkhsba_server::issue_round(const std::vector<Req*>& batch) {
             ctx_iter_pre(r->ctx);
             cudaEventRecord(r->ev_pre, ctx_stream(r->ctx));
             cudaStreamWaitEvent(rst, r->ev_pre, 0);
-            h_jobs[off + k] = ctx_pair_job(r->ctx);
+            hjobs[off + k] = ctx_pair_job(r->ctx);
         }
-        cudaMemcpyAsync(jobs + off, h_jobs.data() + off, sizeof(PairJob) * n, cudaMemcpyHostToDevice, rst);
+        cudaMemcpyAsync(jobs + off, hjobs + off, sizeof(PairJob) * n, cudaMemcpyHostToDevice, rst);
         cudaMemsetAsync(counters + gi, 0, sizeof(int), rst);
         launch_pairs_multi(jobs + off, n, grp.layout, counters + gi, num_sms, grp.ctas, rst);
         off += n;
         ++gi;
     }
-    cudaEventRecord(ev_mid[ri], rst);
+    cudaEventRecord(rs_free->ev_mid, rst);
     for (Group& grp : groups)
         for (Req* r : grp.reqs) {
             cudaStream_t rs = ctx_stream(r->ctx);
-            cudaStreamWaitEvent(rs, ev_mid[ri], 0);
+            cudaStreamWaitEvent(rs, rs_free->ev_mid, 0);
             ctx_iter_post(r->ctx);
             cudaMemcpyAsync(r->mirror, ctx_state_dev(r->ctx), sizeof(LMState), cudaMemcpyDeviceToHost, rs);
             cudaEventRecord(r->ev, rs);
@@ -531,29 +559,25 @@ rkhsba_status rkhsba_server_create(rkhsba_server** out, const rkhsba_server_conf
     }
     if (s->cfg.mode == 0) {
         cudaDeviceGetAttribute(&s->num_sms, cudaDevAttrMultiProcessorCount, s->device);
-        s->h_jobs.assign(s->cfg.max_inflight, PairJob{});
-        bool ok = true;
-        for (int i = 0; i < rkhsba_server::N_ROUND && ok; ++i)
-            ok = cudaStreamCreateWithFlags(&s->round_stream[i], cudaStreamNonBlocking) == cudaSuccess &&
-                 cudaEventCreateWithFlags(&s->ev_mid[i], cudaEventDisableTiming) == cudaSuccess;
-        ok = ok && cudaMalloc(&s->d_jobs, sizeof(PairJob) * s->cfg.max_inflight * rkhsba_server::N_ROUND) == cudaSuccess &&
-             cudaMalloc(&s->d_counters, sizeof(int) * s->cfg.max_inflight * rkhsba_server::N_ROUND) == cudaSuccess &&
-             cudaMallocHost(&s->h_mirror, sizeof(LMState) * s->cfg.max_inflight) == cudaSuccess;
+        const int n = s->cfg.max_inflight;
+        s->rounds.resize(n + 1);
+        bool ok = cudaMallocHost(&s->h_mirror, sizeof(LMState) * n) == cudaSuccess;
+        for (auto& x : s->rounds) {
+            ok = ok && cudaStreamCreateWithFlags(&x.stream, cudaStreamNonBlocking) == cudaSuccess &&
+                 cudaEventCreateWithFlags(&x.ev_mid, cudaEventDisableTiming) == cudaSuccess &&
+                 cudaMallocHost(&x.h_jobs, sizeof(PairJob) * n) == cudaSuccess &&
+                 cudaMalloc(&x.d_jobs, sizeof(PairJob) * n) == cudaSuccess &&
+                 cudaMalloc(&x.d_counters, sizeof(int) * n) == cudaSuccess;
+        }
         if (!ok) {
             cudaGetLastError();
             for (auto x : s->streams) cudaStreamDestroy(x);
-            for (int i = 0; i < rkhsba_server::N_ROUND; ++i) {
-                if (s->round_stream[i]) cudaStreamDestroy(s->round_stream[i]);
-                if (s->ev_mid[i]) cudaEventDestroy(s->ev_mid[i]);
-            }
-            cudaFree(s->d_jobs);
-            cudaFree(s->d_counters);
-            if (s->h_mirror) cudaFreeHost(s->h_mirror);
+            s->release_rounds();
             delete s;
             set_thread_error("batched-mode resources could not be created");
             return RKHSBA_ECUDA;
         }
-        std::memset(s->h_mirror, 0, sizeof(LMState) * s->cfg.max_inflight);
+        std::memset(s->h_mirror, 0, sizeof(LMState) * n);
     }
     s->admit_thr = std::thread([s] { s->admit_loop(); });
     if (s->cfg.mode == 0) s->step_thr = std::thread([s] { s->step_loop_batched(); });
@@ -582,16 +606,7 @@ void rkhsba_server_destroy(rkhsba_server* s) {
         cudaStreamSynchronize(st);
         cudaStreamDestroy(st);
     }
-    for (int i = 0; i < rkhsba_server::N_ROUND; ++i) {
-        if (s->round_stream[i]) {
-            cudaStreamSynchronize(s->round_stream[i]);
-            cudaStreamDestroy(s->round_stream[i]);
-        }
-        if (s->ev_mid[i]) cudaEventDestroy(s->ev_mid[i]);
-    }
-    cudaFree(s->d_jobs);
-    cudaFree(s->d_counters);
-    if (s->h_mirror) cudaFreeHost(s->h_mirror);
+    s->release_rounds();
     for (auto& kv : s->all) delete kv.second;
     delete s;
 }
