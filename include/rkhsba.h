@@ -360,13 +360,15 @@ rkhsba_status rkhsba_get_tuning(const rkhsba_ctx* ctx, rkhsba_tuning* out);
 
 /*
  * rkhsba_autotune -- time the evaluation of one problem under every
- * candidate setting (cell_scale 1, 1.25, 1.5 x unit_queries 16, 32 x
- * ctas_per_sm 1, all) and report the fastest.  For each cell size a
- * temporary context is built from the inputs (arguments as for
- * rkhsba_create, or as for rkhsba_create_device when inputs_on_device is 1);
- * each setting is run once untimed, then `reps` (1..100) evaluations at
- * `poses` ([K*16] HOST) are timed with CUDA events on cuda_stream.
- *   best      HOST out: the fastest setting and its mean time (ms)
+ * candidate setting (cell_scale 1, 1.25, 1.5 x unit_queries 32, 16 x
+ * ctas_per_sm all, 1; the default setting first) and report the fastest.
+ * For each cell size a temporary context is built from the inputs
+ * (arguments as for rkhsba_create, or as for rkhsba_create_device when
+ * inputs_on_device is 1); each setting is run once untimed, then at least
+ * `reps` (1..100) evaluations at `poses` ([K*16] HOST), and at least 20 ms of
+ * them, are timed with CUDA events on cuda_stream.  The default setting is
+ * kept unless another is faster by more than 3%.
+ *   best      HOST out: the chosen setting and its mean time (ms)
  *   table     HOST out [table_cap] (may be NULL when table_cap is 0): every
  *             setting tried, in order; *n_table receives the count (12)
  * Creating a context with params.cell_scale = best.cell_scale and calling

@@ -63,7 +63,6 @@ struct Req {
     rkhsba_ctx* ctx = nullptr;
     int slot = -1;
     cudaEvent_t ev = nullptr;        // end of the last issued work
-    cudaEvent_t ev_pre = nullptr;    // end of the round's first half (batched mode)
     bool started = false;
     bool inflight = false;           // batched mode: an issued iteration has not completed
     LMState* mirror = nullptr;       // batched mode: pinned copy of the LM state after each iteration
@@ -205,10 +204,6 @@ void rkhsba_server::finish(Req* r, int state, int status) {
         cudaEventDestroy(r->ev);
         r->ev = nullptr;
     }
-    if (r->ev_pre) {
-        cudaEventDestroy(r->ev_pre);
-        r->ev_pre = nullptr;
-    }
     {
         std::lock_guard<std::mutex> lk(mu);
         if (r->slot >= 0) free_slots.push_back(r->slot);
@@ -272,14 +267,11 @@ void rkhsba_server::admit_loop() {
                                         (void*)streams[slot]);
         if (s == RKHSBA_OK && tuned_ok) s = rkhsba_set_tuning(ctx, tune.unit_queries, tune.ctas_per_sm);
         if (s == RKHSBA_OK) s = ctx_begin_solve(ctx, r->poses0.data());
-        cudaEvent_t ev = nullptr, ev_pre = nullptr;
-        if (s == RKHSBA_OK && (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess ||
-                               cudaEventCreateWithFlags(&ev_pre, cudaEventDisableTiming) != cudaSuccess))
-            s = RKHSBA_ECUDA;
+        cudaEvent_t ev = nullptr;
+        if (s == RKHSBA_OK && cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) s = RKHSBA_ECUDA;
         if (s != RKHSBA_OK) {
             r->ctx = ctx;
             r->ev = ev;
-            r->ev_pre = ev_pre;
             {
                 std::lock_guard<std::mutex> lk(mu);
                 mem_in_use -= std::min(mem_in_use, r->est);
@@ -296,7 +288,6 @@ void rkhsba_server::admit_loop() {
             std::lock_guard<std::mutex> lk(mu);
             r->ctx = ctx;
             r->ev = ev;
-            r->ev_pre = ev_pre;
             const size_t real = ctx_bytes(ctx);
             mem_in_use = mem_in_use - std::min(mem_in_use, r->est) + real;
             r->bytes = real;
@@ -391,13 +382,15 @@ bool rkhsba_server::tuning_for(Req* r, rkhsba_tuning* t) {
     return true;
 }
 
-// One LM iteration of every request in `batch` (requests whose previous
-// iteration has completed): first halves on their own streams, then on the
-// next round stream one batched pair launch per label layout (after the
-// first halves of its members), then second halves on their own streams
-// after the launches, each followed by a copy of the LM state to the
-// request's pinned mirror.  Requests with the neighbour-limited variant (its
-// own kernel) run whole iterations on their streams.
+// The rest of one LM iteration of every request in `batch` (requests whose
+// first half -- damped solve and query binning -- has completed; r->ev marks
+// its end): on a free round slot one batched pair launch per label layout,
+// then on each request's stream the second half (assembly, accept/reject),
+// a copy of the LM state to the request's pinned mirror, and at once the
+// first half of the next iteration, so that it runs while the host notices
+// the end of this one (a finished solve makes it a no-op).  Requests with the
+// neighbour-limited variant (its own kernel) run whole iterations on their
+// streams.
 void rkhsba_server::issue_round(const std::vector<Req*>& batch) {
     struct Group { int key; GridParams layout; int ctas; std::vector<Req*> reqs; };
     std::vector<Group> groups;
@@ -440,9 +433,7 @@ void rkhsba_server::issue_round(const std::vector<Req*>& batch) {
         const int n = (int)grp.reqs.size();
         for (int k = 0; k < n; ++k) {
             Req* r = grp.reqs[k];
-            ctx_iter_pre(r->ctx);
-            cudaEventRecord(r->ev_pre, ctx_stream(r->ctx));
-            cudaStreamWaitEvent(rst, r->ev_pre, 0);
+            cudaStreamWaitEvent(rst, r->ev, 0);
             hjobs[off + k] = ctx_pair_job(r->ctx);
         }
         cudaMemcpyAsync(jobs + off, hjobs + off, sizeof(PairJob) * n, cudaMemcpyHostToDevice, rst);
@@ -458,16 +449,19 @@ void rkhsba_server::issue_round(const std::vector<Req*>& batch) {
             cudaStreamWaitEvent(rs, rs_free->ev_mid, 0);
             ctx_iter_post(r->ctx);
             cudaMemcpyAsync(r->mirror, ctx_state_dev(r->ctx), sizeof(LMState), cudaMemcpyDeviceToHost, rs);
+            ctx_iter_pre(r->ctx);
             cudaEventRecord(r->ev, rs);
         }
 }
 
-// Rolling rounds: every pass collects the requests whose last iteration
-// has completed (an event query, no waiting), ends those whose LM state (its
-// pinned mirror) says done or that hit max_iters, applies cancellations and
-// the watchdog, and issues one round over the rest.  Requests that are still
-// running join a later round, so small problems are not held back by large
-// ones, and problems that become ready together share one pair launch.
+// Rolling rounds: every pass collects the requests whose issued work has
+// completed (an event query, no waiting), ends those whose LM state (its
+// pinned mirror, copied after the second half) says done or that reached
+// max_iters, applies cancellations and the watchdog, and issues one round
+// over the rest.  A newly admitted request first gets the first half of its
+// first iteration.  Requests that are still running join a later round, so
+// small problems are not held back by large ones, and problems that become
+// ready together share one pair launch.
 void rkhsba_server::step_loop_batched() {
     cudaSetDevice(device);
     std::vector<Req*> snap, batch;
@@ -489,8 +483,7 @@ void rkhsba_server::step_loop_batched() {
                     finish(r, RQ_FAILED, RKHSBA_ECUDA);
                     continue;
                 }
-                ++r->issued;
-                if (r->mirror->done || r->issued >= ctx_max_iters(r->ctx)) {
+                if (r->issued > 0 && (r->mirror->done || r->issued >= ctx_max_iters(r->ctx))) {
                     finish(r, RQ_DONE, RKHSBA_OK);
                     continue;
                 }
@@ -503,6 +496,17 @@ void rkhsba_server::step_loop_batched() {
                 finish(r, RQ_FAILED, RKHSBA_ETIMEOUT);
                 continue;
             }
+            if (!r->started) {
+                r->started = true;
+                r->inflight = true;
+                if (ctx_layout(r->ctx).top_k == 0) {
+                    ctx_iter_pre(r->ctx);
+                    cudaEventRecord(r->ev, ctx_stream(r->ctx));
+                } else {
+                    cudaEventRecord(r->ev, ctx_stream(r->ctx));
+                }
+                continue;
+            }
             batch.push_back(r);
         }
         if (batch.empty()) {
@@ -511,8 +515,8 @@ void rkhsba_server::step_loop_batched() {
         }
         issue_round(batch);
         for (Req* r : batch) {
-            r->started = true;
             r->inflight = true;
+            ++r->issued;
         }
     }
 }

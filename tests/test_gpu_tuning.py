@@ -4,8 +4,9 @@ The knobs (grid cell size, queries per unit, CTAs per SM) change how the pair
 sum is cut into work, never which pairs it holds: under every setting the
 evaluation matches the FP64 oracle within the parity tolerances and the pair
 set is bit-exact outside the cutoff band.  The autotuner times every setting
-on the caller's problem and returns the fastest; applying it reproduces a
-context built with that setting bit for bit.
+on the caller's problem and returns the fastest (keeping the default unless
+another is more than 3% faster); applying it reproduces a context built with
+that setting bit for bit.
 """
 import numpy as np
 import pytest
@@ -78,7 +79,11 @@ def test_autotune_picks_the_fastest_and_applies(pk):
     assert {t["cell_scale"] for t in table} == {1.0, 1.25, 1.5}
     assert {t["unit_queries"] for t in table} == {16, 32}
     assert all(t["ms"] > 0 for t in table)
-    assert best["ms"] == min(t["ms"] for t in table)
+    fastest = min(t["ms"] for t in table)
+    default = table[0]
+    assert (default["cell_scale"], default["unit_queries"], default["ctas_per_sm"]) == (1.0, 32, 0)
+    # the fastest setting, unless the default is within 3% of it
+    assert best["ms"] == fastest or (best == default and fastest >= 0.97 * default["ms"])
     # the chosen setting, applied two ways, gives the same evaluation bit for bit
     outs = []
     for _ in range(2):
