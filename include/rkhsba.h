@@ -419,9 +419,11 @@ typedef struct {
                                   persistent pair launch over the units of all of
                                   them that share a label layout; 1: per-request
                                   streams, iters_per_issue whole iterations per issue */
-    int32_t autotune;          /* 1: the first request of each label layout is timed
-                                  under the autotuner's settings (rkhsba_autotune) and
-                                  the fastest is used for it and later ones; 0: off */
+    int32_t autotune;          /* 1: the first request of each workload class (label
+                                  layout; mean points per frame < 16k, < 64k, more) is
+                                  timed under the autotuner's settings (rkhsba_autotune)
+                                  and the chosen one is used for it and later ones of
+                                  that class; 0: off */
 } rkhsba_server_config;
 
 typedef struct {

@@ -21,10 +21,10 @@
 // and stable in its sorts, a request's result does not depend on which other
 // requests share the GPU, nor on the mode.
 //
-// With autotuning on, the first request of each label layout is timed under
-// the autotuner's candidate settings (rkhsba_autotune) before it is built,
-// and the fastest setting is used for it and every later request of that
-// layout.
+// With autotuning on, the first request of each workload class (label layout
+// and density class) is timed under the autotuner's candidate settings
+// (rkhsba_autotune) before it is built, and the chosen setting is used for it
+// and every later request of that class.
 #include "common.cuh"
 #include "rkhsba.h"
 
@@ -147,7 +147,7 @@ struct rkhsba_server {
     LMState* h_mirror = nullptr;        // [max_inflight] pinned LM-state copies, one per request slot
     int num_sms = 1;
 
-    // autotuning: per label layout (sem_pad, bf16, colour) the chosen setting
+    // autotuning: per workload class (label layout, density class) the chosen setting
     struct Tuned { int key; rkhsba_tuning t; };
     std::vector<Tuned> tuned;
     std::mutex tune_mu;
@@ -355,14 +355,23 @@ void rkhsba_server::step_loop() {
     }
 }
 
-// Label layout of a request (the template class of its pair kernel).
-static int layout_key(const rkhsba_params& p, bool has_rgb) {
+// Workload class of a request for autotuning: its label layout (the
+// template class of its pair kernel) and its density class (mean points per
+// frame below 16k, below 64k, or more), since the best setting of a small
+// problem is not that of a large one.
+static int workload_class(const Req& r) {
+    const rkhsba_params& p = r.p;
     const int pad = p.sem_dim > 0 ? (p.sem_dim + 3) / 4 : 0;
-    return pad * 4 + (p.sem_bf16 ? 2 : 0) + ((has_rgb && p.ell_color > 0.0) ? 1 : 0);
+    const int layout = pad * 4 + (p.sem_bf16 ? 2 : 0) + ((!r.rgb.empty() && p.ell_color > 0.0) ? 1 : 0);
+    long long n = 0;
+    for (int64_t x : r.n) n += x;
+    const double per_frame = (double)n / (r.K > 0 ? r.K : 1);
+    const int size = per_frame < 16384.0 ? 0 : (per_frame < 65536.0 ? 1 : 2);
+    return layout * 4 + size;
 }
 
 bool rkhsba_server::tuning_for(Req* r, rkhsba_tuning* t) {
-    const int key = layout_key(r->p, !r->rgb.empty());
+    const int key = workload_class(*r);
     {
         std::lock_guard<std::mutex> lk(tune_mu);
         for (const Tuned& x : tuned)
