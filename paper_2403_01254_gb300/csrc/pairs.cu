@@ -448,6 +448,21 @@ __device__ __forceinline__ int stream_point(const Rows& R, int v, int& dx, int& 
     return i;
 }
 
+// The same with the row prefix held in registers (pre[0] = 0).
+__device__ __forceinline__ int stream_point_r(const Rows& R, const int (&pre)[9], int v, int& dx, int& dy, int& dz) {
+    int r = 0;
+#pragma unroll
+    for (int k = 1; k < 9; ++k) r += (pre[k] <= v) ? 1 : 0;
+    int base = pre[0];
+#pragma unroll
+    for (int k = 1; k < 9; ++k) base = (r == k) ? pre[k] : base;
+    const int i = R.rb[r] + (v - base);
+    dx = (i >= R.b1[r]) + (i >= R.b2[r]) - 1;
+    dy = (r % 3) - 1;
+    dz = (r / 3) - 1;
+    return i;
+}
+
 // Unit header shared by the pair and the pair-list kernels: home cell of the
 // unit starting at sorted query k0, and the number of its queries (<= UQ).
 __device__ __forceinline__ int unit_queries(const uint32_t* __restrict__ qkey, long long Q, int k0,
@@ -533,13 +548,40 @@ __device__ __forceinline__ void mma_bf16_16816(float (&d)[4], const unsigned (&a
                  : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
+// Query-side (B) fragments of the Gram MMAs: lane (g, t4) holds words
+// 8 ks + t4 and 8 ks + t4 + 4 of query row 8 nt + g; the unit's queries do
+// not change from batch to batch, so they are loaded once per unit.
 template <int DP>
-__device__ __forceinline__ void label_gram_bf16(const unsigned* __restrict__ semw, const float* ssq, int cand_i,
+struct GramB {
+    static constexpr int KS = (DP + 15) / 16;   // k16 steps; words beyond DP are zero
+    unsigned b[4][KS][2];
+    __device__ __forceinline__ void load(const float* ssq, int lane) {
+        constexpr int RW = DP / 2;
+        const int g = lane >> 2, t4 = lane & 3;
+        const unsigned* qw = reinterpret_cast<const unsigned*>(ssq);
+#pragma unroll
+        for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+            for (int ks = 0; ks < KS; ++ks) {
+                const unsigned* qrow = qw + (8 * nt + g) * RW;
+                const int w0 = 8 * ks + t4, w1 = w0 + 4;
+                b[nt][ks][0] = (w0 < RW) ? qrow[w0] : 0u;
+                b[nt][ks][1] = (w1 < RW) ? qrow[w1] : 0u;
+            }
+    }
+};
+
+// Column of candidate c in row q of the Gram tile: XOR-swizzled by q so that
+// the MMA fragment stores (four query rows of one candidate per instruction)
+// hit 32 different banks.
+__device__ __forceinline__ int gram_col(int q, int c) { return c ^ (((q >> 1) & 3) << 3); }
+
+template <int DP>
+__device__ __forceinline__ void label_gram_bf16(const unsigned* __restrict__ semw, const GramB<DP>& B, int cand_i,
                                                 unsigned has_mask, int lane, float* G) {
-    constexpr int KS = (DP + 15) / 16;   // k16 steps; words beyond DP are zero
+    constexpr int KS = GramB<DP>::KS;
     constexpr int RW = DP / 2;           // 32-bit words per label row
     const int g = lane >> 2, t4 = lane & 3;
-    const unsigned* qw = reinterpret_cast<const unsigned*>(ssq);
     float acc[2][4][4];
 #pragma unroll
     for (int mt = 0; mt < 2; ++mt)
@@ -563,12 +605,7 @@ __device__ __forceinline__ void label_gram_bf16(const unsigned* __restrict__ sem
             a[2] = (v0 && w1 < RW) ? __ldg(row0 + w1) : 0u;
             a[3] = (v1 && w1 < RW) ? __ldg(row1 + w1) : 0u;
 #pragma unroll
-            for (int nt = 0; nt < 4; ++nt) {
-                const unsigned* qrow = qw + (8 * nt + g) * RW;
-                const unsigned b0 = (w0 < RW) ? qrow[w0] : 0u;
-                const unsigned b1 = (w1 < RW) ? qrow[w1] : 0u;
-                mma_bf16_16816(acc[mt][nt], a, b0, b1);
-            }
+            for (int nt = 0; nt < 4; ++nt) mma_bf16_16816(acc[mt][nt], a, B.b[nt][ks][0], B.b[nt][ks][1]);
         }
     }
 #pragma unroll
@@ -576,10 +613,10 @@ __device__ __forceinline__ void label_gram_bf16(const unsigned* __restrict__ sem
 #pragma unroll
         for (int nt = 0; nt < 4; ++nt) {
             const int c = 16 * mt + g, q = 8 * nt + 2 * t4;      // candidate row, query column
-            G[q * GRAM_LD + c] = acc[mt][nt][0];
-            G[(q + 1) * GRAM_LD + c] = acc[mt][nt][1];
-            G[q * GRAM_LD + c + 8] = acc[mt][nt][2];
-            G[(q + 1) * GRAM_LD + c + 8] = acc[mt][nt][3];
+            G[q * GRAM_LD + gram_col(q, c)] = acc[mt][nt][0];
+            G[(q + 1) * GRAM_LD + gram_col(q + 1, c)] = acc[mt][nt][1];
+            G[q * GRAM_LD + gram_col(q, c + 8)] = acc[mt][nt][2];
+            G[(q + 1) * GRAM_LD + gram_col(q + 1, c + 8)] = acc[mt][nt][3];
         }
 }
 
@@ -664,11 +701,28 @@ __device__ __forceinline__ void pair_unit(const PairArgs& A, int k0, float* wb, 
     // a candidate farther than r_c from the query box pairs with none of
     // the queries; the margin keeps every candidate the exact test passes
     const float box_thr = gp.rc2 * 1.0001f;
+    // BF16 labels: the Gram path leaves registers free, so the stencil row
+    // prefix, the query-side MMA fragments and the per-lane unit sums live
+    // in registers instead of shared memory
+    constexpr bool REG = BF16 && DP > 0;
+    int pre[9];
+    if constexpr (REG) {
+#pragma unroll
+        for (int k = 0; k < 9; ++k) pre[k] = R.pre[k];
+    }
+    GramB<(BF16 && DP > 0) ? DP : 16> gb;
+    if constexpr (REG) gb.load(ssq, lane);
 
     // per lane, over its candidates x with sums w0 = sum w, dc = sum w d,
     // qc = sum w d d^T: W, D, Q and sum w0 x, sum w0 x x^T, sum x dc^T
+    float racc[REG ? N_ACC : 1];
+    if constexpr (REG) {
 #pragma unroll
-    for (int k = 0; k < N_ACC / 4; ++k) sacc[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int k = 0; k < N_ACC; ++k) racc[k] = 0.f;
+    } else {
+#pragma unroll
+        for (int k = 0; k < N_ACC / 4; ++k) sacc[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
     int cnt = 0;
     int c_s = 0, qhead = 0, qlen = 0;            // stream position, ring head and fill
     while (c_s < C || qlen > 0) {
@@ -680,7 +734,9 @@ __device__ __forceinline__ void pair_unit(const PairArgs& A, int k0, float* wb, 
             float4 ent = make_float4(0.f, 0.f, 0.f, 0.f);
             if (v < C) {
                 int dx, dy, dz;
-                const int i = stream_point(R, v, dx, dy, dz);
+                int i;
+                if constexpr (REG) i = stream_point_r(R, pre, v, dx, dy, dz);
+                else i = stream_point(R, v, dx, dy, dz);
                 const float4 p = __ldg(pts4 + i);
                 ent.x = fmaf((float)dx, gp.hf, p.x);
                 ent.y = fmaf((float)dy, gp.hf, p.y);
@@ -726,11 +782,10 @@ __device__ __forceinline__ void pair_unit(const PairArgs& A, int k0, float* wb, 
         }
         if (!has) mk = 0u;
         if constexpr (BF16 && DP > 0) {
-            label_gram_bf16<DP>(reinterpret_cast<const unsigned*>(sem_sorted), ssq, i, __ballot_sync(FULL, has),
+            label_gram_bf16<DP>(reinterpret_cast<const unsigned*>(sem_sorted), gb, i, __ballot_sync(FULL, has),
                                 lane, gram);
             __syncwarp();
         }
-        const float* gcol = gram + lane;                      // column of this lane's candidate
         const u64 XA = f2(x0, x1), XB = f2(x2, x0);
         float w0 = 0.f, dz_s = 0.f, q12 = 0.f, q22 = 0.f;
         u64 D01 = 0ull, Q0011 = 0ull, Q0201 = 0ull;
@@ -756,7 +811,7 @@ __device__ __forceinline__ void pair_unit(const PairArgs& A, int k0, float* wb, 
                     arg = fmaf(fmaf(cr, cr, fmaf(cg, cg, cb * cb)), gp.kc, arg);
                 }
                 float s;
-                if constexpr (BF16 && DP > 0) s = gcol[j * GRAM_LD];
+                if constexpr (BF16 && DP > 0) s = gram[j * GRAM_LD + gram_col(j, lane)];
                 else s = SemRow<DP, BF16>::dot(cs, ssq + j * SW);
                 kept = true;
                 if constexpr (PRUNE) kept = s >= gp.sem_min;
@@ -804,11 +859,14 @@ __device__ __forceinline__ void pair_unit(const PairArgs& A, int k0, float* wb, 
         const float x[3] = {x0, x1, x2};
         const float dc[3] = {dxy.x, dxy.y, dz_s};
         const float qc[6] = {q0011.x, q0201.y, q0201.x, q0011.y, q12, q22};
-        float a[N_ACC];
+        float a_s[REG ? 1 : N_ACC];
+        float* a = REG ? racc : a_s;
+        if constexpr (!REG) {
 #pragma unroll
-        for (int k = 0; k < N_ACC / 4; ++k) {
-            const float4 t = sacc[k];
-            a[4 * k] = t.x; a[4 * k + 1] = t.y; a[4 * k + 2] = t.z; a[4 * k + 3] = t.w;
+            for (int k = 0; k < N_ACC / 4; ++k) {
+                const float4 t = sacc[k];
+                a[4 * k] = t.x; a[4 * k + 1] = t.y; a[4 * k + 2] = t.z; a[4 * k + 3] = t.w;
+            }
         }
         a[A_W] += w0;
 #pragma unroll
@@ -826,14 +884,20 @@ __device__ __forceinline__ void pair_unit(const PairArgs& A, int k0, float* wb, 
                 a[A_SWXX + t6] = fmaf(wx, x[l], a[A_SWXX + t6]);
             }
         }
+        if constexpr (!REG) {
 #pragma unroll
-        for (int k = 0; k < N_ACC / 4; ++k) sacc[k] = make_float4(a[4 * k], a[4 * k + 1], a[4 * k + 2], a[4 * k + 3]);
+            for (int k = 0; k < N_ACC / 4; ++k)
+                sacc[k] = make_float4(a[4 * k], a[4 * k + 1], a[4 * k + 2], a[4 * k + 3]);
+        }
     }
-    float a[N_ACC];
+    float a_s[REG ? 1 : N_ACC];
+    float* a = REG ? racc : a_s;
+    if constexpr (!REG) {
 #pragma unroll
-    for (int k = 0; k < N_ACC / 4; ++k) {
-        const float4 t = sacc[k];
-        a[4 * k] = t.x; a[4 * k + 1] = t.y; a[4 * k + 2] = t.z; a[4 * k + 3] = t.w;
+        for (int k = 0; k < N_ACC / 4; ++k) {
+            const float4 t = sacc[k];
+            a[4 * k] = t.x; a[4 * k + 1] = t.y; a[4 * k + 2] = t.z; a[4 * k + 3] = t.w;
+        }
     }
     const float W = a[A_W];
     const float Dv[3] = {a[A_D], a[A_D + 1], a[A_D + 2]};
