@@ -170,7 +170,7 @@ struct rkhsba_server {
     void admit_loop();
     void step_loop();
     void step_loop_batched();
-    void issue_round(const std::vector<Req*>& batch);
+    void issue_round(const std::vector<Req*>& batch, int n_iter);
     bool tuning_for(Req* r, rkhsba_tuning* t);
     void finish(Req* r, int state, int status);   // called without mu held
 };
@@ -391,23 +391,24 @@ bool rkhsba_server::tuning_for(Req* r, rkhsba_tuning* t) {
     return true;
 }
 
-// The rest of one LM iteration of every request in `batch` (requests whose
-// first half -- damped solve and query binning -- has completed; r->ev marks
-// its end): on a free round slot one batched pair launch per label layout,
-// then on each request's stream the second half (assembly, accept/reject),
-// a copy of the LM state to the request's pinned mirror, and at once the
-// first half of the next iteration, so that it runs while the host notices
-// the end of this one (a finished solve makes it a no-op).  Requests with the
+// n_iter LM iterations of every request in `batch` (requests whose first
+// half -- damped solve and query binning -- has completed; r->ev marks its
+// end), on one free round slot: per iteration one batched pair launch per
+// label layout on the slot's stream, then on each request's stream the
+// second half (assembly, accept/reject), a copy of the LM state to the
+// request's pinned mirror, and at once the first half of the next
+// iteration, so that the GPU does not wait for the host between iterations
+// (a finished solve makes the rest no-ops).  Requests with the
 // neighbour-limited variant (its own kernel) run whole iterations on their
 // streams.
-void rkhsba_server::issue_round(const std::vector<Req*>& batch) {
+void rkhsba_server::issue_round(const std::vector<Req*>& batch, int n_iter) {
     struct Group { int key; GridParams layout; int ctas; std::vector<Req*> reqs; };
     std::vector<Group> groups;
     for (Req* r : batch) {
         const GridParams g = ctx_layout(r->ctx);
         if (g.top_k > 0) {
             cudaStream_t rs = ctx_stream(r->ctx);
-            ctx_iterate(r->ctx, 1);
+            ctx_iterate(r->ctx, n_iter);
             cudaMemcpyAsync(r->mirror, ctx_state_dev(r->ctx), sizeof(LMState), cudaMemcpyDeviceToHost, rs);
             cudaEventRecord(r->ev, rs);
             continue;
@@ -437,30 +438,35 @@ void rkhsba_server::issue_round(const std::vector<Req*>& batch) {
     PairJob* jobs = rs_free->d_jobs;
     PairJob* hjobs = rs_free->h_jobs;
     int* counters = rs_free->d_counters;
-    int off = 0, gi = 0;
-    for (Group& grp : groups) {
-        const int n = (int)grp.reqs.size();
-        for (int k = 0; k < n; ++k) {
-            Req* r = grp.reqs[k];
-            cudaStreamWaitEvent(rst, r->ev, 0);
-            hjobs[off + k] = ctx_pair_job(r->ctx);
+    {
+        int off = 0;
+        for (Group& grp : groups) {
+            for (size_t k = 0; k < grp.reqs.size(); ++k) hjobs[off + k] = ctx_pair_job(grp.reqs[k]->ctx);
+            off += (int)grp.reqs.size();
         }
-        cudaMemcpyAsync(jobs + off, hjobs + off, sizeof(PairJob) * n, cudaMemcpyHostToDevice, rst);
-        cudaMemsetAsync(counters + gi, 0, sizeof(int), rst);
-        launch_pairs_multi(jobs + off, n, grp.layout, counters + gi, num_sms, grp.ctas, rst);
-        off += n;
-        ++gi;
+        cudaMemcpyAsync(jobs, hjobs, sizeof(PairJob) * off, cudaMemcpyHostToDevice, rst);
     }
-    cudaEventRecord(rs_free->ev_mid, rst);
-    for (Group& grp : groups)
-        for (Req* r : grp.reqs) {
-            cudaStream_t rs = ctx_stream(r->ctx);
-            cudaStreamWaitEvent(rs, rs_free->ev_mid, 0);
-            ctx_iter_post(r->ctx);
-            cudaMemcpyAsync(r->mirror, ctx_state_dev(r->ctx), sizeof(LMState), cudaMemcpyDeviceToHost, rs);
-            ctx_iter_pre(r->ctx);
-            cudaEventRecord(r->ev, rs);
+    for (int it = 0; it < n_iter; ++it) {
+        int off = 0, gi = 0;
+        for (Group& grp : groups) {
+            const int n = (int)grp.reqs.size();
+            for (Req* r : grp.reqs) cudaStreamWaitEvent(rst, r->ev, 0);
+            cudaMemsetAsync(counters + gi, 0, sizeof(int), rst);
+            launch_pairs_multi(jobs + off, n, grp.layout, counters + gi, num_sms, grp.ctas, rst);
+            off += n;
+            ++gi;
         }
+        cudaEventRecord(rs_free->ev_mid, rst);
+        for (Group& grp : groups)
+            for (Req* r : grp.reqs) {
+                cudaStream_t rs = ctx_stream(r->ctx);
+                cudaStreamWaitEvent(rs, rs_free->ev_mid, 0);
+                ctx_iter_post(r->ctx);
+                cudaMemcpyAsync(r->mirror, ctx_state_dev(r->ctx), sizeof(LMState), cudaMemcpyDeviceToHost, rs);
+                ctx_iter_pre(r->ctx);
+                cudaEventRecord(r->ev, rs);
+            }
+    }
 }
 
 // Rolling rounds: every pass collects the requests whose issued work has
@@ -522,10 +528,11 @@ void rkhsba_server::step_loop_batched() {
             std::this_thread::sleep_for(std::chrono::microseconds(20));
             continue;
         }
-        issue_round(batch);
+        const int chunk = std::max(1, cfg.iters_per_issue);
+        issue_round(batch, chunk);
         for (Req* r : batch) {
             r->inflight = true;
-            ++r->issued;
+            r->issued += chunk;
         }
     }
 }
