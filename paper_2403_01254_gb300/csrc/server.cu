@@ -66,6 +66,7 @@ struct Req {
     bool started = false;
     bool inflight = false;           // batched mode: an issued iteration has not completed
     LMState* mirror = nullptr;       // batched mode: pinned copy of the LM state after each iteration
+    int cost_class = 0;              // batched mode: total points < 64k, < 256k, < 1M, more
     int issued = 0;
     Clock::time_point t_submit, t_admit, t_done;
     rkhsba_solve_info info{};
@@ -528,11 +529,21 @@ void rkhsba_server::step_loop_batched() {
             std::this_thread::sleep_for(std::chrono::microseconds(20));
             continue;
         }
+        // one round per cost class (total points: < 64k, < 256k, < 1M, more),
+        // each on its own round slot, so that a round's pair launch and the
+        // iterations it gates do not hold small problems back behind large ones
         const int chunk = std::max(1, cfg.iters_per_issue);
-        issue_round(batch, chunk);
-        for (Req* r : batch) {
-            r->inflight = true;
-            r->issued += chunk;
+        std::vector<Req*> part;
+        for (int cls = 0; cls < 4; ++cls) {
+            part.clear();
+            for (Req* r : batch)
+                if (r->cost_class == cls) part.push_back(r);
+            if (part.empty()) continue;
+            issue_round(part, chunk);
+            for (Req* r : part) {
+                r->inflight = true;
+                r->issued += chunk;
+            }
         }
     }
 }
@@ -674,6 +685,7 @@ rkhsba_status rkhsba_submit(rkhsba_server* s, int32_t n_frames, const int64_t* n
             return RKHSBA_EINVAL;
         }
     r->est = estimate_bytes(*r);
+    r->cost_class = N < (1LL << 16) ? 0 : (N < (1LL << 18) ? 1 : (N < (1LL << 20) ? 2 : 3));
     r->t_submit = Clock::now();
     {
         std::lock_guard<std::mutex> lk(s->mu);
