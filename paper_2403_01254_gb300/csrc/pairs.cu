@@ -374,8 +374,7 @@ __device__ __forceinline__ float ex2_approx(float x) {
 //   walk  [UQ]    float4 (m_x, m_y, m_z, m_x): pairs (m_x, m_y), (m_z, m_x)
 //   test  [UQ/2]  8 floats per query pair (j, j+1):
 //                 (m_x j, m_x j+1, m_y j, m_y j+1, m_z j, m_z j+1, |y|^2 j, |y|^2 j+1)
-//   colours [UQ] float4, labels [UQ][row words], stencil rows [80] ints (row
-//   starts, first home-x and x+1 points, length prefix, packed per-row int4),
+//   colours [UQ] float4, labels [UQ][row words], stencil rows [40] ints,
 //   per-lane unit sums [32][N_ACC] (kept in shared memory to free registers),
 //   candidate queue [CQ_N] float4 (x relative to the home centre, point index),
 //   with BF16 labels the batch's label Gram [32 queries][GRAM_LD] floats.
@@ -391,7 +390,7 @@ constexpr int A_W = 0, A_D = 1, A_Q = 4, A_SWX = 10, A_SWXX = 13, A_SXD = 19;
 
 template <int DP, bool BF16, bool COLOR>
 __host__ __device__ constexpr int warp_smem_words() {
-    return UQ * 4 + UQ * 4 + (COLOR ? UQ * 4 : 0) + UQ * SemRow<DP, BF16>::WORDS + 4 * 20 + 32 * N_ACC +
+    return UQ * 4 + UQ * 4 + (COLOR ? UQ * 4 : 0) + UQ * SemRow<DP, BF16>::WORDS + 4 * 10 + 32 * N_ACC +
            4 * CQ_N + ((BF16 && DP > 0) ? 32 * GRAM_LD : 0);
 }
 
@@ -400,7 +399,6 @@ struct Rows {
     int* b1;    // [9] first point of the home-x cell
     int* b2;    // [9] first point of the x+1 cell
     int* pre;   // [10] prefix of row lengths
-    int4* rows4 = nullptr;   // [9] optional packed (rb - pre, b1, b2, 0) per row
 };
 
 // Rows of the 3x3x3 stencil around home cell (hx, hy, hz): lanes 0..8 fill one
@@ -430,7 +428,6 @@ __device__ __forceinline__ int build_rows(const Rows& R, const int* __restrict__
         R.b1[lane] = b1;
         R.b2[lane] = b2;
         R.pre[lane] = inc - len;
-        if (R.rows4) R.rows4[lane] = make_int4(rb - (inc - len), b1, b2, 0);
     }
     const int total = __shfl_sync(FULL, inc, 8);
     if (lane == 9) R.pre[9] = total;
@@ -451,15 +448,16 @@ __device__ __forceinline__ int stream_point(const Rows& R, int v, int& dx, int& 
     return i;
 }
 
-// The same with the row prefix held in registers (pre[0] = 0) and the
-// per-row starts packed in R.rows4: one shared-memory load per candidate.
+// The same with the row prefix held in registers (pre[0] = 0).
 __device__ __forceinline__ int stream_point_r(const Rows& R, const int (&pre)[9], int v, int& dx, int& dy, int& dz) {
     int r = 0;
 #pragma unroll
     for (int k = 1; k < 9; ++k) r += (pre[k] <= v) ? 1 : 0;
-    const int4 w = R.rows4[r];
-    const int i = w.x + v;
-    dx = (i >= w.y) + (i >= w.z) - 1;
+    int base = pre[0];
+#pragma unroll
+    for (int k = 1; k < 9; ++k) base = (r == k) ? pre[k] : base;
+    const int i = R.rb[r] + (v - base);
+    dx = (i >= R.b1[r]) + (i >= R.b2[r]) - 1;
     dy = (r % 3) - 1;
     dz = (r / 3) - 1;
     return i;
@@ -646,9 +644,9 @@ __device__ __forceinline__ void pair_unit(const PairArgs& A, int k0, float* wb, 
     float4* scq = reinterpret_cast<float4*>(wb + 8 * UQ);             // [UQ] query colours
     float* ssq = wb + (COLOR ? 12 : 8) * UQ;                          // [UQ][SW] query labels
     int* ri = reinterpret_cast<int*>(ssq + UQ * SW);
-    const Rows R{ri, ri + 9, ri + 18, ri + 27, reinterpret_cast<int4*>(ri + 40)};
-    float4* sacc = reinterpret_cast<float4*>(ri + 80) + lane * (N_ACC / 4);   // this lane's unit sums
-    float4* cq = reinterpret_cast<float4*>(ri + 80) + 32 * (N_ACC / 4);       // candidate ring
+    const Rows R{ri, ri + 9, ri + 18, ri + 27};
+    float4* sacc = reinterpret_cast<float4*>(ri + 40) + lane * (N_ACC / 4);   // this lane's unit sums
+    float4* cq = reinterpret_cast<float4*>(ri + 40) + 32 * (N_ACC / 4);       // candidate ring
     float* gram = reinterpret_cast<float*>(cq + CQ_N);                        // [query][candidate] (BF16)
     const ulonglong2* walk2 = reinterpret_cast<const ulonglong2*>(smw);
     const ulonglong2* test2 = reinterpret_cast<const ulonglong2*>(smt);
