@@ -248,6 +248,9 @@ rkhsba_status build(rkhsba_ctx* c, const double* xyz, const float* sem, const fl
     if (c->Q_total >= (1LL << 31) - 64) return fail(c, RKHSBA_EINVAL, "more than 2^31 queries over all edges");
     c->qbits = 1;
     while ((1LL << c->qbits) <= c->total_bins) ++c->qbits;   // invalid key sorts last
+    // three more key bits order a home cell's queries by octant, when they fit
+    c->gp.key_sub = (c->qbits + 3 <= 31) ? 3 : 0;
+    c->qbits += c->gp.key_sub;
     long long scan_n = std::max<long long>((long long)radix_hist_elems(N),
                                            (long long)radix_hist_elems(c->Q_total));
     RK_TRY(alloc(c, &c->d_scan_ws, (long long)scan_ws_elems(scan_n) + 64));
@@ -314,8 +317,10 @@ void run_binning(rkhsba_ctx* c, const double* poses, const int* done) {
                    c->d_scan_ws, c->d_err + 1, st, &alt);
     c->q_sorted_key = alt ? c->d_qkey_alt : c->d_qkey;
     const int* qv = alt ? c->d_qval_alt : c->d_qval;
-    launch_query_gather(c->q_sorted_key, qv, c->d_qrec, c->Q_total, c->d_slots, c->d_bin_first, done, st);
-    launch_units(c->q_sorted_key, c->d_bin_first, c->Q_total, c->tune_uq, c->d_unit_start, c->d_ucount, done, st);
+    launch_query_gather(c->q_sorted_key, qv, c->d_qrec, c->Q_total, c->gp.key_sub, c->d_slots, c->d_bin_first, done,
+                        st);
+    launch_units(c->q_sorted_key, c->d_bin_first, c->Q_total, c->tune_uq, c->gp.key_sub, c->d_unit_start,
+                 c->d_ucount, done, st);
 }
 
 // One evaluation at the device poses `poses`, results into the cand

@@ -97,6 +97,7 @@ struct GridParams {
     int sem_dim, sem_pad, sem_bf16, color;
     int top_k;            // 0: every pair; else the top_k pairs of largest w per query
     float sem_min;        // pairs with <l_i, l_j> below this are dropped (-inf: off)
+    int key_sub;          // low bits of a query key below its home-cell key (3: octant, 0: none)
 };
 
 constexpr int TOPK_MAX = 8;   // largest top_k of the neighbour-limited variant
@@ -182,9 +183,9 @@ void launch_query_keys(const EdgeDev* edges, int E, const FrameDev* frames, cons
                        const uint32_t* pt_cell, const float4* pts4, GridParams gp, long long Q,
                        uint32_t* qkey, int* qval, float4* qrec, const int* done, cudaStream_t st);
 void launch_query_gather(const uint32_t* qkey_sorted, const int* qval_sorted, const float4* qrec,
-                         long long Q, float4* slots, int* bin_first, const int* done,
+                         long long Q, int sub, float4* slots, int* bin_first, const int* done,
                          cudaStream_t st);
-void launch_units(const uint32_t* qkey_sorted, const int* bin_first, long long Q, int uq, int* unit_start,
+void launch_units(const uint32_t* qkey_sorted, const int* bin_first, long long Q, int uq, int sub, int* unit_start,
                   int* n_units, const int* done, cudaStream_t st);
 void launch_pairs(const PairLaunch& L, const PairArgs& A);
 // One persistent launch over the units of n_jobs problems (device array

@@ -214,6 +214,8 @@ extern "C" rkhsba_status rkhsba_eval_static(int32_t n_frames, const int64_t* n_p
     if (Q > MAX_Q) return fail(RKHSBA_EINVAL, "rkhsba_eval_static: more than 131072 queries over all edges");
     int qbits = 1;
     while ((1LL << qbits) <= bins) ++qbits;
+    gp.key_sub = (qbits + 3 <= 31) ? 3 : 0;
+    qbits += gp.key_sub;
     int cbits = 0;
     while ((1LL << cbits) < C) ++cbits;
     int inc_off[MAX_K + 1], inc_list[2 * MAX_E];
@@ -275,8 +277,8 @@ extern "C" rkhsba_status rkhsba_eval_static(int32_t n_frames, const int64_t* n_p
     bool qalt = false;
     radix_sort_u32(d_qkey, d_qval, d_qkey_alt, d_qval_alt, Q, qbits, d_hist, d_ws, d_err + 1, st, &qalt);
     const uint32_t* qk = qalt ? d_qkey_alt : d_qkey;
-    launch_query_gather(qk, qalt ? d_qval_alt : d_qval, d_qrec, Q, d_slots, d_bin_first, nullptr, st);
-    launch_units(qk, d_bin_first, Q, UNIT_Q, d_units, d_ucount, nullptr, st);
+    launch_query_gather(qk, qalt ? d_qval_alt : d_qval, d_qrec, Q, gp.key_sub, d_slots, d_bin_first, nullptr, st);
+    launch_units(qk, d_bin_first, Q, UNIT_Q, gp.key_sub, d_units, d_ucount, nullptr, st);
     {
         PairArgs a{};
         a.qkey = qk;

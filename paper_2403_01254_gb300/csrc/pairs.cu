@@ -157,25 +157,32 @@ __global__ void k_query_keys(const EdgeDev* __restrict__ edges, int E, const Fra
         const int hx = (int)(K[0] + mx) - Fa.lo[0];
         const int hy = (int)(K[1] + my) - Fa.lo[1];
         const int hz = (int)(K[2] + mz) - Fa.lo[2];
+        const float ox = fmaf(-mx, gp.hf, vx), oy = fmaf(-my, gp.hf, vy), oz = fmaf(-mz, gp.hf, vz);
         uint32_t key = NO_KEY;
-        if (hx >= 0 && hy >= 0 && hz >= 0 && hx < Fa.dim[0] && hy < Fa.dim[1] && hz < Fa.dim[2])
+        if (hx >= 0 && hy >= 0 && hz >= 0 && hx < Fa.dim[0] && hy < Fa.dim[1] && hz < Fa.dim[2]) {
             key = (uint32_t)(Ed.bin_off + ((long long)hz * Fa.dim[1] + hy) * Fa.dim[0] + hx);
+            // with key_sub = 3 the low bits hold the query's octant of its home
+            // cell, so a cell's queries sort by octant and a unit's are close
+            if (gp.key_sub)
+                key = (key << 3) | (ox >= 0.f ? 1u : 0u) | (oy >= 0.f ? 2u : 0u) | (oz >= 0.f ? 4u : 0u);
+        }
         qkey[q] = key;
         qval[q] = (int)q;
-        qrec[q] = make_float4(fmaf(-mx, gp.hf, vx), fmaf(-my, gp.hf, vy), fmaf(-mz, gp.hf, vz),
-                              __int_as_float(s));
+        qrec[q] = make_float4(ox, oy, oz, __int_as_float(s));
     }
 }
 
+// sorted query records, and the first sorted query of every home cell (keys
+// >> sub are home-cell keys)
 __global__ void k_query_gather(const uint32_t* __restrict__ key, const int* __restrict__ val,
-                               const float4* __restrict__ qrec, long long Q, float4* __restrict__ slots,
+                               const float4* __restrict__ qrec, long long Q, int sub, float4* __restrict__ slots,
                                int* __restrict__ bin_first, const int* done) {
     if (done && *done) return;
     for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < Q;
          k += (long long)gridDim.x * blockDim.x) {
         slots[k] = qrec[val[k]];
         const uint32_t kk = key[k];
-        if (kk != NO_KEY && (k == 0 || key[k - 1] != kk)) bin_first[kk] = (int)k;
+        if (kk != NO_KEY && (k == 0 || (key[k - 1] >> sub) != (kk >> sub))) bin_first[kk >> sub] = (int)k;
     }
 }
 
@@ -183,7 +190,7 @@ __global__ void k_query_gather(const uint32_t* __restrict__ key, const int* __re
 // after (uq <= 32); one atomic per block reserves the block's slots in the
 // unit list
 __global__ void __launch_bounds__(256) k_units(const uint32_t* __restrict__ key, const int* __restrict__ bin_first,
-                                               long long Q, int uq, int* __restrict__ unit_start,
+                                               long long Q, int uq, int sub, int* __restrict__ unit_start,
                                                int* __restrict__ n_units, const int* done) {
     if (done && *done) return;
     __shared__ int s_cnt[8];
@@ -194,7 +201,7 @@ __global__ void __launch_bounds__(256) k_units(const uint32_t* __restrict__ key,
         bool st = false;
         if (k < Q) {
             const uint32_t kk = key[k];
-            st = kk != NO_KEY && ((k - bin_first[kk]) % uq) == 0;
+            st = kk != NO_KEY && ((k - bin_first[kk >> sub]) % uq) == 0;
         }
         const unsigned m = __ballot_sync(FULL, st);
         if (lane == 0) s_cnt[warp] = __popc(m);
@@ -466,11 +473,11 @@ __device__ __forceinline__ int stream_point_r(const Rows& R, const int (&pre)[9]
 // Unit header shared by the pair and the pair-list kernels: home cell of the
 // unit starting at sorted query k0, and the number of its queries (<= UQ).
 __device__ __forceinline__ int unit_queries(const uint32_t* __restrict__ qkey, long long Q, int k0,
-                                            uint32_t key0, int lane, int uq) {
+                                            uint32_t key0, int lane, int uq, int sub) {
     // units start every uq queries of a home cell, so a unit holds at most uq
     // of them even when the cell continues past k0 + uq
     const long long k1 = (long long)k0 + lane;
-    const bool m1 = k1 < Q && qkey[k1] == key0;
+    const bool m1 = k1 < Q && (qkey[k1] >> sub) == (key0 >> sub);
     const int n = __popc(__ballot_sync(FULL, m1));
     return n < uq ? n : uq;
 }
@@ -651,8 +658,9 @@ __device__ __forceinline__ void pair_unit(const PairArgs& A, int k0, float* wb, 
     const ulonglong2* walk2 = reinterpret_cast<const ulonglong2*>(smw);
     const ulonglong2* test2 = reinterpret_cast<const ulonglong2*>(smt);
     const u64 H2 = f2(0.5f, 0.5f);
-    const uint32_t key0 = qkey[k0];
-    const int qcount = unit_queries(qkey, Q, k0, key0, lane, A.uq);
+    const uint32_t kq0 = qkey[k0];
+    const int qcount = unit_queries(qkey, Q, k0, kq0, lane, A.uq, gp.key_sub);
+    const uint32_t key0 = kq0 >> gp.key_sub;                 // home-cell key
     const int e = find_edge_bin(edges, E, key0);
     const FrameDev& Fa = frames[edges[e].a];
     const int dx0 = Fa.dim[0], dy0 = Fa.dim[1], dz0 = Fa.dim[2];
@@ -1040,8 +1048,9 @@ k_pairs_topk(const int* __restrict__ unit_start, const int* __restrict__ n_units
         u = __shfl_sync(FULL, u, 0);
         if (u >= nu) break;
         const int k0 = unit_start[u];
-        const uint32_t key0 = qkey[k0];
-        const int qcount = unit_queries(qkey, Q, k0, key0, lane, uq);
+        const uint32_t kq0 = qkey[k0];
+        const int qcount = unit_queries(qkey, Q, k0, kq0, lane, uq, gp.key_sub);
+        const uint32_t key0 = kq0 >> gp.key_sub;
         const int e = find_edge_bin(edges, E, key0);
         const FrameDev& Fa = frames[edges[e].a];
         const int dx0 = Fa.dim[0], dy0 = Fa.dim[1], dz0 = Fa.dim[2];
@@ -1204,10 +1213,11 @@ k_emit_pairs(const int* __restrict__ unit_start, const int* __restrict__ n_units
         u = __shfl_sync(FULL, u, 0);
         if (u >= nu) break;
         const int k0 = unit_start[u];
-        const uint32_t key0 = qkey[k0];
+        const uint32_t kq0 = qkey[k0];
+        const uint32_t key0 = kq0 >> gp.key_sub;
         const int e = find_edge_bin(edges, E, key0);
         if (e != edge_sel) continue;
-        const int qcount = unit_queries(qkey, Q, k0, key0, lane, uq);
+        const int qcount = unit_queries(qkey, Q, k0, kq0, lane, uq, gp.key_sub);
         const FrameDev& Fa = frames[edges[e].a];
         const int dx0 = Fa.dim[0], dy0 = Fa.dim[1], dz0 = Fa.dim[2];
         const int cell = (int)(key0 - edges[e].bin_off);
@@ -1342,19 +1352,19 @@ void launch_query_keys(const EdgeDev* edges, int E, const FrameDev* frames, cons
 }
 
 void launch_query_gather(const uint32_t* qkey_sorted, const int* qval_sorted, const float4* qrec,
-                         long long Q, float4* slots, int* bin_first, const int* done,
+                         long long Q, int sub, float4* slots, int* bin_first, const int* done,
                          cudaStream_t st) {
     if (Q <= 0) return;
-    k_query_gather<<<blocks_for(Q, 256), 256, 0, st>>>(qkey_sorted, qval_sorted, qrec, Q, slots, bin_first,
+    k_query_gather<<<blocks_for(Q, 256), 256, 0, st>>>(qkey_sorted, qval_sorted, qrec, Q, sub, slots, bin_first,
                                                       done);
     count_launch();
 }
 
-void launch_units(const uint32_t* qkey_sorted, const int* bin_first, long long Q, int uq, int* unit_start,
+void launch_units(const uint32_t* qkey_sorted, const int* bin_first, long long Q, int uq, int sub, int* unit_start,
                   int* n_units, const int* done, cudaStream_t st) {
     if (Q <= 0) return;
     if (uq < 1 || uq > UQ) uq = UQ;
-    k_units<<<blocks_for(Q, 256), 256, 0, st>>>(qkey_sorted, bin_first, Q, uq, unit_start, n_units, done);
+    k_units<<<blocks_for(Q, 256), 256, 0, st>>>(qkey_sorted, bin_first, Q, uq, sub, unit_start, n_units, done);
     count_launch();
 }
 
