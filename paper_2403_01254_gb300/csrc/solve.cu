@@ -13,6 +13,8 @@
 // poses by the next evaluation (Sec. V-A, last paragraph).
 #include "common.cuh"
 
+#include <algorithm>
+
 namespace rk {
 
 namespace {
@@ -252,6 +254,66 @@ __device__ __forceinline__ double rsqrt_nr(double d) {
 constexpr int LM_T = 512;
 constexpr int LM_SMEM_N = 160;   // n <= 160 keeps the factor in shared memory
 
+// Tail of the LM step, after the damped system is factored (L in the lower
+// triangle of A, row-major n x n, with 1 / L_kk in rinv): forward and back
+// substitution of y = -b in one warp, the step's infinity norm, and the
+// candidate poses T_m exp(delta_m^) (frame 0 fixed).  A failed factorization
+// gives a zero step.  Called by every thread of the block.
+__device__ void lm_finish(int K, int n, const double* __restrict__ A, double* __restrict__ y,
+                          const double* __restrict__ rinv, int fail, const double* __restrict__ Tcur,
+                          double* __restrict__ Tcand, LMState* S, double* red) {
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int nt = blockDim.x;
+    if (!fail) {
+        if (warp == 0) {                          // substitutions in one warp
+            for (int k = 0; k < n; ++k) {         // L z = -b
+                const double yk = y[k] * rinv[k];
+                __syncwarp();
+                if (lane == 0) y[k] = yk;
+                for (int i = k + 1 + lane; i < n; i += 32) y[i] = fma(-A[(long long)i * n + k], yk, y[i]);
+                __syncwarp();
+            }
+            for (int k = n - 1; k >= 0; --k) {    // L^T delta = z
+                const double yk = y[k] * rinv[k];
+                __syncwarp();
+                if (lane == 0) y[k] = yk;
+                for (int i = lane; i < k; i += 32) y[i] = fma(-A[(long long)k * n + i], yk, y[i]);
+                __syncwarp();
+            }
+        }
+        __syncthreads();
+    } else {
+        for (int i = tid; i < n; i += nt) y[i] = 0.0;
+        __syncthreads();
+    }
+    double st = 0.0;
+    for (int i = tid; i < n; i += nt) st = fmax(st, fabs(y[i]));
+    st = block_max(st, red);
+    // candidate poses: frame 0 fixed, T_m exp(delta_m^) otherwise
+    for (int m = tid; m < K; m += nt) {
+        const double* T = Tcur + 16 * m;
+        double* O = Tcand + 16 * m;
+        if (m == 0) {
+            for (int k = 0; k < 16; ++k) O[k] = T[k];
+            continue;
+        }
+        double E12[12];
+        se3_exp_dev(y + 6 * (m - 1), E12);
+        for (int i = 0; i < 3; ++i) {
+            for (int j = 0; j < 4; ++j) {
+                double s = (j == 3) ? T[4 * i + 3] : 0.0;
+                for (int k = 0; k < 3; ++k) s += T[4 * i + k] * E12[4 * k + j];
+                O[4 * i + j] = s;
+            }
+        }
+        O[12] = 0.0; O[13] = 0.0; O[14] = 0.0; O[15] = 1.0;
+    }
+    if (tid == 0) {
+        S->step_inf = st;
+        S->chol_fail = fail;
+    }
+}
+
 __global__ void __launch_bounds__(LM_T) k_lm_solve(int K, const double* __restrict__ Hc,
                                                    const double* __restrict__ bc,
                                                    const double* __restrict__ Tcur,
@@ -316,54 +378,163 @@ __global__ void __launch_bounds__(LM_T) k_lm_solve(int K, const double* __restri
         if (tid == 0 && k + 1 < n) pivot(k + 1);
         __syncthreads();
     }
-    if (!fail) {
-        if (warp == 0) {                          // substitutions in one warp
-            for (int k = 0; k < n; ++k) {         // L z = -b
-                const double yk = y[k] * rinv[k];
-                __syncwarp();
-                if (lane == 0) y[k] = yk;
-                for (int i = k + 1 + lane; i < n; i += 32) y[i] = fma(-A[(long long)i * n + k], yk, y[i]);
-                __syncwarp();
-            }
-            for (int k = n - 1; k >= 0; --k) {    // L^T delta = z
-                const double yk = y[k] * rinv[k];
-                __syncwarp();
-                if (lane == 0) y[k] = yk;
-                for (int i = lane; i < k; i += 32) y[i] = fma(-A[(long long)k * n + i], yk, y[i]);
-                __syncwarp();
-            }
+    lm_finish(K, n, A, y, rinv, fail, Tcur, Tcand, S, red);
+}
+
+// ---- blocked Cholesky over many blocks, for large systems -----------------
+// For n = 6(K-1) >= LM_BLOCKED_N the single-block factorization is bound by
+// one SM reading the trailing matrix from L2; the blocked right-looking form
+// spreads it over the GPU: for each tile column k (tiles of CT = 32 rows) the
+// diagonal tile is factored, the tile column below it solved (one block per
+// tile), and L_ik L_jk^T subtracted from every trailing tile (i, j),
+// k < j <= i (one block per tile).  A sits in the workspace (row-major n x n,
+// lower triangle used); rows and columns beyond n are padded as the identity.
+constexpr int CT = 32;
+constexpr int CH_T = 256;
+constexpr int LM_BLOCKED_N = 192;
+
+// the damped system A = H_ff + lambda Dm and y = -b_f (as k_lm_solve builds them)
+__global__ void __launch_bounds__(CH_T) k_lm_prep(int K, const double* __restrict__ Hc, const double* __restrict__ bc,
+                                                  const LMState* S, double* __restrict__ ws) {
+    __shared__ double red[33];
+    if (S->done) return;
+    const int n = 6 * (K - 1), ld = 6 * K;
+    double* A = ws;
+    double* y = A + (long long)n * n;
+    double dmax = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) dmax = fmax(dmax, Hc[(long long)(6 + i) * ld + 6 + i]);
+    dmax = block_max(dmax, red);
+    const double floor_d = 1e-9 * (dmax > 0.0 ? dmax : 1e-300);
+    const double lam = S->lambda;
+    const long long nn = (long long)n * n;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < nn;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(idx / n), j = (int)(idx % n);
+        double v = Hc[(long long)(6 + i) * ld + 6 + j];
+        if (i == j) v += lam * fmax(v, floor_d);
+        A[idx] = v;
+    }
+    if (blockIdx.x == 0)
+        for (int i = threadIdx.x; i < n; i += blockDim.x) y[i] = -bc[6 + i];
+}
+
+// tile (ti, tj) of A into T[CT][CT + 1]; outside n: identity on the diagonal
+__device__ __forceinline__ void load_tile(const double* __restrict__ A, int n, int ti, int tj, double (*T)[CT + 1]) {
+    for (int e = threadIdx.x; e < CT * CT; e += blockDim.x) {
+        const int r = e / CT, c = e % CT;
+        const int gi = ti * CT + r, gj = tj * CT + c;
+        T[r][c] = (gi < n && gj < n) ? A[(long long)gi * n + gj] : (gi == gj ? 1.0 : 0.0);
+    }
+}
+
+// diagonal tile k: factored in shared memory by one block, written back with
+// the pivot reciprocals
+__global__ void __launch_bounds__(CH_T) k_chol_diag(int K, int k, LMState* S, double* __restrict__ ws) {
+    __shared__ double L[CT][CT + 1];
+    __shared__ int bad;
+    if (S->done || S->chol_fail) return;
+    const int n = 6 * (K - 1);
+    double* A = ws;
+    double* rinv = A + (long long)n * n + n;
+    if (threadIdx.x == 0) bad = 0;
+    load_tile(A, n, k, k, L);
+    __syncthreads();
+    for (int c = 0; c < CT; ++c) {
+        if (threadIdx.x == 0) {
+            const double d = L[c][c];
+            if (!(d > 0.0) || !isfinite(d)) bad = 1;
+            else L[c][c] = sqrt(d);
         }
         __syncthreads();
-    } else {
-        for (int i = tid; i < n; i += LM_T) y[i] = 0.0;
+        if (bad) break;
+        const double inv = 1.0 / L[c][c];
+        for (int r = c + 1 + threadIdx.x; r < CT; r += blockDim.x) L[r][c] *= inv;
+        __syncthreads();
+        for (int e = threadIdx.x; e < CT * CT; e += blockDim.x) {
+            const int r = e / CT, j = e % CT;
+            if (j > c && j <= r) L[r][j] = fma(-L[r][c], L[j][c], L[r][j]);
+        }
         __syncthreads();
     }
-    double st = 0.0;
-    for (int i = tid; i < n; i += LM_T) st = fmax(st, fabs(y[i]));
-    st = block_max(st, red);
-    // candidate poses: frame 0 fixed, T_m exp(delta_m^) otherwise
-    for (int m = tid; m < K; m += LM_T) {
-        const double* T = Tcur + 16 * m;
-        double* O = Tcand + 16 * m;
-        if (m == 0) {
-            for (int k = 0; k < 16; ++k) O[k] = T[k];
-            continue;
-        }
-        double E12[12];
-        se3_exp_dev(y + 6 * (m - 1), E12);
-        for (int i = 0; i < 3; ++i) {
-            for (int j = 0; j < 4; ++j) {
-                double s = (j == 3) ? T[4 * i + 3] : 0.0;
-                for (int k = 0; k < 3; ++k) s += T[4 * i + k] * E12[4 * k + j];
-                O[4 * i + j] = s;
-            }
-        }
-        O[12] = 0.0; O[13] = 0.0; O[14] = 0.0; O[15] = 1.0;
+    if (bad) {
+        if (threadIdx.x == 0) S->chol_fail = 1;
+        return;
     }
-    if (tid == 0) {
-        S->step_inf = st;
-        S->chol_fail = fail;
+    for (int e = threadIdx.x; e < CT * CT; e += blockDim.x) {
+        const int r = e / CT, c = e % CT;
+        const int gi = k * CT + r, gj = k * CT + c;
+        if (c <= r && gi < n && gj < n) A[(long long)gi * n + gj] = L[r][c];
     }
+    for (int r = threadIdx.x; r < CT; r += blockDim.x)
+        if (k * CT + r < n) rinv[k * CT + r] = 1.0 / L[r][r];
+}
+
+// tile column below diagonal tile k: X L_kk^T = A_ik for tile row i = k + 1 +
+// block, one row of X per thread of the first warp
+__global__ void __launch_bounds__(CH_T) k_chol_panel(int K, int k, const LMState* S, double* __restrict__ ws) {
+    __shared__ double L[CT][CT + 1];
+    __shared__ double X[CT][CT + 1];
+    if (S->done || S->chol_fail) return;
+    const int n = 6 * (K - 1);
+    double* A = ws;
+    const int ti = k + 1 + blockIdx.x;
+    load_tile(A, n, k, k, L);
+    load_tile(A, n, ti, k, X);
+    __syncthreads();
+    if (threadIdx.x < CT) {
+        const int r = threadIdx.x;
+        for (int c = 0; c < CT; ++c) {
+            double v = X[r][c];
+            for (int j = 0; j < c; ++j) v = fma(-X[r][j], L[c][j], v);
+            X[r][c] = v / L[c][c];
+        }
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < CT * CT; e += blockDim.x) {
+        const int r = e / CT, c = e % CT;
+        const int gi = ti * CT + r, gj = k * CT + c;
+        if (gi < n && gj < n) A[(long long)gi * n + gj] = X[r][c];
+    }
+}
+
+__global__ void __launch_bounds__(CH_T) k_chol_update(int K, int k, const LMState* S, double* __restrict__ ws) {
+    __shared__ double Li[CT][CT + 1];
+    __shared__ double Lj[CT][CT + 1];
+    if (S->done || S->chol_fail) return;
+    const int n = 6 * (K - 1);
+    double* A = ws;
+    // block b -> trailing tile (i, j), k < j <= i, rows of the lower triangle in order
+    int b = blockIdx.x, i = 0;
+    while (b > i) {
+        b -= i + 1;
+        ++i;
+    }
+    const int ti = k + 1 + i, tj = k + 1 + b;
+    load_tile(A, n, ti, k, Li);
+    load_tile(A, n, tj, k, Lj);
+    __syncthreads();
+    for (int e = threadIdx.x; e < CT * CT; e += blockDim.x) {
+        const int r = e / CT, c = e % CT;
+        const int gi = ti * CT + r, gj = tj * CT + c;
+        if (gi >= n || gj >= n || gj > gi) continue;
+        double v = A[(long long)gi * n + gj];
+#pragma unroll 8
+        for (int q = 0; q < CT; ++q) v = fma(-Li[r][q], Lj[c][q], v);
+        A[(long long)gi * n + gj] = v;
+    }
+}
+
+// substitutions and candidate poses after the blocked factorization
+__global__ void __launch_bounds__(LM_T) k_lm_subst(int K, const double* __restrict__ Tcur,
+                                                   double* __restrict__ Tcand, LMState* S,
+                                                   double* __restrict__ ws) {
+    __shared__ double red[33];
+    if (S->done) return;
+    const int n = 6 * (K - 1);
+    double* A = ws;
+    double* y = A + (long long)n * n;
+    double* rinv = y + n;
+    lm_finish(K, n, A, y, rinv, S->chol_fail, Tcur, Tcand, S, red);
 }
 
 __global__ void k_lm_accept(int K, LMState* S, const double* __restrict__ Fc,
@@ -447,6 +618,26 @@ void launch_lm_solve(int K, const double* H_cur, const double* b_cur, const doub
         cudaFuncSetAttribute(k_lm_solve, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)((size_t)(LM_SMEM_N * LM_SMEM_N + 2 * LM_SMEM_N) * sizeof(double)));
         attr_set = true;
+    }
+    if (n >= LM_BLOCKED_N) {
+        const int nt = (n + CT - 1) / CT;
+        const long long nn = (long long)n * n;
+        k_lm_prep<<<(unsigned)std::min<long long>((nn + CH_T - 1) / CH_T, 4096), CH_T, 0, st>>>(K, H_cur, b_cur,
+                                                                                            st_dev, ws);
+        count_launch();
+        for (int k = 0; k < nt; ++k) {
+            k_chol_diag<<<1, CH_T, 0, st>>>(K, k, st_dev, ws);
+            count_launch();
+            const int m = nt - k - 1;
+            if (m > 0) {
+                k_chol_panel<<<m, CH_T, 0, st>>>(K, k, st_dev, ws);
+                k_chol_update<<<m * (m + 1) / 2, CH_T, 0, st>>>(K, k, st_dev, ws);
+                count_launch(2);
+            }
+        }
+        k_lm_subst<<<1, LM_T, 0, st>>>(K, poses_cur, poses_cand, st_dev, ws);
+        count_launch();
+        return;
     }
     k_lm_solve<<<1, LM_T, smem, st>>>(K, H_cur, b_cur, poses_cur, poses_cand, st_dev, ws);
     count_launch();

@@ -312,3 +312,29 @@ def test_many_frames(pk):
     grad = b / 0.1 ** 2
     assert abs(out["loss"] + F) <= LOSS_TOL * F
     assert _reln(out["grad"], grad) <= GRAD_TOL
+
+
+def test_solve_parity_large_system(pk):
+    """40 frames: the 234 x 234 damped system is factored by the blocked
+    multi-block Cholesky (n >= 192); poses after 10 LM iterations against the
+    oracle's LM."""
+    rng = np.random.default_rng(4040)
+    K, n = 40, 150
+    base = rng.uniform(0, 0.6, (n, 3))
+    gt = [np.eye(4)] + [scenes.random_pose(rng, 10.0, 0.1) for _ in range(K - 1)]
+    xyz = [scenes.to_local(base + rng.normal(scale=0.01, size=base.shape), T) for T in gt]
+    init = np.stack([gt[0]] + [scenes.perturb(rng, T, 2.0, 0.03) for T in gt[1:]])
+    edges = np.array([[m, m + d] for m in range(K) for d in (1, 2) if m + d < K], np.int32)
+    prob = dict(xyz=xyz, sem=None, rgb=None, edges=edges, poses0=init,
+                params=dict(ell=0.1, cutoff_mult=3.0, sigma=1.0, ell_color=0.0, sem_bf16=0))
+    ref = O.lm_solve(prob, params=dict(max_iters=10))
+    g = pk.Problem.from_scene(prob, max_iters=10)
+    try:
+        T, info = g.solve(init)
+    finally:
+        g.close()
+    assert info["iters"] == ref["iters"]
+    dr, dt = _pose_errs(T, ref["poses"])
+    assert dr <= POSE_TOL and dt <= POSE_TOL, (dr, dt, info, ref["status"])
+    moved = max(O.pose_error(a, b)[1] for a, b in zip(ref["poses"], init))
+    assert moved > 100 * POSE_TOL
