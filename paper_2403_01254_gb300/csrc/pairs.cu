@@ -627,6 +627,390 @@ __device__ __forceinline__ void label_gram_bf16(const unsigned* __restrict__ sem
         }
 }
 
+// ------------------------------------------------------ dense tile path ----
+// BF16 labels without colour or pruning.  On the dense workloads most of a
+// batch's 32 x 32 candidate x query tests pass the cutoff (about two thirds
+// after the box cull), so instead of walking each lane's set bits the warp
+// evaluates the whole tile in MMA fragment layout and moves the moment sums
+// onto the tensor cores:
+//   1. S = L_q L_c^T, the tile's label products (BF16 MMA; rows are the
+//      unit's queries, columns the batch's candidates);
+//   2. per element: the exact cutoff test of the bit-walk kernel (same FP32
+//      formula, so the same pair set), w = s 2^(kg |d|^2) (one ex2), and 0
+//      outside r_c; |d|^2 = |y|^2 - 2 x.y + |x|^2;
+//   3. the weights, now an A operand in registers (the accumulator layout of
+//      step 1 is the A-fragment layout of the next MMA), split into FP16
+//      hi + lo, times the candidate features f(x) = (1, x, x x^T), also
+//      split: per query q the sums k_q = sum_c w, X1_q = sum_c w x_c and
+//      X2_q = sum_c w x_c x_c^T accumulate over the unit's batches
+//      (hi*hi + hi*lo + lo*hi: products of 22-bit operands, FP32 sums,
+//      added into FP32 running sums once per batch);
+//   4. at the unit's end each lane takes one query and forms, with y = y_q,
+//      W = k, D = X1 - k y, sum w y = k y, sum w y y^T = k y y^T,
+//      sum w d y^T = D y^T and Q = X2 - X1 y^T - y X1^T + k y y^T, which
+//      enter the same fixed-point reduction as the bit-walk kernel.
+// Scaling: w is carried as w 2^KW with 2^KW |l|max^2 <= 2^14 and the
+// features as x 2^-EX with 2^EX >= h, so every FP16 operand stays inside
+// its range; both are powers of two and undone exactly at the unit's end.
+
+// ldmatrix: four / two / one 8x8 b16 matrices from shared memory; lanes
+// 8m..8m+7 give the row addresses of matrix m.
+__device__ __forceinline__ void ldsm_x4(unsigned (&r)[4], const void* p) {
+    const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]) : "r"(a) : "memory");
+}
+__device__ __forceinline__ void ldsm_x4_t(unsigned (&r)[4], const void* p) {
+    const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]) : "r"(a) : "memory");
+}
+__device__ __forceinline__ void ldsm_x2(unsigned& r0, unsigned& r1, const void* p) {
+    const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+    asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0,%1}, [%2];" : "=r"(r0), "=r"(r1) : "r"(a) : "memory");
+}
+__device__ __forceinline__ void ldsm_x1(unsigned& r0, const void* p) {
+    const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+    asm volatile("ldmatrix.sync.aligned.m8n8.x1.shared.b16 {%0}, [%1];" : "=r"(r0) : "r"(a) : "memory");
+}
+
+__device__ __forceinline__ void mma_bf16_1688(float (&d)[4], unsigned a0, unsigned a1, unsigned b0) {
+    asm("mma.sync.aligned.m16n8k8.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5}, {%6}, {%0,%1,%2,%3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a0), "r"(a1), "r"(b0));
+}
+__device__ __forceinline__ void mma_bf16_16816_r(float (&d)[4], unsigned a0, unsigned a1, unsigned a2, unsigned a3,
+                                                 unsigned b0, unsigned b1) {
+    asm("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+__device__ __forceinline__ void mma_f16_16816(float (&d)[4], const unsigned (&a)[4], unsigned b0, unsigned b1) {
+    asm("mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// (lo, hi) rounded to FP16 (nearest even), lo in the low half
+__device__ __forceinline__ unsigned f16x2_rn(float lo, float hi) {
+    unsigned r;
+    asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
+    return r;
+}
+__device__ __forceinline__ float2 f16x2_to_f32(unsigned v) {
+    float2 r;
+    asm("{\n\t.reg .f16 l, h;\n\tmov.b32 {l, h}, %2;\n\tcvt.f32.f16 %0, l;\n\tcvt.f32.f16 %1, h;\n\t}"
+        : "=f"(r.x), "=f"(r.y) : "r"(v));
+    return r;
+}
+// v0 ~ hi.lo + lo.lo, v1 ~ hi.hi + lo.hi: two FP16 pieces per value (22 bits)
+__device__ __forceinline__ void split_f16x2(float v0, float v1, unsigned& hi, unsigned& lo) {
+    hi = f16x2_rn(v0, v1);
+    const float2 h = f16x2_to_f32(hi);
+    lo = f16x2_rn(v0 - h.x, v1 - h.y);
+}
+
+// Per-warp shared memory of the dense path, in 32-bit words.
+template <int DP>
+struct DenseSmem {
+    static constexpr int RW = DP / 2;                          // words per BF16 label row
+    static constexpr int LW = (RW % 8 == 0) ? RW + 4 : RW;     // row stride: 4 x odd, conflict-free ldmatrix
+    static constexpr int QG = 0;                               // [32][8] (mx mx my my mz mz yy yy), m = -2y
+    static constexpr int QL = QG + 32 * 8;                     // [32][LW] query label rows
+    static constexpr int CL = QL + 32 * LW;                    // [32][LW] the batch's candidate label rows
+    static constexpr int CG = CL + 32 * LW;                    // [16][12] candidate pairs (2p, 2p+1):
+                                                               //   x0 x0' x1 x1' | x2 x2' thr thr' | xk xk' - -
+    static constexpr int CF = CG + 16 * 12;                    // [32][16] features: FP16 hi (8 words), lo (8);
+                                                               //   16-byte chunks XOR-swizzled by (c >> 1) & 3;
+                                                               //   at the unit's end [32 queries][16] FP32 sums
+    static constexpr int RUN = CF + 32 * 16;                   // [32 lanes][20] running sums (16 used)
+    static constexpr int RING = RUN + 32 * 20;                 // [CQ_N] float4 candidate ring
+    static constexpr int ROWS = RING + 4 * CQ_N;               // [40] stencil rows
+    static constexpr int WORDS = ROWS + 40;
+};
+
+template <int DP>
+__device__ __forceinline__ void pair_unit_dense(const PairArgs& A, int k0, float* wb, int lane) {
+    using L = DenseSmem<DP>;
+    constexpr int RW = L::RW, LW = L::LW;
+    constexpr int NKC = DP / 8;                 // 8-wide chunks of a label row (1..4)
+    const GridParams& gp = A.gp;
+    float* qg = wb + L::QG;
+    unsigned* ql = reinterpret_cast<unsigned*>(wb + L::QL);
+    unsigned* cl = reinterpret_cast<unsigned*>(wb + L::CL);
+    float* cg = wb + L::CG;
+    unsigned* cf = reinterpret_cast<unsigned*>(wb + L::CF);
+    float4* cq = reinterpret_cast<float4*>(wb + L::RING);
+    int* ri = reinterpret_cast<int*>(wb + L::ROWS);
+    const Rows R{ri, ri + 9, ri + 18, ri + 27};
+    const int g = lane >> 2, t4 = lane & 3;
+    const float INF = __int_as_float(0x7f800000);
+
+    const uint32_t kq0 = A.qkey[k0];
+    const int qcount = unit_queries(A.qkey, A.Q, k0, kq0, lane, A.uq, gp.key_sub);
+    const uint32_t key0 = kq0 >> gp.key_sub;
+    const int e = find_edge_bin(A.edges, A.E, key0);
+    const FrameDev& Fa = A.frames[A.edges[e].a];
+    const FrameDev& Fb = A.frames[A.edges[e].b];
+    const int dx0 = Fa.dim[0], dy0 = Fa.dim[1], dz0 = Fa.dim[2];
+    const int cell = (int)(key0 - A.edges[e].bin_off);
+    const int hx = cell % dx0, hy = (cell / dx0) % dy0, hz = cell / (dx0 * dy0);
+    // power-of-two scales of the FP16 operands
+    int ew, ex;
+    frexpf(Fa.sem_norm_max * Fb.sem_norm_max, &ew);
+    frexpf(gp.hf, &ex);
+    const int KW = min(max(14 - ew, -100), 100);
+    const float kwf = (float)KW;
+    const float xs = ldexpf(1.f, -ex);
+    __syncwarp();
+    // stage the unit's queries: geometry, label rows (zero rows for absent
+    // queries, whose |y|^2 = inf fails every test), bounding box
+    float blo0 = INF, blo1 = INF, blo2 = INF, bhi0 = -INF, bhi1 = -INF, bhi2 = -INF;
+    {
+        float4* q4 = reinterpret_cast<float4*>(qg) + 2 * lane;
+        uint4* qrow = reinterpret_cast<uint4*>(ql + lane * LW);
+        if (lane < qcount) {
+            const float4 r = A.slots[(long long)k0 + lane];
+            blo0 = bhi0 = r.x;
+            blo1 = bhi1 = r.y;
+            blo2 = bhi2 = r.z;
+            const int s = __float_as_int(r.w);
+            const float mx = -2.f * r.x, my = -2.f * r.y, mz = -2.f * r.z;
+            const float yy = fmaf(r.x, r.x, fmaf(r.y, r.y, r.z * r.z));
+            q4[0] = make_float4(mx, mx, my, my);
+            q4[1] = make_float4(mz, mz, yy, yy);
+            const uint4* src = reinterpret_cast<const uint4*>(A.sem_sorted) + (size_t)s * (RW / 4);
+#pragma unroll
+            for (int k = 0; k < RW / 4; ++k) qrow[k] = __ldg(src + k);
+        } else {
+            q4[0] = make_float4(0.f, 0.f, 0.f, 0.f);
+            q4[1] = make_float4(0.f, 0.f, INF, INF);
+#pragma unroll
+            for (int k = 0; k < RW / 4; ++k) qrow[k] = make_uint4(0u, 0u, 0u, 0u);
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        blo0 = fminf(blo0, __shfl_xor_sync(FULL, blo0, o));
+        blo1 = fminf(blo1, __shfl_xor_sync(FULL, blo1, o));
+        blo2 = fminf(blo2, __shfl_xor_sync(FULL, blo2, o));
+        bhi0 = fmaxf(bhi0, __shfl_xor_sync(FULL, bhi0, o));
+        bhi1 = fmaxf(bhi1, __shfl_xor_sync(FULL, bhi1, o));
+        bhi2 = fmaxf(bhi2, __shfl_xor_sync(FULL, bhi2, o));
+    }
+    const int C = build_rows(R, A.cell_start, Fa.cell_off, dx0, dy0, dz0, hx, hy, hz, lane);
+    const float box_thr = gp.rc2 * 1.0001f;
+    const int n_mt = qcount > 16 ? 2 : 1;       // m tiles of 16 queries that hold queries
+    const u64 KG2 = f2(gp.kg, gp.kg);
+    // this lane's running sums [m tile][feature tile][4], in shared memory
+    float4* run4 = reinterpret_cast<float4*>(wb + L::RUN + 20 * lane);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) run4[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+    int cnt = 0;
+    int c_s = 0, qhead = 0, qlen = 0;
+    while (c_s < C || qlen > 0) {
+        while (qlen < 32 && c_s < C) {
+            const int v = c_s + lane;
+            bool keep = false;
+            float4 ent = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (v < C) {
+                int dx, dy, dz;
+                const int i = stream_point(R, v, dx, dy, dz);
+                const float4 p = __ldg(A.pts4 + i);
+                ent.x = fmaf((float)dx, gp.hf, p.x);
+                ent.y = fmaf((float)dy, gp.hf, p.y);
+                ent.z = fmaf((float)dz, gp.hf, p.z);
+                ent.w = __int_as_float(i);
+                const float e0 = fmaxf(fmaxf(blo0 - ent.x, ent.x - bhi0), 0.f);
+                const float e1 = fmaxf(fmaxf(blo1 - ent.y, ent.y - bhi1), 0.f);
+                const float e2 = fmaxf(fmaxf(blo2 - ent.z, ent.z - bhi2), 0.f);
+                keep = fmaf(e0, e0, fmaf(e1, e1, e2 * e2)) < box_thr;
+            }
+            const unsigned bal = __ballot_sync(FULL, keep);
+            if (keep) cq[(qhead + qlen + __popc(bal & ((1u << lane) - 1u))) & (CQ_N - 1)] = ent;
+            qlen += __popc(bal);
+            c_s += 32;
+        }
+        __syncwarp();
+        const int nb = qlen < 32 ? qlen : 32;
+        if (nb == 0) break;
+        // lane c stages candidate c of the batch (absent ones: zero rows,
+        // zero features, thr = -inf)
+        {
+            const bool has = lane < nb;
+            const float4 ent = has ? cq[(qhead + lane) & (CQ_N - 1)] : make_float4(0.f, 0.f, 0.f, 0.f);
+            const int i = __float_as_int(ent.w);
+            const float x0 = ent.x, x1 = ent.y, x2 = ent.z;
+            const float xx = fmaf(x0, x0, fmaf(x1, x1, x2 * x2));
+            float* cgp = cg + 12 * (lane >> 1) + (lane & 1);
+            cgp[0] = x0;
+            cgp[2] = x1;
+            cgp[4] = x2;
+            cgp[6] = has ? gp.rc2 - xx : -INF;
+            cgp[8] = fmaf(xx, gp.kg, kwf);
+            uint4* crow = reinterpret_cast<uint4*>(cl + lane * LW);
+            const uint4* src = reinterpret_cast<const uint4*>(A.sem_sorted) + (size_t)i * (RW / 4);
+#pragma unroll
+            for (int k = 0; k < RW / 4; ++k) crow[k] = has ? __ldg(src + k) : make_uint4(0u, 0u, 0u, 0u);
+            const float u0 = x0 * xs, u1 = x1 * xs, u2 = x2 * xs;
+            unsigned h0, h1, h2, h3, h4, l0, l1, l2, l3, l4;
+            split_f16x2(has ? 1.f : 0.f, u0, h0, l0);
+            split_f16x2(u1, u2, h1, l1);
+            split_f16x2(u0 * u0, u0 * u1, h2, l2);
+            split_f16x2(u0 * u2, u1 * u1, h3, l3);
+            split_f16x2(u1 * u2, u2 * u2, h4, l4);
+            const int sw = (lane >> 1) & 3;
+            uint4* frow = reinterpret_cast<uint4*>(cf + 16 * lane);
+            frow[0 ^ sw] = make_uint4(h0, h1, h2, h3);
+            frow[1 ^ sw] = make_uint4(h4, 0u, 0u, 0u);
+            frow[2 ^ sw] = make_uint4(l0, l1, l2, l3);
+            frow[3 ^ sw] = make_uint4(l4, 0u, 0u, 0u);
+        }
+        qhead = (qhead + nb) & (CQ_N - 1);
+        qlen -= nb;
+        __syncwarp();
+#pragma unroll
+        for (int mt = 0; mt < 2; ++mt) {
+            if (mt >= n_mt) break;
+            // query-side A fragments of the label products: rows 16 mt ..
+            // 16 mt + 15, 8-wide chunks in pairs
+            unsigned qa[2 * NKC];
+            {
+                const unsigned* rowp = ql + (16 * mt + (lane & 7) + 8 * ((lane >> 3) & 1)) * LW;
+#pragma unroll
+                for (int kc = 0; kc + 1 < NKC; kc += 2) {
+                    unsigned r[4];
+                    ldsm_x4(r, rowp + 4 * (kc + (lane >> 4)));
+                    qa[2 * kc] = r[0];
+                    qa[2 * kc + 1] = r[1];
+                    qa[2 * kc + 2] = r[2];
+                    qa[2 * kc + 3] = r[3];
+                }
+                if constexpr (NKC & 1) ldsm_x2(qa[2 * (NKC - 1)], qa[2 * (NKC - 1) + 1], rowp + 4 * (NKC - 1));
+            }
+            // per candidate tile nt (8 candidates): label products, then the
+            // weights of rows q0 = 16 mt + g, q0 + 8 and columns 8 nt + 2 t4,
+            // + 1, split into the FP16 A operands of the moment MMAs
+            unsigned ah[2][4], al[2][4];
+            const ulonglong2* q2 = reinterpret_cast<const ulonglong2*>(qg);
+#pragma unroll
+            for (int nt = 0; nt < 4; ++nt) {
+                unsigned cb[NKC];
+                {
+                    const unsigned* rowp = cl + (8 * nt + (lane & 7)) * LW;
+                    if constexpr (NKC == 4) {
+                        unsigned r[4];
+                        ldsm_x4(r, rowp + 4 * (lane >> 3));
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) cb[k] = r[k];
+                    } else if constexpr (NKC == 3) {
+                        ldsm_x2(cb[0], cb[1], rowp + 4 * ((lane >> 3) & 1));
+                        ldsm_x1(cb[2], rowp + 8);
+                    } else if constexpr (NKC == 2) {
+                        ldsm_x2(cb[0], cb[1], rowp + 4 * ((lane >> 3) & 1));
+                    } else {
+                        ldsm_x1(cb[0], rowp);
+                    }
+                }
+                float s[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+                for (int kc = 0; kc + 1 < NKC; kc += 2)
+                    mma_bf16_16816_r(s, qa[2 * kc], qa[2 * kc + 1], qa[2 * kc + 2], qa[2 * kc + 3], cb[kc], cb[kc + 1]);
+                if constexpr (NKC & 1) mma_bf16_1688(s, qa[2 * (NKC - 1)], qa[2 * (NKC - 1) + 1], cb[NKC - 1]);
+                const int p = 4 * nt + t4;
+                const ulonglong2 c01 = *reinterpret_cast<const ulonglong2*>(cg + 12 * p);
+                const ulonglong2 c2t = *reinterpret_cast<const ulonglong2*>(cg + 12 * p + 4);
+                const u64 XK = *reinterpret_cast<const u64*>(cg + 12 * p + 8);
+                const float2 thr = f2_split(c2t.y);
+#pragma unroll
+                for (int i = 0; i < 2; ++i) {
+                    const int q = 16 * mt + g + 8 * i;
+                    const ulonglong2 QA = q2[2 * q], QB = q2[2 * q + 1];
+                    const u64 T = ffma2(c01.x, QA.x, ffma2(c01.y, QA.y, ffma2(c2t.x, QB.x, QB.y)));
+                    const float2 t = f2_split(T);
+                    const float2 a = f2_split(ffma2(T, KG2, XK));
+                    const bool in0 = t.x < thr.x, in1 = t.y < thr.y;
+                    const float2 w = f2_split(fmul2(f2(s[2 * i], s[2 * i + 1]), f2(ex2_approx(a.x), ex2_approx(a.y))));
+                    cnt += (in0 ? 1 : 0) + (in1 ? 1 : 0);
+                    split_f16x2(in0 ? w.x : 0.f, in1 ? w.y : 0.f, ah[nt >> 1][2 * (nt & 1) + i],
+                                al[nt >> 1][2 * (nt & 1) + i]);
+                }
+            }
+            // per query: sum over the batch's candidates of w (1, x, x x^T);
+            // feature B fragments (FP16 hi and lo) of each 16-candidate k step
+            float t[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
+#pragma unroll
+            for (int ks = 0; ks < 2; ++ks) {
+                unsigned fh[4], fl[4];
+                const int c = 16 * ks + (lane & 7) + 8 * ((lane >> 3) & 1);
+                const int sw = (c >> 1) & 3;
+                const unsigned* rowp = cf + 16 * c;
+                ldsm_x4_t(fh, rowp + 4 * ((lane >> 4) ^ sw));
+                ldsm_x4_t(fl, rowp + 4 * ((2 + (lane >> 4)) ^ sw));
+#pragma unroll
+                for (int n2 = 0; n2 < 2; ++n2) {
+                    mma_f16_16816(t[n2], ah[ks], fh[2 * n2], fh[2 * n2 + 1]);
+                    mma_f16_16816(t[n2], ah[ks], fl[2 * n2], fl[2 * n2 + 1]);
+                    mma_f16_16816(t[n2], al[ks], fh[2 * n2], fh[2 * n2 + 1]);
+                }
+            }
+#pragma unroll
+            for (int n2 = 0; n2 < 2; ++n2) {
+                float4 r = run4[2 * mt + n2];
+                r.x += t[n2][0];
+                r.y += t[n2][1];
+                r.z += t[n2][2];
+                r.w += t[n2][3];
+                run4[2 * mt + n2] = r;
+            }
+        }
+    }
+    // unit end: per-query sums through shared memory to one lane per query
+    __syncwarp();
+    float* sq = reinterpret_cast<float*>(cf);    // [32][16]
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+        for (int n2 = 0; n2 < 2; ++n2) {
+            const int q0 = 16 * mt + g, n = 8 * n2 + 2 * t4;
+            const float4 r = run4[2 * mt + n2];
+            *reinterpret_cast<float2*>(sq + 16 * q0 + n) = make_float2(r.x, r.y);
+            *reinterpret_cast<float2*>(sq + 16 * (q0 + 8) + n) = make_float2(r.z, r.w);
+        }
+    __syncwarp();
+    const float4* rq = reinterpret_cast<const float4*>(sq + 16 * lane);
+    const float4 r0 = rq[0], r1 = rq[1], r2 = rq[2];
+    const float4 qm = reinterpret_cast<const float4*>(qg)[2 * lane];
+    const float qz = qg[8 * lane + 4];
+    const float y[3] = {-0.5f * qm.x, -0.5f * qm.z, -0.5f * qz};
+    const float s0 = ldexpf(1.f, -KW), s1 = ldexpf(1.f, ex - KW), s2 = ldexpf(1.f, 2 * ex - KW);
+    const float W = r0.x * s0;
+    const float X1[3] = {r0.y * s1, r0.z * s1, r0.w * s1};
+    const float X2[6] = {r1.x * s2, r1.y * s2, r1.z * s2, r1.w * s2, r2.x * s2, r2.y * s2};
+    float Dv[3], Sy[3], Myy[6], Mdy[9], Qm[6];
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+        Sy[m] = W * y[m];
+        Dv[m] = X1[m] - Sy[m];
+    }
+    int t6 = 0;
+#pragma unroll
+    for (int m = 0; m < 3; ++m)
+#pragma unroll
+        for (int l = m; l < 3; ++l, ++t6) {
+            Myy[t6] = Sy[m] * y[l];
+            Qm[t6] = X2[t6] - X1[m] * y[l] - y[m] * X1[l] + Myy[t6];
+        }
+#pragma unroll
+    for (int m = 0; m < 3; ++m)
+#pragma unroll
+        for (int l = 0; l < 3; ++l) Mdy[3 * m + l] = Dv[m] * y[l];
+    store_moments(W, Dv, Sy, Myy, Mdy, Qm, cnt, Fa, hx, hy, hz, gp, A.edges[e].scale,
+                  A.acc + (long long)e * ACC_N, lane);
+}
+
 // One unit (<= A.uq queries of one frame-a home cell, starting at sorted
 // query k0) of the pair sum: stage the queries, stream the candidates of the
 // 27-cell stencil, test, walk and fold, and add the unit's moments to its
@@ -938,7 +1322,21 @@ __device__ __forceinline__ void pair_unit(const PairArgs& A, int k0, float* wb, 
 
 }
 
-template <int DP, bool BF16, bool COLOR>
+// Shared-memory words per warp of the bit-walk (DENSE false) or the dense
+// tile unit (BF16 labels, no colour).
+template <int DP, bool BF16, bool COLOR, bool DENSE>
+__host__ __device__ constexpr int unit_smem_words() {
+    if constexpr (DENSE) return DenseSmem<(DP > 0 ? DP : 8)>::WORDS;
+    else return warp_smem_words<DP, BF16, COLOR>();
+}
+
+template <int DP, bool BF16, bool COLOR, bool DENSE>
+__device__ __forceinline__ void run_unit(const PairArgs& A, int k0, float* wb, int lane) {
+    if constexpr (DENSE && BF16 && DP > 0 && !COLOR) pair_unit_dense<DP>(A, k0, wb, lane);
+    else pair_unit<DP, BF16, COLOR>(A, k0, wb, lane);
+}
+
+template <int DP, bool BF16, bool COLOR, bool DENSE>
 __global__ void __launch_bounds__(PAIR_T, (BF16 && DP > 0) ? 2 : RK_PAIR_MINB)
 k_pairs(const int* __restrict__ unit_start, const int* __restrict__ n_units, int* unit_counter,
         const PairArgs A, const int* done) {
@@ -946,14 +1344,14 @@ k_pairs(const int* __restrict__ unit_start, const int* __restrict__ n_units, int
     extern __shared__ float4 smem4[];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
-    float* wb = reinterpret_cast<float*>(smem4) + warp * warp_smem_words<DP, BF16, COLOR>();
+    float* wb = reinterpret_cast<float*>(smem4) + warp * unit_smem_words<DP, BF16, COLOR, DENSE>();
     const int nu = *n_units;
     for (;;) {
         int u = 0;
         if (lane == 0) u = atomicAdd(unit_counter, 1);
         u = __shfl_sync(FULL, u, 0);
         if (u >= nu) break;
-        pair_unit<DP, BF16, COLOR>(A, unit_start[u], wb, lane);
+        run_unit<DP, BF16, COLOR, DENSE>(A, unit_start[u], wb, lane);
     }
 }
 
@@ -963,7 +1361,7 @@ k_pairs(const int* __restrict__ unit_start, const int* __restrict__ n_units, int
 // the job by binary search over the prefix, and run the unit with that
 // job's arrays.  Every job adds into its own fixed-point accumulators, so a
 // problem's results do not depend on which other problems share the launch.
-template <int DP, bool BF16, bool COLOR>
+template <int DP, bool BF16, bool COLOR, bool DENSE>
 __global__ void __launch_bounds__(PAIR_T, (BF16 && DP > 0) ? 2 : RK_PAIR_MINB)
 k_pairs_multi(const PairJob* __restrict__ jobs, int n_jobs, int* unit_counter) {
     __shared__ int s_pref[MAX_PAIR_JOBS + 1];
@@ -992,7 +1390,7 @@ k_pairs_multi(const PairJob* __restrict__ jobs, int n_jobs, int* unit_counter) {
     }
     __syncthreads();
     const int total = s_pref[n_jobs];
-    float* wb = reinterpret_cast<float*>(smem4) + warp * warp_smem_words<DP, BF16, COLOR>();
+    float* wb = reinterpret_cast<float*>(smem4) + warp * unit_smem_words<DP, BF16, COLOR, DENSE>();
     for (;;) {
         int u = 0;
         if (lane == 0) u = atomicAdd(unit_counter, 1);
@@ -1004,7 +1402,7 @@ k_pairs_multi(const PairJob* __restrict__ jobs, int n_jobs, int* unit_counter) {
             if (s_pref[mid] <= u) lo = mid; else hi = mid - 1;
         }
         const PairJob* J = jobs + lo;
-        pair_unit<DP, BF16, COLOR>(J->a, J->unit_start[u - s_pref[lo]], wb, lane);
+        run_unit<DP, BF16, COLOR, DENSE>(J->a, J->unit_start[u - s_pref[lo]], wb, lane);
     }
 }
 
@@ -1281,6 +1679,18 @@ inline unsigned pair_grid(int num_sms, int resident, int ctas_per_sm) {
     return (unsigned)(num_sms * per_sm);
 }
 
+// The dense tile unit serves BF16 labels without colour and without
+// semantic pruning (top_k has its own kernel); RK_NO_DENSE builds the
+// bit-walk kernel for every layout.
+inline bool dense_path(const GridParams& gp) {
+#ifdef RK_NO_DENSE
+    (void)gp;
+    return false;
+#else
+    return gp.sem_bf16 && gp.sem_pad > 0 && !gp.color && !(gp.sem_min > -__builtin_huge_valf()) && gp.top_k == 0;
+#endif
+}
+
 template <int DP, bool BF16, bool COLOR>
 void run_pairs(const PairLaunch& L, const PairArgs& A) {
     if (A.gp.top_k > 0) {
@@ -1292,21 +1702,41 @@ void run_pairs(const PairLaunch& L, const PairArgs& A) {
             A.pts4, A.sem_sorted, A.col4, A.gp, A.acc, A.uq, L.done);
         return;
     }
+    if constexpr (BF16 && DP > 0 && !COLOR) {
+        if (dense_path(A.gp)) {
+            const size_t smem = sizeof(float) * (PAIR_T / 32) * unit_smem_words<DP, BF16, COLOR, true>();
+            static int resident = 0;
+            const int r = pair_blocks_per_sm(k_pairs<DP, BF16, COLOR, true>, smem, &resident);
+            k_pairs<DP, BF16, COLOR, true><<<pair_grid(L.num_sms, r, L.ctas_per_sm), PAIR_T, smem, L.stream>>>(
+                L.unit_start, L.n_units, L.unit_counter, A, L.done);
+            return;
+        }
+    }
     const size_t smem = sizeof(float) * (PAIR_T / 32) * warp_smem_words<DP, BF16, COLOR>();
     static int resident = 0;   // opt in to > 48 KB and size the persistent grid, once
-    const int r = pair_blocks_per_sm(k_pairs<DP, BF16, COLOR>, smem, &resident);
-    k_pairs<DP, BF16, COLOR><<<pair_grid(L.num_sms, r, L.ctas_per_sm), PAIR_T, smem, L.stream>>>(
+    const int r = pair_blocks_per_sm(k_pairs<DP, BF16, COLOR, false>, smem, &resident);
+    k_pairs<DP, BF16, COLOR, false><<<pair_grid(L.num_sms, r, L.ctas_per_sm), PAIR_T, smem, L.stream>>>(
         L.unit_start, L.n_units, L.unit_counter, A, L.done);
 }
 
 template <int DP, bool BF16, bool COLOR>
-void run_pairs_multi(const PairJob* jobs, int n_jobs, int* counter, int num_sms, int ctas_per_sm,
+void run_pairs_multi(const PairJob* jobs, int n_jobs, int* counter, int num_sms, int ctas_per_sm, bool dense,
                      cudaStream_t st) {
+    if constexpr (BF16 && DP > 0 && !COLOR) {
+        if (dense) {
+            const size_t smem = sizeof(float) * (PAIR_T / 32) * unit_smem_words<DP, BF16, COLOR, true>();
+            static int resident = 0;
+            const int r = pair_blocks_per_sm(k_pairs_multi<DP, BF16, COLOR, true>, smem, &resident);
+            k_pairs_multi<DP, BF16, COLOR, true><<<pair_grid(num_sms, r, ctas_per_sm), PAIR_T, smem, st>>>(
+                jobs, n_jobs, counter);
+            return;
+        }
+    }
     const size_t smem = sizeof(float) * (PAIR_T / 32) * warp_smem_words<DP, BF16, COLOR>();
     static int resident = 0;
-    const int r = pair_blocks_per_sm(k_pairs_multi<DP, BF16, COLOR>, smem, &resident);
-    k_pairs_multi<DP, BF16, COLOR><<<pair_grid(num_sms, r, ctas_per_sm), PAIR_T, smem, st>>>(jobs, n_jobs,
-                                                                                            counter);
+    const int r = pair_blocks_per_sm(k_pairs_multi<DP, BF16, COLOR, false>, smem, &resident);
+    k_pairs_multi<DP, BF16, COLOR, false><<<pair_grid(num_sms, r, ctas_per_sm), PAIR_T, smem, st>>>(
+        jobs, n_jobs, counter);
 }
 
 // Calls F.template operator()<DP, BF16>() for the label layout of gp
@@ -1382,13 +1812,14 @@ struct MultiLaunch {
     const PairJob* jobs;
     int n_jobs;
     bool color;
+    bool dense;
     int* counter;
     int num_sms, ctas_per_sm;
     cudaStream_t st;
     template <int DP, bool BF16>
     void operator()() const {
-        if (color) run_pairs_multi<DP, BF16, true>(jobs, n_jobs, counter, num_sms, ctas_per_sm, st);
-        else run_pairs_multi<DP, BF16, false>(jobs, n_jobs, counter, num_sms, ctas_per_sm, st);
+        if (color) run_pairs_multi<DP, BF16, true>(jobs, n_jobs, counter, num_sms, ctas_per_sm, dense, st);
+        else run_pairs_multi<DP, BF16, false>(jobs, n_jobs, counter, num_sms, ctas_per_sm, dense, st);
     }
 };
 }  // namespace
@@ -1401,8 +1832,8 @@ void launch_pairs(const PairLaunch& L, const PairArgs& A) {
 bool launch_pairs_multi(const PairJob* jobs, int n_jobs, const GridParams& layout, int* counter, int num_sms,
                         int ctas_per_sm, cudaStream_t st) {
     if (n_jobs <= 0 || n_jobs > MAX_PAIR_JOBS || layout.top_k > 0) return false;
-    const bool ok = with_label_layout(layout, MultiLaunch{jobs, n_jobs, layout.color != 0, counter, num_sms,
-                                                          ctas_per_sm, st});
+    const bool ok = with_label_layout(layout, MultiLaunch{jobs, n_jobs, layout.color != 0, dense_path(layout),
+                                                          counter, num_sms, ctas_per_sm, st});
     if (ok) count_launch();
     return ok;
 }

@@ -414,7 +414,9 @@ void rkhsba_server::issue_round(const std::vector<Req*>& batch, int n_iter) {
             cudaEventRecord(r->ev, rs);
             continue;
         }
-        const int key = g.sem_pad * 4 + (g.sem_bf16 ? 2 : 0) + (g.color ? 1 : 0);
+        // one launch serves one label layout, colour use and pruning use
+        const bool prune = g.sem_min > -__builtin_huge_valf();
+        const int key = g.sem_pad * 8 + (prune ? 4 : 0) + (g.sem_bf16 ? 2 : 0) + (g.color ? 1 : 0);
         Group* grp = nullptr;
         for (Group& x : groups)
             if (x.key == key && (int)x.reqs.size() < MAX_PAIR_JOBS) grp = &x;
