@@ -366,6 +366,9 @@ constexpr int PAIR_T = 256;
 #ifndef RK_PAIR_MINB
 #define RK_PAIR_MINB 2              // resident CTAs per SM the register budget targets
 #endif
+#ifndef RK_DENSE_MINB
+#define RK_DENSE_MINB 2             // resident CTAs per SM of the dense tile kernels
+#endif
 constexpr int UQ = UNIT_Q;          // queries per unit: one 32-bit mask word
 static_assert(UQ == 32, "units hold 32 queries");
 
@@ -658,20 +661,20 @@ __device__ __forceinline__ void label_gram_bf16(const unsigned* __restrict__ sem
 __device__ __forceinline__ void ldsm_x4(unsigned (&r)[4], const void* p) {
     const unsigned a = (unsigned)__cvta_generic_to_shared(p);
     asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]) : "r"(a) : "memory");
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]) : "r"(a));
 }
 __device__ __forceinline__ void ldsm_x4_t(unsigned (&r)[4], const void* p) {
     const unsigned a = (unsigned)__cvta_generic_to_shared(p);
     asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]) : "r"(a) : "memory");
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]) : "r"(a));
 }
 __device__ __forceinline__ void ldsm_x2(unsigned& r0, unsigned& r1, const void* p) {
     const unsigned a = (unsigned)__cvta_generic_to_shared(p);
-    asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0,%1}, [%2];" : "=r"(r0), "=r"(r1) : "r"(a) : "memory");
+    asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0,%1}, [%2];" : "=r"(r0), "=r"(r1) : "r"(a));
 }
 __device__ __forceinline__ void ldsm_x1(unsigned& r0, const void* p) {
     const unsigned a = (unsigned)__cvta_generic_to_shared(p);
-    asm volatile("ldmatrix.sync.aligned.m8n8.x1.shared.b16 {%0}, [%1];" : "=r"(r0) : "r"(a) : "memory");
+    asm volatile("ldmatrix.sync.aligned.m8n8.x1.shared.b16 {%0}, [%1];" : "=r"(r0) : "r"(a));
 }
 
 __device__ __forceinline__ void mma_bf16_1688(float (&d)[4], unsigned a0, unsigned a1, unsigned b0) {
@@ -710,6 +713,14 @@ __device__ __forceinline__ void split_f16x2(float v0, float v1, unsigned& hi, un
     hi = f16x2_rn(v0, v1);
     const float2 h = f16x2_to_f32(hi);
     lo = f16x2_rn(v0 - h.x, v1 - h.y);
+}
+
+// w when t < thr (the pair is inside r_c), counted in cnt; else 0
+__device__ __forceinline__ float inside_count(float t, float thr, float w, int& cnt) {
+    float r;
+    asm("{\n\t.reg .pred p;\n\tsetp.lt.f32 p, %2, %3;\n\tselp.f32 %0, %4, 0f00000000, p;\n\t@p add.s32 %1, %1, 1;\n\t}"
+        : "=f"(r), "+r"(cnt) : "f"(t), "f"(thr), "f"(w));
+    return r;
 }
 
 // Per-warp shared memory of the dense path, in 32-bit words.
@@ -931,11 +942,9 @@ __device__ __forceinline__ void pair_unit_dense(const PairArgs& A, int k0, float
                     const u64 T = ffma2(c01.x, QA.x, ffma2(c01.y, QA.y, ffma2(c2t.x, QB.x, QB.y)));
                     const float2 t = f2_split(T);
                     const float2 a = f2_split(ffma2(T, KG2, XK));
-                    const bool in0 = t.x < thr.x, in1 = t.y < thr.y;
-                    const float2 w = f2_split(fmul2(f2(s[2 * i], s[2 * i + 1]), f2(ex2_approx(a.x), ex2_approx(a.y))));
-                    cnt += (in0 ? 1 : 0) + (in1 ? 1 : 0);
-                    split_f16x2(in0 ? w.x : 0.f, in1 ? w.y : 0.f, ah[nt >> 1][2 * (nt & 1) + i],
-                                al[nt >> 1][2 * (nt & 1) + i]);
+                    const float w0 = s[2 * i] * ex2_approx(a.x), w1 = s[2 * i + 1] * ex2_approx(a.y);
+                    split_f16x2(inside_count(t.x, thr.x, w0, cnt), inside_count(t.y, thr.y, w1, cnt),
+                                ah[nt >> 1][2 * (nt & 1) + i], al[nt >> 1][2 * (nt & 1) + i]);
                 }
             }
             // per query: sum over the batch's candidates of w (1, x, x x^T);
@@ -1337,7 +1346,7 @@ __device__ __forceinline__ void run_unit(const PairArgs& A, int k0, float* wb, i
 }
 
 template <int DP, bool BF16, bool COLOR, bool DENSE>
-__global__ void __launch_bounds__(PAIR_T, (BF16 && DP > 0) ? 2 : RK_PAIR_MINB)
+__global__ void __launch_bounds__(PAIR_T, DENSE ? RK_DENSE_MINB : ((BF16 && DP > 0) ? 2 : RK_PAIR_MINB))
 k_pairs(const int* __restrict__ unit_start, const int* __restrict__ n_units, int* unit_counter,
         const PairArgs A, const int* done) {
     if (done && *done) return;
@@ -1362,7 +1371,7 @@ k_pairs(const int* __restrict__ unit_start, const int* __restrict__ n_units, int
 // job's arrays.  Every job adds into its own fixed-point accumulators, so a
 // problem's results do not depend on which other problems share the launch.
 template <int DP, bool BF16, bool COLOR, bool DENSE>
-__global__ void __launch_bounds__(PAIR_T, (BF16 && DP > 0) ? 2 : RK_PAIR_MINB)
+__global__ void __launch_bounds__(PAIR_T, DENSE ? RK_DENSE_MINB : ((BF16 && DP > 0) ? 2 : RK_PAIR_MINB))
 k_pairs_multi(const PairJob* __restrict__ jobs, int n_jobs, int* unit_counter) {
     __shared__ int s_pref[MAX_PAIR_JOBS + 1];
     extern __shared__ float4 smem4[];
