@@ -723,30 +723,136 @@ __device__ __forceinline__ float inside_count(float t, float thr, float w, int& 
     return r;
 }
 
-// Per-warp shared memory of the dense path, in 32-bit words.
-template <int DP>
+// Per-warp shared memory of the dense path, in 32-bit words.  Label rows:
+// BF16 rows as stored (DP values); FP32 rows (SPLIT) as an FP16 hi part and an
+// FP16 lo part of DPH values each (DP rounded up to 8), scaled by a power of two.
+template <int DP, bool SPLIT>
 struct DenseSmem {
-    static constexpr int RW = DP / 2;                          // words per BF16 label row
-    static constexpr int LW = (RW % 8 == 0) ? RW + 4 : RW;     // row stride: 4 x odd, conflict-free ldmatrix
-    static constexpr int QG = 0;                               // [32][8] (mx mx my my mz mz yy yy), m = -2y
-    static constexpr int QL = QG + 32 * 8;                     // [32][LW] query label rows
-    static constexpr int CL = QL + 32 * LW;                    // [32][LW] the batch's candidate label rows
-    static constexpr int CG = CL + 32 * LW;                    // [16][12] candidate pairs (2p, 2p+1):
-                                                               //   x0 x0' x1 x1' | x2 x2' thr thr' | xk xk' - -
-    static constexpr int CF = CG + 16 * 12;                    // [32][16] features: FP16 hi (8 words), lo (8);
-                                                               //   16-byte chunks XOR-swizzled by (c >> 1) & 3;
-                                                               //   at the unit's end [32 queries][16] FP32 sums
-    static constexpr int RUN = CF + 32 * 16;                   // [32 lanes][20] running sums (16 used)
-    static constexpr int RING = RUN + 32 * 20;                 // [CQ_N] float4 candidate ring
-    static constexpr int ROWS = RING + 4 * CQ_N;               // [40] stencil rows
+    static constexpr int DPH = SPLIT ? ((DP + 7) / 8) * 8 : DP;    // values per part
+    static constexpr int PW = DPH / 2;                            // words per part
+    static constexpr int RW = SPLIT ? 2 * PW : PW;                // words per staged row
+    static constexpr int LW = (RW % 8 == 0) ? RW + 4 : RW;        // row stride: 4 x odd, conflict-free ldmatrix
+    static constexpr int QGW = SPLIT ? 4 : 8;                     // query geometry words:
+                                                                  //   (mx mx my my mz mz yy yy) or (mx my mz yy), m = -2y
+    static constexpr int QG = 0;                                  // [32][QGW]
+    static constexpr int QL = QG + 32 * QGW;                      // [32][LW] query label rows
+    static constexpr int CL = QL + 32 * LW;                       // [32][LW] the batch's candidate label rows
+    static constexpr int CG = CL + 32 * LW;                       // [16][12] candidate pairs (2p, 2p+1):
+                                                                  //   x0 x0' x1 x1' | x2 x2' thr thr' | xk xk' - -
+    static constexpr int CF = CG + 16 * 12;                       // [32][16] features: FP16 hi (8 words), lo (8);
+                                                                  //   16-byte chunks XOR-swizzled by (c >> 1) & 3;
+                                                                  //   at the unit's end [32 queries][16] FP32 sums
+    static constexpr int RUN = CF + 32 * 16;                      // [32 lanes][16] running sums, float4 k of
+                                                                  //   lane l at k ^ ((l >> 1) & 3)
+    static constexpr int RING = RUN + 32 * 16;                    // [CQ_N] float4 candidate ring
+    static constexpr int ROWS = RING + 4 * CQ_N;                  // [40] stencil rows
     static constexpr int WORDS = ROWS + 40;
 };
 
-template <int DP>
+// Stage one label row into shared memory: BF16 rows copied; FP32 rows scaled
+// by ls and split into FP16 hi and lo parts (zeros beyond DP); a zero row when
+// !valid.
+template <int DP, bool SPLIT>
+__device__ __forceinline__ void stage_label_row(unsigned* row, const void* base, int i, float ls, bool valid) {
+    using L = DenseSmem<DP, SPLIT>;
+    uint4* dst = reinterpret_cast<uint4*>(row);
+    if constexpr (!SPLIT) {
+        const uint4* src = reinterpret_cast<const uint4*>(base) + (size_t)i * (L::PW / 4);
+#pragma unroll
+        for (int k = 0; k < L::PW / 4; ++k) dst[k] = valid ? __ldg(src + k) : make_uint4(0u, 0u, 0u, 0u);
+    } else {
+        float v[L::DPH];
+        const float4* src = reinterpret_cast<const float4*>(base) + (size_t)i * (DP / 4);
+#pragma unroll
+        for (int k = 0; k < DP / 4; ++k) {
+            const float4 t = valid ? __ldg(src + k) : make_float4(0.f, 0.f, 0.f, 0.f);
+            v[4 * k] = t.x * ls;
+            v[4 * k + 1] = t.y * ls;
+            v[4 * k + 2] = t.z * ls;
+            v[4 * k + 3] = t.w * ls;
+        }
+#pragma unroll
+        for (int k = DP; k < L::DPH; ++k) v[k] = 0.f;
+        unsigned hw[L::PW], lw[L::PW];
+#pragma unroll
+        for (int j = 0; j < L::PW; ++j) split_f16x2(v[2 * j], v[2 * j + 1], hw[j], lw[j]);
+#pragma unroll
+        for (int k = 0; k < L::PW / 4; ++k) {
+            dst[k] = make_uint4(hw[4 * k], hw[4 * k + 1], hw[4 * k + 2], hw[4 * k + 3]);
+            dst[L::PW / 4 + k] = make_uint4(lw[4 * k], lw[4 * k + 1], lw[4 * k + 2], lw[4 * k + 3]);
+        }
+    }
+}
+
+// The 8-wide chunks [0, NKC) of one part of the staged rows as MMA fragments:
+// query side (A, rows 16 mt .. + 15; two registers per chunk) and candidate
+// side (B, candidates 8 nt .. + 7; one register per chunk).
+template <int NKC>
+__device__ __forceinline__ void load_a_chunks(unsigned (&qa)[2 * NKC], const unsigned* rowp) {
+    // rowp: this lane's row (16 mt + (lane & 7) + 8 ((lane >> 3) & 1)) at the part's first word
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int kc = 0; kc + 1 < NKC; kc += 2) {
+        unsigned r[4];
+        ldsm_x4(r, rowp + 4 * (kc + (lane >> 4)));
+        qa[2 * kc] = r[0];
+        qa[2 * kc + 1] = r[1];
+        qa[2 * kc + 2] = r[2];
+        qa[2 * kc + 3] = r[3];
+    }
+    if constexpr (NKC & 1) ldsm_x2(qa[2 * (NKC - 1)], qa[2 * (NKC - 1) + 1], rowp + 4 * (NKC - 1));
+}
+template <int NKC>
+__device__ __forceinline__ void load_b_chunks(unsigned (&cb)[NKC], const unsigned* rowp) {
+    // rowp: row of candidate 8 nt + (lane & 7) at the part's first word
+    const int lane = threadIdx.x & 31;
+    if constexpr (NKC == 4) {
+        unsigned r[4];
+        ldsm_x4(r, rowp + 4 * (lane >> 3));
+#pragma unroll
+        for (int k = 0; k < 4; ++k) cb[k] = r[k];
+    } else if constexpr (NKC == 3) {
+        ldsm_x2(cb[0], cb[1], rowp + 4 * ((lane >> 3) & 1));
+        ldsm_x1(cb[2], rowp + 8);
+    } else if constexpr (NKC == 2) {
+        ldsm_x2(cb[0], cb[1], rowp + 4 * ((lane >> 3) & 1));
+    } else {
+        ldsm_x1(cb[0], rowp);
+    }
+}
+
+__device__ __forceinline__ void mma_f16_1688(float (&d)[4], unsigned a0, unsigned a1, unsigned b0) {
+    asm("mma.sync.aligned.m16n8k8.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5}, {%6}, {%0,%1,%2,%3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a0), "r"(a1), "r"(b0));
+}
+__device__ __forceinline__ void mma_f16_16816_r(float (&d)[4], unsigned a0, unsigned a1, unsigned a2, unsigned a3,
+                                                unsigned b0, unsigned b1) {
+    asm("mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+// s += A B over NKC chunks: BF16 (F16 false) or FP16 operands.
+template <int NKC, bool F16>
+__device__ __forceinline__ void gram_chunks(float (&s)[4], const unsigned (&qa)[2 * NKC], const unsigned (&cb)[NKC]) {
+#pragma unroll
+    for (int kc = 0; kc + 1 < NKC; kc += 2) {
+        if constexpr (F16) mma_f16_16816_r(s, qa[2 * kc], qa[2 * kc + 1], qa[2 * kc + 2], qa[2 * kc + 3], cb[kc], cb[kc + 1]);
+        else mma_bf16_16816_r(s, qa[2 * kc], qa[2 * kc + 1], qa[2 * kc + 2], qa[2 * kc + 3], cb[kc], cb[kc + 1]);
+    }
+    if constexpr (NKC & 1) {
+        if constexpr (F16) mma_f16_1688(s, qa[2 * (NKC - 1)], qa[2 * (NKC - 1) + 1], cb[NKC - 1]);
+        else mma_bf16_1688(s, qa[2 * (NKC - 1)], qa[2 * (NKC - 1) + 1], cb[NKC - 1]);
+    }
+}
+
+template <int DP, bool SPLIT>
 __device__ __forceinline__ void pair_unit_dense(const PairArgs& A, int k0, float* wb, int lane) {
-    using L = DenseSmem<DP>;
-    constexpr int RW = L::RW, LW = L::LW;
-    constexpr int NKC = DP / 8;                 // 8-wide chunks of a label row (1..4)
+    using L = DenseSmem<DP, SPLIT>;
+    constexpr int LW = L::LW, PW = L::PW;
+    constexpr int NKC = L::DPH / 8;             // 8-wide chunks of a label row part (1..4)
     const GridParams& gp = A.gp;
     float* qg = wb + L::QG;
     unsigned* ql = reinterpret_cast<unsigned*>(wb + L::QL);
@@ -773,34 +879,47 @@ __device__ __forceinline__ void pair_unit_dense(const PairArgs& A, int k0, float
     frexpf(Fa.sem_norm_max * Fb.sem_norm_max, &ew);
     frexpf(gp.hf, &ex);
     const int KW = min(max(14 - ew, -100), 100);
-    const float kwf = (float)KW;
+    // FP32 labels enter the FP16 parts scaled by ls = 2^-el (|l| ls < 1), so
+    // the products carry 2^-2el, which the exponent offset undoes
+    int el = 0;
+    if constexpr (SPLIT) {
+        frexpf(fmaxf(Fa.sem_norm_max, Fb.sem_norm_max), &el);
+        el = min(max(el, -60), 60);
+    }
+    const float ls = ldexpf(1.f, -el);
+    const float kwf = (float)(KW + 2 * el);
     const float xs = ldexpf(1.f, -ex);
     __syncwarp();
     // stage the unit's queries: geometry, label rows (zero rows for absent
     // queries, whose |y|^2 = inf fails every test), bounding box
     float blo0 = INF, blo1 = INF, blo2 = INF, bhi0 = -INF, bhi1 = -INF, bhi2 = -INF;
     {
-        float4* q4 = reinterpret_cast<float4*>(qg) + 2 * lane;
-        uint4* qrow = reinterpret_cast<uint4*>(ql + lane * LW);
-        if (lane < qcount) {
+        float4* q4 = reinterpret_cast<float4*>(qg) + (L::QGW / 4) * lane;
+        const bool qv = lane < qcount;
+        int s = 0;
+        if (qv) {
             const float4 r = A.slots[(long long)k0 + lane];
             blo0 = bhi0 = r.x;
             blo1 = bhi1 = r.y;
             blo2 = bhi2 = r.z;
-            const int s = __float_as_int(r.w);
+            s = __float_as_int(r.w);
             const float mx = -2.f * r.x, my = -2.f * r.y, mz = -2.f * r.z;
             const float yy = fmaf(r.x, r.x, fmaf(r.y, r.y, r.z * r.z));
-            q4[0] = make_float4(mx, mx, my, my);
-            q4[1] = make_float4(mz, mz, yy, yy);
-            const uint4* src = reinterpret_cast<const uint4*>(A.sem_sorted) + (size_t)s * (RW / 4);
-#pragma unroll
-            for (int k = 0; k < RW / 4; ++k) qrow[k] = __ldg(src + k);
+            if constexpr (SPLIT) {
+                q4[0] = make_float4(mx, my, mz, yy);
+            } else {
+                q4[0] = make_float4(mx, mx, my, my);
+                q4[1] = make_float4(mz, mz, yy, yy);
+            }
         } else {
-            q4[0] = make_float4(0.f, 0.f, 0.f, 0.f);
-            q4[1] = make_float4(0.f, 0.f, INF, INF);
-#pragma unroll
-            for (int k = 0; k < RW / 4; ++k) qrow[k] = make_uint4(0u, 0u, 0u, 0u);
+            if constexpr (SPLIT) {
+                q4[0] = make_float4(0.f, 0.f, 0.f, INF);
+            } else {
+                q4[0] = make_float4(0.f, 0.f, 0.f, 0.f);
+                q4[1] = make_float4(0.f, 0.f, INF, INF);
+            }
         }
+        stage_label_row<DP, SPLIT>(ql + lane * LW, A.sem_sorted, s, ls, qv);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -816,7 +935,8 @@ __device__ __forceinline__ void pair_unit_dense(const PairArgs& A, int k0, float
     const int n_mt = qcount > 16 ? 2 : 1;       // m tiles of 16 queries that hold queries
     const u64 KG2 = f2(gp.kg, gp.kg);
     // this lane's running sums [m tile][feature tile][4], in shared memory
-    float4* run4 = reinterpret_cast<float4*>(wb + L::RUN + 20 * lane);
+    float4* run4 = reinterpret_cast<float4*>(wb + L::RUN + 16 * lane);
+    const int rsw = (lane >> 1) & 3;
 #pragma unroll
     for (int k = 0; k < 4; ++k) run4[k] = make_float4(0.f, 0.f, 0.f, 0.f);
     int cnt = 0;
@@ -853,6 +973,7 @@ __device__ __forceinline__ void pair_unit_dense(const PairArgs& A, int k0, float
             const bool has = lane < nb;
             const float4 ent = has ? cq[(qhead + lane) & (CQ_N - 1)] : make_float4(0.f, 0.f, 0.f, 0.f);
             const int i = __float_as_int(ent.w);
+            stage_label_row<DP, SPLIT>(cl + lane * LW, A.sem_sorted, i, ls, has);
             const float x0 = ent.x, x1 = ent.y, x2 = ent.z;
             const float xx = fmaf(x0, x0, fmaf(x1, x1, x2 * x2));
             float* cgp = cg + 12 * (lane >> 1) + (lane & 1);
@@ -861,10 +982,6 @@ __device__ __forceinline__ void pair_unit_dense(const PairArgs& A, int k0, float
             cgp[4] = x2;
             cgp[6] = has ? gp.rc2 - xx : -INF;
             cgp[8] = fmaf(xx, gp.kg, kwf);
-            uint4* crow = reinterpret_cast<uint4*>(cl + lane * LW);
-            const uint4* src = reinterpret_cast<const uint4*>(A.sem_sorted) + (size_t)i * (RW / 4);
-#pragma unroll
-            for (int k = 0; k < RW / 4; ++k) crow[k] = has ? __ldg(src + k) : make_uint4(0u, 0u, 0u, 0u);
             const float u0 = x0 * xs, u1 = x1 * xs, u2 = x2 * xs;
             unsigned h0, h1, h2, h3, h4, l0, l1, l2, l3, l4;
             split_f16x2(has ? 1.f : 0.f, u0, h0, l0);
@@ -886,50 +1003,34 @@ __device__ __forceinline__ void pair_unit_dense(const PairArgs& A, int k0, float
         for (int mt = 0; mt < 2; ++mt) {
             if (mt >= n_mt) break;
             // query-side A fragments of the label products: rows 16 mt ..
-            // 16 mt + 15, 8-wide chunks in pairs
+            // 16 mt + 15 (FP32 labels: hi and lo parts)
+            const unsigned* qrowp = ql + (16 * mt + (lane & 7) + 8 * ((lane >> 3) & 1)) * LW;
             unsigned qa[2 * NKC];
-            {
-                const unsigned* rowp = ql + (16 * mt + (lane & 7) + 8 * ((lane >> 3) & 1)) * LW;
-#pragma unroll
-                for (int kc = 0; kc + 1 < NKC; kc += 2) {
-                    unsigned r[4];
-                    ldsm_x4(r, rowp + 4 * (kc + (lane >> 4)));
-                    qa[2 * kc] = r[0];
-                    qa[2 * kc + 1] = r[1];
-                    qa[2 * kc + 2] = r[2];
-                    qa[2 * kc + 3] = r[3];
-                }
-                if constexpr (NKC & 1) ldsm_x2(qa[2 * (NKC - 1)], qa[2 * (NKC - 1) + 1], rowp + 4 * (NKC - 1));
-            }
+            load_a_chunks<NKC>(qa, qrowp);
+            unsigned qal[SPLIT ? 2 * NKC : 1];
+            if constexpr (SPLIT) load_a_chunks<NKC>(qal, qrowp + PW);
             // per candidate tile nt (8 candidates): label products, then the
             // weights of rows q0 = 16 mt + g, q0 + 8 and columns 8 nt + 2 t4,
             // + 1, split into the FP16 A operands of the moment MMAs
             unsigned ah[2][4], al[2][4];
             const ulonglong2* q2 = reinterpret_cast<const ulonglong2*>(qg);
+            const float4* qg4 = reinterpret_cast<const float4*>(qg);
 #pragma unroll
             for (int nt = 0; nt < 4; ++nt) {
+                const unsigned* crowp = cl + (8 * nt + (lane & 7)) * LW;
                 unsigned cb[NKC];
-                {
-                    const unsigned* rowp = cl + (8 * nt + (lane & 7)) * LW;
-                    if constexpr (NKC == 4) {
-                        unsigned r[4];
-                        ldsm_x4(r, rowp + 4 * (lane >> 3));
-#pragma unroll
-                        for (int k = 0; k < 4; ++k) cb[k] = r[k];
-                    } else if constexpr (NKC == 3) {
-                        ldsm_x2(cb[0], cb[1], rowp + 4 * ((lane >> 3) & 1));
-                        ldsm_x1(cb[2], rowp + 8);
-                    } else if constexpr (NKC == 2) {
-                        ldsm_x2(cb[0], cb[1], rowp + 4 * ((lane >> 3) & 1));
-                    } else {
-                        ldsm_x1(cb[0], rowp);
-                    }
-                }
+                load_b_chunks<NKC>(cb, crowp);
                 float s[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-                for (int kc = 0; kc + 1 < NKC; kc += 2)
-                    mma_bf16_16816_r(s, qa[2 * kc], qa[2 * kc + 1], qa[2 * kc + 2], qa[2 * kc + 3], cb[kc], cb[kc + 1]);
-                if constexpr (NKC & 1) mma_bf16_1688(s, qa[2 * (NKC - 1)], qa[2 * (NKC - 1) + 1], cb[NKC - 1]);
+                if constexpr (SPLIT) {
+                    // FP32 labels: hi*hi + hi*lo + lo*hi of the FP16 parts
+                    unsigned cbl[NKC];
+                    load_b_chunks<NKC>(cbl, crowp + PW);
+                    gram_chunks<NKC, true>(s, qa, cb);
+                    gram_chunks<NKC, true>(s, qa, cbl);
+                    gram_chunks<NKC, true>(s, qal, cb);
+                } else {
+                    gram_chunks<NKC, false>(s, qa, cb);
+                }
                 const int p = 4 * nt + t4;
                 const ulonglong2 c01 = *reinterpret_cast<const ulonglong2*>(cg + 12 * p);
                 const ulonglong2 c2t = *reinterpret_cast<const ulonglong2*>(cg + 12 * p + 4);
@@ -938,7 +1039,15 @@ __device__ __forceinline__ void pair_unit_dense(const PairArgs& A, int k0, float
 #pragma unroll
                 for (int i = 0; i < 2; ++i) {
                     const int q = 16 * mt + g + 8 * i;
-                    const ulonglong2 QA = q2[2 * q], QB = q2[2 * q + 1];
+                    ulonglong2 QA, QB;
+                    if constexpr (SPLIT) {
+                        const float4 qv = qg4[q];
+                        QA = make_ulonglong2(f2(qv.x, qv.x), f2(qv.y, qv.y));
+                        QB = make_ulonglong2(f2(qv.z, qv.z), f2(qv.w, qv.w));
+                    } else {
+                        QA = q2[2 * q];
+                        QB = q2[2 * q + 1];
+                    }
                     const u64 T = ffma2(c01.x, QA.x, ffma2(c01.y, QA.y, ffma2(c2t.x, QB.x, QB.y)));
                     const float2 t = f2_split(T);
                     const float2 a = f2_split(ffma2(T, KG2, XK));
@@ -967,12 +1076,12 @@ __device__ __forceinline__ void pair_unit_dense(const PairArgs& A, int k0, float
             }
 #pragma unroll
             for (int n2 = 0; n2 < 2; ++n2) {
-                float4 r = run4[2 * mt + n2];
+                float4 r = run4[(2 * mt + n2) ^ rsw];
                 r.x += t[n2][0];
                 r.y += t[n2][1];
                 r.z += t[n2][2];
                 r.w += t[n2][3];
-                run4[2 * mt + n2] = r;
+                run4[(2 * mt + n2) ^ rsw] = r;
             }
         }
     }
@@ -984,16 +1093,25 @@ __device__ __forceinline__ void pair_unit_dense(const PairArgs& A, int k0, float
 #pragma unroll
         for (int n2 = 0; n2 < 2; ++n2) {
             const int q0 = 16 * mt + g, n = 8 * n2 + 2 * t4;
-            const float4 r = run4[2 * mt + n2];
+            const float4 r = run4[(2 * mt + n2) ^ rsw];
             *reinterpret_cast<float2*>(sq + 16 * q0 + n) = make_float2(r.x, r.y);
             *reinterpret_cast<float2*>(sq + 16 * (q0 + 8) + n) = make_float2(r.z, r.w);
         }
     __syncwarp();
     const float4* rq = reinterpret_cast<const float4*>(sq + 16 * lane);
     const float4 r0 = rq[0], r1 = rq[1], r2 = rq[2];
-    const float4 qm = reinterpret_cast<const float4*>(qg)[2 * lane];
-    const float qz = qg[8 * lane + 4];
-    const float y[3] = {-0.5f * qm.x, -0.5f * qm.z, -0.5f * qz};
+    float y[3];
+    if constexpr (SPLIT) {
+        const float4 qm = reinterpret_cast<const float4*>(qg)[lane];
+        y[0] = -0.5f * qm.x;
+        y[1] = -0.5f * qm.y;
+        y[2] = -0.5f * qm.z;
+    } else {
+        const float4 qm = reinterpret_cast<const float4*>(qg)[2 * lane];
+        y[0] = -0.5f * qm.x;
+        y[1] = -0.5f * qm.z;
+        y[2] = -0.5f * qg[8 * lane + 4];
+    }
     const float s0 = ldexpf(1.f, -KW), s1 = ldexpf(1.f, ex - KW), s2 = ldexpf(1.f, 2 * ex - KW);
     const float W = r0.x * s0;
     const float X1[3] = {r0.y * s1, r0.z * s1, r0.w * s1};
@@ -1335,13 +1453,13 @@ __device__ __forceinline__ void pair_unit(const PairArgs& A, int k0, float* wb, 
 // tile unit (BF16 labels, no colour).
 template <int DP, bool BF16, bool COLOR, bool DENSE>
 __host__ __device__ constexpr int unit_smem_words() {
-    if constexpr (DENSE) return DenseSmem<(DP > 0 ? DP : 8)>::WORDS;
+    if constexpr (DENSE) return DenseSmem<(DP > 0 ? DP : 8), !BF16>::WORDS;
     else return warp_smem_words<DP, BF16, COLOR>();
 }
 
 template <int DP, bool BF16, bool COLOR, bool DENSE>
 __device__ __forceinline__ void run_unit(const PairArgs& A, int k0, float* wb, int lane) {
-    if constexpr (DENSE && BF16 && DP > 0 && !COLOR) pair_unit_dense<DP>(A, k0, wb, lane);
+    if constexpr (DENSE && DP > 0 && !COLOR) pair_unit_dense<DP, !BF16>(A, k0, wb, lane);
     else pair_unit<DP, BF16, COLOR>(A, k0, wb, lane);
 }
 
@@ -1696,7 +1814,7 @@ inline bool dense_path(const GridParams& gp) {
     (void)gp;
     return false;
 #else
-    return gp.sem_bf16 && gp.sem_pad > 0 && !gp.color && !(gp.sem_min > -__builtin_huge_valf()) && gp.top_k == 0;
+    return gp.sem_pad > 0 && !gp.color && !(gp.sem_min > -__builtin_huge_valf()) && gp.top_k == 0;
 #endif
 }
 
@@ -1711,7 +1829,7 @@ void run_pairs(const PairLaunch& L, const PairArgs& A) {
             A.pts4, A.sem_sorted, A.col4, A.gp, A.acc, A.uq, L.done);
         return;
     }
-    if constexpr (BF16 && DP > 0 && !COLOR) {
+    if constexpr (DP > 0 && !COLOR) {
         if (dense_path(A.gp)) {
             const size_t smem = sizeof(float) * (PAIR_T / 32) * unit_smem_words<DP, BF16, COLOR, true>();
             static int resident = 0;
@@ -1731,7 +1849,7 @@ void run_pairs(const PairLaunch& L, const PairArgs& A) {
 template <int DP, bool BF16, bool COLOR>
 void run_pairs_multi(const PairJob* jobs, int n_jobs, int* counter, int num_sms, int ctas_per_sm, bool dense,
                      cudaStream_t st) {
-    if constexpr (BF16 && DP > 0 && !COLOR) {
+    if constexpr (DP > 0 && !COLOR) {
         if (dense) {
             const size_t smem = sizeof(float) * (PAIR_T / 32) * unit_smem_words<DP, BF16, COLOR, true>();
             static int resident = 0;
