@@ -75,12 +75,18 @@ def recorded_traffic(workload_name):
 FLOPS_PER_PAIR = 110
 
 
-def kernel_flops_per_pair(sem_dim, color):
-    """FP32 flops the pair kernel itself spends per pair-term (FMA = 2): d
-    (3), |d|^2 (5), exponent (1), label dot (2 D), w = s k (1), per-pair sums
-    W, D, Q (1 + 3 + 3 + 12); the 28 moments are folded once per candidate,
-    not per pair.  Colour adds 9.  Reported beside the algorithmic basis."""
-    return 29 + 2 * sem_dim + (9 if color else 0)
+def kernel_path(flat):
+    """Which pair kernel serves the workload and where its arithmetic runs.
+    Without colour the dense tile kernel evaluates every candidate x query
+    element of a 32 x 32 batch: the cutoff test, the exponent and w = s k on
+    the FP32 pipe (9 flops per element) and one ex2; the label products and
+    the per-query moment sums on the tensor cores (mma.sync, BF16 or split
+    FP16 operands, FP32 accumulation)."""
+    if flat["color"]:
+        return "bit-walk (colour): FP32 label dot and moment sums per pair on the FP32 pipe"
+    return ("dense tile: test, exponent and weight on the FP32 pipe (9 flops per tested element), label "
+            "products and moment sums on the tensor cores (mma.sync, %s operands)"
+            % ("BF16 labels / split FP16 features" if flat["P"].get("sem_bf16", 0) else "split FP16"))
 
 
 WORKLOADS = {
@@ -338,25 +344,22 @@ def measure_device(pk, rb, prob, steps, warmup, dev, stream, flush, world=1, clo
 
 
 def roofline_of(name, m, steps, dev, sm_max):
-    """Roofline of the dominant kernel (the pair kernel, bound by FP32 issue):
-    achieved = algorithmic flops (110 per pair-term) of the pair-terms one
-    launch processes / that launch's CUDA-event time; peak = SMs x 128 FP32
-    lanes x 2 flop x clock."""
+    """Roofline of the dominant kernel (the pair kernel, bound by instruction
+    issue): achieved = algorithmic flops (110 per pair-term) of the
+    pair-terms one launch processes / that launch's CUDA-event time; peak =
+    SMs x 128 FP32 lanes x 2 flop x clock."""
     import torch
     pair_ms, pair_n = m["prof"]["pairs"]
     props = torch.cuda.get_device_properties(dev)
     peak = props.multi_processor_count * 128 * 2 * sm_max * 1e6 / 1e12
     terms = m["pairs_per_step"] * steps
     achieved = terms * FLOPS_PER_PAIR / (pair_ms / 1e3) / 1e12 if pair_ms > 0 else None
-    kfl = kernel_flops_per_pair(m["flat"]["sem_dim"], m["flat"]["color"])
-    k_achieved = terms * kfl / (pair_ms / 1e3) / 1e12 if pair_ms > 0 else None
     return dict(bound="alu", achieved=achieved, peak=peak, unit="TFLOP/s",
                 frac=(achieved / peak) if achieved else None, traffic=recorded_traffic(name),
                 kernel="k_pairs", flops_per_pair_term=FLOPS_PER_PAIR,
                 peak_basis="%d SMs x 128 FP32 lanes x 2 flop x %.0f MHz (nominal unit counts; no measured FP32 peak)"
                            % (props.multi_processor_count, sm_max),
-                kernel_flops_per_pair_term=kfl,
-                frac_kernel_flops=(k_achieved / peak) if k_achieved else None,
+                kernel_path=kernel_path(m["flat"]),
                 pair_terms_per_launch=m["pairs_per_step"] / 2,
                 pair_kernel_ms_per_launch=pair_ms / max(pair_n, 1),
                 pair_terms_per_s_in_kernel=terms / (pair_ms / 1e3) if pair_ms > 0 else None,
