@@ -343,7 +343,9 @@ rkhsba_status rkhsba_solve_ell_decay(rkhsba_ctx* ctx, const rkhsba_ell_schedule*
  * FP32 rounding (pair sets and the exact fixed-point sums do not change):
  *   cell_scale    grid cell edge in units of r_c (params.cell_scale, fixed
  *                 at rkhsba_create: the grids are built for it)
- *   unit_queries  queries of one home cell handed to a warp at a time (1..32)
+ *   unit_queries  queries of one home cell handed to a warp at a time (1..32;
+ *                 1..64 for BF16 labels without colour, pruning or top_k,
+ *                 whose dense pair kernel takes units of up to 64 queries)
  *   ctas_per_sm   resident CTAs per SM of the persistent pair launch
  *                 (0: as many as fit)
  * ------------------------------------------------------------------------ */
@@ -360,8 +362,9 @@ rkhsba_status rkhsba_get_tuning(const rkhsba_ctx* ctx, rkhsba_tuning* out);
 
 /*
  * rkhsba_autotune -- time the evaluation of one problem under every
- * candidate setting (cell_scale 1, 1.25, 1.5 x unit_queries 32, 16 x
- * ctas_per_sm all, 1; the default setting first) and report the fastest.
+ * candidate setting (cell_scale 1, 1.25, 1.5 x unit_queries 32, 16 and,
+ * where the pair kernel takes it, 64 x ctas_per_sm all, 1; the default
+ * setting first) and report the fastest.
  * For each cell size a temporary context is built from the inputs
  * (arguments as for rkhsba_create, or as for rkhsba_create_device when
  * inputs_on_device is 1); each setting is run once untimed, then at least
@@ -370,7 +373,8 @@ rkhsba_status rkhsba_get_tuning(const rkhsba_ctx* ctx, rkhsba_tuning* out);
  * kept unless another is faster by more than 3%.
  *   best      HOST out: the chosen setting and its mean time (ms)
  *   table     HOST out [table_cap] (may be NULL when table_cap is 0): every
- *             setting tried, in order; *n_table receives the count (12)
+ *             setting tried, in order; *n_table receives the count (12, or
+ *             18 with 64-query units)
  * Creating a context with params.cell_scale = best.cell_scale and calling
  * rkhsba_set_tuning(ctx, best.unit_queries, best.ctas_per_sm) applies it.
  * Synchronous; holds one temporary context at a time.

@@ -556,6 +556,7 @@ PairJob ctx_pair_job(const rkhsba_ctx* c) {
 GridParams ctx_layout(const rkhsba_ctx* c) { return c->gp; }
 int ctx_num_sms(const rkhsba_ctx* c) { return c->num_sms; }
 int ctx_tune_ctas(const rkhsba_ctx* c) { return c->tune_ctas; }
+int ctx_tune_uq(const rkhsba_ctx* c) { return c->tune_uq; }
 cudaStream_t ctx_stream(const rkhsba_ctx* c) { return c->stream; }
 const void* ctx_state_dev(const rkhsba_ctx* c) { return c->d_state; }
 const double* ctx_poses_dev(const rkhsba_ctx* c) { return c->d_poses_cur; }
@@ -784,7 +785,9 @@ int64_t rkhsba_launch_count(void) { return g_launches.load(); }
 
 rkhsba_status rkhsba_set_tuning(rkhsba_ctx* c, int32_t unit_queries, int32_t ctas_per_sm) {
     if (!c) return fail(nullptr, RKHSBA_EINVAL, "ctx is NULL");
-    if (unit_queries < 1 || unit_queries > UNIT_Q) return fail(c, RKHSBA_EINVAL, "unit_queries must be in [1, 32]");
+    if (unit_queries < 1 || unit_queries > pair_unit_max(c->gp))
+        return fail(c, RKHSBA_EINVAL, "unit_queries must be in [1, 32] (up to 64 for BF16 labels without "
+                                      "colour, pruning or top_k)");
     if (ctas_per_sm < 0 || ctas_per_sm > 32) return fail(c, RKHSBA_EINVAL, "ctas_per_sm must be in [0, 32]");
     c->tune_uq = unit_queries;
     c->tune_ctas = ctas_per_sm;
@@ -819,7 +822,7 @@ rkhsba_status rkhsba_autotune(int32_t n_frames, const int64_t* n_points, const d
     // the default setting (cell_scale 1, 32 queries per unit, all CTAs that
     // fit) is timed first
     static const double scales[] = {1.0, 1.25, 1.5};
-    static const int uqs[] = {32, 16};
+    static const int uqs_all[] = {32, 16, 64};   // 64 only where the pair kernel takes it
     static const int ctas[] = {0, 1};
     int n = 0;
     best->ms = -1.0;
@@ -841,8 +844,9 @@ rkhsba_status rkhsba_autotune(int32_t n_frames, const int64_t* n_points, const d
         st = check_poses(c, poses);
         if (st == RKHSBA_OK) {
             cudaMemcpyAsync(c->d_poses_cand, poses, sizeof(double) * 16 * c->K, cudaMemcpyHostToDevice, c->stream);
-            for (int uq : uqs)
+            for (int uq : uqs_all)
                 for (int ct : ctas) {
+                    if (uq > pair_unit_max(c->gp)) continue;
                     c->tune_uq = uq;
                     c->tune_ctas = ct;
                     float ms = 0.f, ms0 = 0.f;

@@ -188,12 +188,15 @@ void launch_query_gather(const uint32_t* qkey_sorted, const int* qval_sorted, co
 void launch_units(const uint32_t* qkey_sorted, const int* bin_first, long long Q, int uq, int sub, int* unit_start,
                   int* n_units, const int* done, cudaStream_t st);
 void launch_pairs(const PairLaunch& L, const PairArgs& A);
+// Largest unit (queries of one home cell per warp) the pair kernel of this
+// layout takes: 64 for the dense tile kernel with BF16 labels, else 32.
+int pair_unit_max(const GridParams& gp);
 // One persistent launch over the units of n_jobs problems (device array
-// `jobs`) that share the label layout, colour use and variant of `layout`;
-// false when the layout has no batched kernel (top_k variant) or n_jobs is
-// out of range.  *counter must be zero.
-bool launch_pairs_multi(const PairJob* jobs, int n_jobs, const GridParams& layout, int* counter, int num_sms,
-                        int ctas_per_sm, cudaStream_t st);
+// `jobs`) that share the label layout, colour use and variant of `layout`,
+// with units of at most max_uq queries; false when the layout has no batched
+// kernel (top_k variant) or n_jobs is out of range.  *counter must be zero.
+bool launch_pairs_multi(const PairJob* jobs, int n_jobs, const GridParams& layout, int max_uq, int* counter,
+                        int num_sms, int ctas_per_sm, cudaStream_t st);
 void launch_emit_pairs(const int* unit_start, const int* n_units, int* unit_counter,
                        const uint32_t* qkey, const float4* slots, long long Q, const EdgeDev* edges,
                        int E, const FrameDev* frames, const int* cell_start, const float4* pts4,
@@ -239,4 +242,5 @@ PairJob ctx_pair_job(const rkhsba_ctx* c);
 GridParams ctx_layout(const rkhsba_ctx* c);
 int ctx_num_sms(const rkhsba_ctx* c);
 int ctx_tune_ctas(const rkhsba_ctx* c);
+int ctx_tune_uq(const rkhsba_ctx* c);
 }  // namespace rk

@@ -485,6 +485,20 @@ __device__ __forceinline__ int unit_queries(const uint32_t* __restrict__ qkey, l
     return n < uq ? n : uq;
 }
 
+// The same for units of up to 64 queries (the dense tile unit and the
+// pair-list kernel).
+__device__ __forceinline__ int unit_queries64(const uint32_t* __restrict__ qkey, long long Q, int k0,
+                                              uint32_t key0, int lane, int uq, int sub) {
+    int n = unit_queries(qkey, Q, k0, key0, lane, uq, sub);
+    if (n == 32 && uq > 32) {
+        const long long k1 = (long long)k0 + 32 + lane;
+        const bool m1 = k1 < Q && (qkey[k1] >> sub) == (key0 >> sub);
+        n = 32 + __popc(__ballot_sync(FULL, m1));
+        n = n < uq ? n : uq;
+    }
+    return n;
+}
+
 // One step of the moment reduce-scatter: lanes whose bit `o` is clear keep
 // the lower half of their values, the others the upper half, and each adds
 // the half its partner sends.
@@ -726,25 +740,29 @@ __device__ __forceinline__ float inside_count(float t, float thr, float w, int& 
 // Per-warp shared memory of the dense path, in 32-bit words.  Label rows:
 // BF16 rows as stored (DP values); FP32 rows (SPLIT) as an FP16 hi part and an
 // FP16 lo part of DPH values each (DP rounded up to 8), scaled by a power of two.
-template <int DP, bool SPLIT>
+template <int DP, bool SPLIT, int MQ = 32>
 struct DenseSmem {
     static constexpr int DPH = SPLIT ? ((DP + 7) / 8) * 8 : DP;    // values per part
     static constexpr int PW = DPH / 2;                            // words per part
     static constexpr int RW = SPLIT ? 2 * PW : PW;                // words per staged row
     static constexpr int LW = (RW % 8 == 0) ? RW + 4 : RW;        // row stride: 4 x odd, conflict-free ldmatrix
+    static constexpr int MAXQ = SPLIT ? 32 : MQ;                  // queries per unit (m tiles of 16: MAXQ / 16)
     static constexpr int QGW = SPLIT ? 4 : 8;                     // query geometry words:
                                                                   //   (mx mx my my mz mz yy yy) or (mx my mz yy), m = -2y
-    static constexpr int QG = 0;                                  // [32][QGW]
-    static constexpr int QL = QG + 32 * QGW;                      // [32][LW] query label rows
-    static constexpr int CL = QL + 32 * LW;                       // [32][LW] the batch's candidate label rows
+    static constexpr int QG = 0;                                  // [MAXQ][QGW]
+    static constexpr int QL = QG + MAXQ * QGW;                    // [MAXQ][LW] query label rows
+    static constexpr int CL = QL + MAXQ * LW;                     // [32][LW] the batch's candidate label rows
     static constexpr int CG = CL + 32 * LW;                       // [16][12] candidate pairs (2p, 2p+1):
                                                                   //   x0 x0' x1 x1' | x2 x2' thr thr' | xk xk' - -
     static constexpr int CF = CG + 16 * 12;                       // [32][16] features: FP16 hi (8 words), lo (8);
                                                                   //   16-byte chunks XOR-swizzled by (c >> 1) & 3;
                                                                   //   at the unit's end [32 queries][16] FP32 sums
-    static constexpr int RUN = CF + 32 * 16;                      // [32 lanes][16] running sums, float4 k of
-                                                                  //   lane l at k ^ ((l >> 1) & 3)
-    static constexpr int RING = RUN + 32 * 16;                    // [CQ_N] float4 candidate ring
+    // running per-query sums of the moment MMAs, in the accumulator layout:
+    // feature tile 0 as [m tile][lane] float4; feature tile 1 holds only
+    // features 8 and 9 (lanes with t4 = 0), as [m tile][g] float4
+    static constexpr int RUN = CF + 32 * 16;
+    static constexpr int RUN1 = RUN + (MAXQ / 16) * 32 * 4;
+    static constexpr int RING = RUN1 + (MAXQ / 16) * 8 * 4;      // [CQ_N] float4 candidate ring
     static constexpr int ROWS = RING + 4 * CQ_N;                  // [40] stencil rows
     static constexpr int WORDS = ROWS + 40;
 };
@@ -848,9 +866,9 @@ __device__ __forceinline__ void gram_chunks(float (&s)[4], const unsigned (&qa)[
     }
 }
 
-template <int DP, bool SPLIT>
+template <int DP, bool SPLIT, int MQ>
 __device__ __forceinline__ void pair_unit_dense(const PairArgs& A, int k0, float* wb, int lane) {
-    using L = DenseSmem<DP, SPLIT>;
+    using L = DenseSmem<DP, SPLIT, MQ>;
     constexpr int LW = L::LW, PW = L::PW;
     constexpr int NKC = L::DPH / 8;             // 8-wide chunks of a label row part (1..4)
     const GridParams& gp = A.gp;
@@ -866,7 +884,7 @@ __device__ __forceinline__ void pair_unit_dense(const PairArgs& A, int k0, float
     const float INF = __int_as_float(0x7f800000);
 
     const uint32_t kq0 = A.qkey[k0];
-    const int qcount = unit_queries(A.qkey, A.Q, k0, kq0, lane, A.uq, gp.key_sub);
+    const int qcount = unit_queries64(A.qkey, A.Q, k0, kq0, lane, L::MAXQ < A.uq ? L::MAXQ : A.uq, gp.key_sub);
     const uint32_t key0 = kq0 >> gp.key_sub;
     const int e = find_edge_bin(A.edges, A.E, key0);
     const FrameDev& Fa = A.frames[A.edges[e].a];
@@ -893,15 +911,20 @@ __device__ __forceinline__ void pair_unit_dense(const PairArgs& A, int k0, float
     // stage the unit's queries: geometry, label rows (zero rows for absent
     // queries, whose |y|^2 = inf fails every test), bounding box
     float blo0 = INF, blo1 = INF, blo2 = INF, bhi0 = -INF, bhi1 = -INF, bhi2 = -INF;
-    {
-        float4* q4 = reinterpret_cast<float4*>(qg) + (L::QGW / 4) * lane;
-        const bool qv = lane < qcount;
+#pragma unroll
+    for (int h = 0; h < L::MAXQ / 32; ++h) {
+        const int q = lane + 32 * h;
+        float4* q4 = reinterpret_cast<float4*>(qg) + (L::QGW / 4) * q;
+        const bool qv = q < qcount;
         int s = 0;
         if (qv) {
-            const float4 r = A.slots[(long long)k0 + lane];
-            blo0 = bhi0 = r.x;
-            blo1 = bhi1 = r.y;
-            blo2 = bhi2 = r.z;
+            const float4 r = A.slots[(long long)k0 + q];
+            blo0 = fminf(blo0, r.x);
+            bhi0 = fmaxf(bhi0, r.x);
+            blo1 = fminf(blo1, r.y);
+            bhi1 = fmaxf(bhi1, r.y);
+            blo2 = fminf(blo2, r.z);
+            bhi2 = fmaxf(bhi2, r.z);
             s = __float_as_int(r.w);
             const float mx = -2.f * r.x, my = -2.f * r.y, mz = -2.f * r.z;
             const float yy = fmaf(r.x, r.x, fmaf(r.y, r.y, r.z * r.z));
@@ -919,7 +942,7 @@ __device__ __forceinline__ void pair_unit_dense(const PairArgs& A, int k0, float
                 q4[1] = make_float4(0.f, 0.f, INF, INF);
             }
         }
-        stage_label_row<DP, SPLIT>(ql + lane * LW, A.sem_sorted, s, ls, qv);
+        stage_label_row<DP, SPLIT>(ql + q * LW, A.sem_sorted, s, ls, qv);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -932,13 +955,17 @@ __device__ __forceinline__ void pair_unit_dense(const PairArgs& A, int k0, float
     }
     const int C = build_rows(R, A.cell_start, Fa.cell_off, dx0, dy0, dz0, hx, hy, hz, lane);
     const float box_thr = gp.rc2 * 1.0001f;
-    const int n_mt = qcount > 16 ? 2 : 1;       // m tiles of 16 queries that hold queries
+    const int n_mt = (qcount + 15) >> 4;        // m tiles of 16 queries that hold queries
     const u64 KG2 = f2(gp.kg, gp.kg);
-    // this lane's running sums [m tile][feature tile][4], in shared memory
-    float4* run4 = reinterpret_cast<float4*>(wb + L::RUN + 16 * lane);
-    const int rsw = (lane >> 1) & 3;
+    // this lane's running sums (feature tile 0 for every lane, tile 1 for
+    // the lanes holding features 8 and 9), in shared memory
+    float4* run0 = reinterpret_cast<float4*>(wb + L::RUN) + lane;       // [mt * 32]
+    float4* run1 = reinterpret_cast<float4*>(wb + L::RUN1) + g;         // [mt * 8], t4 == 0
 #pragma unroll
-    for (int k = 0; k < 4; ++k) run4[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int mt = 0; mt < L::MAXQ / 16; ++mt) {
+        run0[32 * mt] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (t4 == 0) run1[8 * mt] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
     int cnt = 0;
     int c_s = 0, qhead = 0, qlen = 0;
     while (c_s < C || qlen > 0) {
@@ -1000,7 +1027,7 @@ __device__ __forceinline__ void pair_unit_dense(const PairArgs& A, int k0, float
         qlen -= nb;
         __syncwarp();
 #pragma unroll
-        for (int mt = 0; mt < 2; ++mt) {
+        for (int mt = 0; mt < L::MAXQ / 16; ++mt) {
             if (mt >= n_mt) break;
             // query-side A fragments of the label products: rows 16 mt ..
             // 16 mt + 15 (FP32 labels: hi and lo parts)
@@ -1074,66 +1101,95 @@ __device__ __forceinline__ void pair_unit_dense(const PairArgs& A, int k0, float
                     mma_f16_16816(t[n2], al[ks], fh[2 * n2], fh[2 * n2 + 1]);
                 }
             }
-#pragma unroll
-            for (int n2 = 0; n2 < 2; ++n2) {
-                float4 r = run4[(2 * mt + n2) ^ rsw];
-                r.x += t[n2][0];
-                r.y += t[n2][1];
-                r.z += t[n2][2];
-                r.w += t[n2][3];
-                run4[(2 * mt + n2) ^ rsw] = r;
+            {
+                float4 r = run0[32 * mt];
+                r.x += t[0][0];
+                r.y += t[0][1];
+                r.z += t[0][2];
+                r.w += t[0][3];
+                run0[32 * mt] = r;
+                if (t4 == 0) {     // features 8, 9 (the other columns of tile 1 are zero)
+                    float4 r1 = run1[8 * mt];
+                    r1.x += t[1][0];
+                    r1.y += t[1][1];
+                    r1.z += t[1][2];
+                    r1.w += t[1][3];
+                    run1[8 * mt] = r1;
+                }
             }
         }
     }
     // unit end: per-query sums through shared memory to one lane per query
-    __syncwarp();
-    float* sq = reinterpret_cast<float*>(cf);    // [32][16]
+    // (32 queries at a time), formed into this lane's moments
+    float W = 0.f, Dv[3] = {0.f, 0.f, 0.f}, Sy[3] = {0.f, 0.f, 0.f}, Myy[6], Mdy[9], Qm[6];
 #pragma unroll
-    for (int mt = 0; mt < 2; ++mt)
+    for (int k = 0; k < 6; ++k) Myy[k] = Qm[k] = 0.f;
 #pragma unroll
-        for (int n2 = 0; n2 < 2; ++n2) {
-            const int q0 = 16 * mt + g, n = 8 * n2 + 2 * t4;
-            const float4 r = run4[(2 * mt + n2) ^ rsw];
-            *reinterpret_cast<float2*>(sq + 16 * q0 + n) = make_float2(r.x, r.y);
-            *reinterpret_cast<float2*>(sq + 16 * (q0 + 8) + n) = make_float2(r.z, r.w);
-        }
-    __syncwarp();
-    const float4* rq = reinterpret_cast<const float4*>(sq + 16 * lane);
-    const float4 r0 = rq[0], r1 = rq[1], r2 = rq[2];
-    float y[3];
-    if constexpr (SPLIT) {
-        const float4 qm = reinterpret_cast<const float4*>(qg)[lane];
-        y[0] = -0.5f * qm.x;
-        y[1] = -0.5f * qm.y;
-        y[2] = -0.5f * qm.z;
-    } else {
-        const float4 qm = reinterpret_cast<const float4*>(qg)[2 * lane];
-        y[0] = -0.5f * qm.x;
-        y[1] = -0.5f * qm.z;
-        y[2] = -0.5f * qg[8 * lane + 4];
-    }
+    for (int k = 0; k < 9; ++k) Mdy[k] = 0.f;
     const float s0 = ldexpf(1.f, -KW), s1 = ldexpf(1.f, ex - KW), s2 = ldexpf(1.f, 2 * ex - KW);
-    const float W = r0.x * s0;
-    const float X1[3] = {r0.y * s1, r0.z * s1, r0.w * s1};
-    const float X2[6] = {r1.x * s2, r1.y * s2, r1.z * s2, r1.w * s2, r2.x * s2, r2.y * s2};
-    float Dv[3], Sy[3], Myy[6], Mdy[9], Qm[6];
+    float* sq = reinterpret_cast<float*>(cf);    // [32][16] (features 0..9 used)
 #pragma unroll
-    for (int m = 0; m < 3; ++m) {
-        Sy[m] = W * y[m];
-        Dv[m] = X1[m] - Sy[m];
-    }
-    int t6 = 0;
+    for (int h = 0; h < L::MAXQ / 32; ++h) {
+        __syncwarp();
 #pragma unroll
-    for (int m = 0; m < 3; ++m)
-#pragma unroll
-        for (int l = m; l < 3; ++l, ++t6) {
-            Myy[t6] = Sy[m] * y[l];
-            Qm[t6] = X2[t6] - X1[m] * y[l] - y[m] * X1[l] + Myy[t6];
+        for (int m2 = 0; m2 < 2; ++m2) {
+            const int mt = 2 * h + m2;
+            const int q0 = 16 * m2 + g;
+            const float4 r = run0[32 * mt];
+            *reinterpret_cast<float2*>(sq + 16 * q0 + 2 * t4) = make_float2(r.x, r.y);
+            *reinterpret_cast<float2*>(sq + 16 * (q0 + 8) + 2 * t4) = make_float2(r.z, r.w);
+            if (t4 == 0) {
+                const float4 r1 = run1[8 * mt];
+                *reinterpret_cast<float2*>(sq + 16 * q0 + 8) = make_float2(r1.x, r1.y);
+                *reinterpret_cast<float2*>(sq + 16 * (q0 + 8) + 8) = make_float2(r1.z, r1.w);
+            }
         }
+        __syncwarp();
+        const int q = lane + 32 * h;
+        const float4* rq = reinterpret_cast<const float4*>(sq + 16 * lane);
+        const float4 r0 = rq[0], r1 = rq[1];
+        const float2 r2 = *reinterpret_cast<const float2*>(sq + 16 * lane + 8);
+        float y[3];
+        if constexpr (SPLIT) {
+            const float4 qm = reinterpret_cast<const float4*>(qg)[q];
+            y[0] = -0.5f * qm.x;
+            y[1] = -0.5f * qm.y;
+            y[2] = -0.5f * qm.z;
+        } else {
+            const float4 qm = reinterpret_cast<const float4*>(qg)[2 * q];
+            y[0] = -0.5f * qm.x;
+            y[1] = -0.5f * qm.z;
+            y[2] = -0.5f * qg[8 * q + 4];
+        }
+        const float k = r0.x * s0;
+        const float X1[3] = {r0.y * s1, r0.z * s1, r0.w * s1};
+        const float X2[6] = {r1.x * s2, r1.y * s2, r1.z * s2, r1.w * s2, r2.x * s2, r2.y * s2};
+        float ky[3], D[3];
 #pragma unroll
-    for (int m = 0; m < 3; ++m)
+        for (int m = 0; m < 3; ++m) {
+            ky[m] = k * y[m];
+            D[m] = X1[m] - ky[m];
+        }
+        W += k;
 #pragma unroll
-        for (int l = 0; l < 3; ++l) Mdy[3 * m + l] = Dv[m] * y[l];
+        for (int m = 0; m < 3; ++m) {
+            Sy[m] += ky[m];
+            Dv[m] += D[m];
+        }
+        int t6 = 0;
+#pragma unroll
+        for (int m = 0; m < 3; ++m)
+#pragma unroll
+            for (int l = m; l < 3; ++l, ++t6) {
+                const float kyy = ky[m] * y[l];
+                Myy[t6] += kyy;
+                Qm[t6] += X2[t6] - X1[m] * y[l] - y[m] * X1[l] + kyy;
+            }
+#pragma unroll
+        for (int m = 0; m < 3; ++m)
+#pragma unroll
+            for (int l = 0; l < 3; ++l) Mdy[3 * m + l] = fmaf(D[m], y[l], Mdy[3 * m + l]);
+    }
     store_moments(W, Dv, Sy, Myy, Mdy, Qm, cnt, Fa, hx, hy, hz, gp, A.edges[e].scale,
                   A.acc + (long long)e * ACC_N, lane);
 }
@@ -1451,19 +1507,21 @@ __device__ __forceinline__ void pair_unit(const PairArgs& A, int k0, float* wb, 
 
 // Shared-memory words per warp of the bit-walk (DENSE false) or the dense
 // tile unit (BF16 labels, no colour).
-template <int DP, bool BF16, bool COLOR, bool DENSE>
+// DENSE: 0 bit walk, 1 dense tile with units of <= 32 queries, 2 dense tile
+// with units of <= 64 queries (BF16 labels).
+template <int DP, bool BF16, bool COLOR, int DENSE>
 __host__ __device__ constexpr int unit_smem_words() {
-    if constexpr (DENSE) return DenseSmem<(DP > 0 ? DP : 8), !BF16>::WORDS;
+    if constexpr (DENSE > 0) return DenseSmem<(DP > 0 ? DP : 8), !BF16, DENSE == 2 ? 64 : 32>::WORDS;
     else return warp_smem_words<DP, BF16, COLOR>();
 }
 
-template <int DP, bool BF16, bool COLOR, bool DENSE>
+template <int DP, bool BF16, bool COLOR, int DENSE>
 __device__ __forceinline__ void run_unit(const PairArgs& A, int k0, float* wb, int lane) {
-    if constexpr (DENSE && DP > 0 && !COLOR) pair_unit_dense<DP, !BF16>(A, k0, wb, lane);
+    if constexpr (DENSE > 0 && DP > 0 && !COLOR) pair_unit_dense<DP, !BF16, DENSE == 2 ? 64 : 32>(A, k0, wb, lane);
     else pair_unit<DP, BF16, COLOR>(A, k0, wb, lane);
 }
 
-template <int DP, bool BF16, bool COLOR, bool DENSE>
+template <int DP, bool BF16, bool COLOR, int DENSE>
 __global__ void __launch_bounds__(PAIR_T, DENSE ? RK_DENSE_MINB : ((BF16 && DP > 0) ? 2 : RK_PAIR_MINB))
 k_pairs(const int* __restrict__ unit_start, const int* __restrict__ n_units, int* unit_counter,
         const PairArgs A, const int* done) {
@@ -1488,7 +1546,7 @@ k_pairs(const int* __restrict__ unit_start, const int* __restrict__ n_units, int
 // the job by binary search over the prefix, and run the unit with that
 // job's arrays.  Every job adds into its own fixed-point accumulators, so a
 // problem's results do not depend on which other problems share the launch.
-template <int DP, bool BF16, bool COLOR, bool DENSE>
+template <int DP, bool BF16, bool COLOR, int DENSE>
 __global__ void __launch_bounds__(PAIR_T, DENSE ? RK_DENSE_MINB : ((BF16 && DP > 0) ? 2 : RK_PAIR_MINB))
 k_pairs_multi(const PairJob* __restrict__ jobs, int n_jobs, int* unit_counter) {
     __shared__ int s_pref[MAX_PAIR_JOBS + 1];
@@ -1724,8 +1782,8 @@ k_emit_pairs(const int* __restrict__ unit_start, const int* __restrict__ n_units
              const int* __restrict__ cell_start, const float4* __restrict__ pts4, GridParams gp,
              int edge_sel, const int* __restrict__ perm_local, long long capacity, int uq,
              int* __restrict__ i_out, int* __restrict__ j_out, unsigned long long* n_out) {
-    __shared__ float4 s_m[PAIR_T / 32][UQ];
-    __shared__ int s_j[PAIR_T / 32][UQ];
+    __shared__ float4 s_m[PAIR_T / 32][64];
+    __shared__ int s_j[PAIR_T / 32][64];
     __shared__ int s_rows[PAIR_T / 32][40];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
@@ -1742,7 +1800,7 @@ k_emit_pairs(const int* __restrict__ unit_start, const int* __restrict__ n_units
         const uint32_t key0 = kq0 >> gp.key_sub;
         const int e = find_edge_bin(edges, E, key0);
         if (e != edge_sel) continue;
-        const int qcount = unit_queries(qkey, Q, k0, kq0, lane, uq, gp.key_sub);
+        const int qcount = unit_queries64(qkey, Q, k0, kq0, lane, uq, gp.key_sub);
         const FrameDev& Fa = frames[edges[e].a];
         const int dx0 = Fa.dim[0], dy0 = Fa.dim[1], dz0 = Fa.dim[2];
         const int cell = (int)(key0 - edges[e].bin_off);
@@ -1818,6 +1876,15 @@ inline bool dense_path(const GridParams& gp) {
 #endif
 }
 
+template <int DP, bool BF16, bool COLOR, int DENSE>
+void launch_k_pairs(const PairLaunch& L, const PairArgs& A) {
+    const size_t smem = sizeof(float) * (PAIR_T / 32) * unit_smem_words<DP, BF16, COLOR, DENSE>();
+    static int resident = 0;   // opt in to > 48 KB and size the persistent grid, once per instantiation
+    const int r = pair_blocks_per_sm(k_pairs<DP, BF16, COLOR, DENSE>, smem, &resident);
+    k_pairs<DP, BF16, COLOR, DENSE><<<pair_grid(L.num_sms, r, L.ctas_per_sm), PAIR_T, smem, L.stream>>>(
+        L.unit_start, L.n_units, L.unit_counter, A, L.done);
+}
+
 template <int DP, bool BF16, bool COLOR>
 void run_pairs(const PairLaunch& L, const PairArgs& A) {
     if (A.gp.top_k > 0) {
@@ -1831,39 +1898,46 @@ void run_pairs(const PairLaunch& L, const PairArgs& A) {
     }
     if constexpr (DP > 0 && !COLOR) {
         if (dense_path(A.gp)) {
-            const size_t smem = sizeof(float) * (PAIR_T / 32) * unit_smem_words<DP, BF16, COLOR, true>();
-            static int resident = 0;
-            const int r = pair_blocks_per_sm(k_pairs<DP, BF16, COLOR, true>, smem, &resident);
-            k_pairs<DP, BF16, COLOR, true><<<pair_grid(L.num_sms, r, L.ctas_per_sm), PAIR_T, smem, L.stream>>>(
-                L.unit_start, L.n_units, L.unit_counter, A, L.done);
+            if constexpr (BF16) {
+                if (A.uq > 32) {
+                    launch_k_pairs<DP, BF16, COLOR, 2>(L, A);
+                    return;
+                }
+            }
+            launch_k_pairs<DP, BF16, COLOR, 1>(L, A);
             return;
         }
     }
-    const size_t smem = sizeof(float) * (PAIR_T / 32) * warp_smem_words<DP, BF16, COLOR>();
-    static int resident = 0;   // opt in to > 48 KB and size the persistent grid, once
-    const int r = pair_blocks_per_sm(k_pairs<DP, BF16, COLOR, false>, smem, &resident);
-    k_pairs<DP, BF16, COLOR, false><<<pair_grid(L.num_sms, r, L.ctas_per_sm), PAIR_T, smem, L.stream>>>(
-        L.unit_start, L.n_units, L.unit_counter, A, L.done);
+    launch_k_pairs<DP, BF16, COLOR, 0>(L, A);
 }
 
+template <int DP, bool BF16, bool COLOR, int DENSE>
+void launch_k_pairs_multi(const PairJob* jobs, int n_jobs, int* counter, int num_sms, int ctas_per_sm,
+                          cudaStream_t st) {
+    const size_t smem = sizeof(float) * (PAIR_T / 32) * unit_smem_words<DP, BF16, COLOR, DENSE>();
+    static int resident = 0;   // opt in to > 48 KB and size the persistent grid, once per instantiation
+    const int r = pair_blocks_per_sm(k_pairs_multi<DP, BF16, COLOR, DENSE>, smem, &resident);
+    k_pairs_multi<DP, BF16, COLOR, DENSE><<<pair_grid(num_sms, r, ctas_per_sm), PAIR_T, smem, st>>>(
+        jobs, n_jobs, counter);
+}
+
+// max_uq: the largest unit size among the jobs
 template <int DP, bool BF16, bool COLOR>
 void run_pairs_multi(const PairJob* jobs, int n_jobs, int* counter, int num_sms, int ctas_per_sm, bool dense,
-                     cudaStream_t st) {
+                     int max_uq, cudaStream_t st) {
     if constexpr (DP > 0 && !COLOR) {
         if (dense) {
-            const size_t smem = sizeof(float) * (PAIR_T / 32) * unit_smem_words<DP, BF16, COLOR, true>();
-            static int resident = 0;
-            const int r = pair_blocks_per_sm(k_pairs_multi<DP, BF16, COLOR, true>, smem, &resident);
-            k_pairs_multi<DP, BF16, COLOR, true><<<pair_grid(num_sms, r, ctas_per_sm), PAIR_T, smem, st>>>(
-                jobs, n_jobs, counter);
+            if constexpr (BF16) {
+                if (max_uq > 32) {
+                    launch_k_pairs_multi<DP, BF16, COLOR, 2>(jobs, n_jobs, counter, num_sms, ctas_per_sm, st);
+                    return;
+                }
+            }
+            launch_k_pairs_multi<DP, BF16, COLOR, 1>(jobs, n_jobs, counter, num_sms, ctas_per_sm, st);
             return;
         }
     }
-    const size_t smem = sizeof(float) * (PAIR_T / 32) * warp_smem_words<DP, BF16, COLOR>();
-    static int resident = 0;
-    const int r = pair_blocks_per_sm(k_pairs_multi<DP, BF16, COLOR, false>, smem, &resident);
-    k_pairs_multi<DP, BF16, COLOR, false><<<pair_grid(num_sms, r, ctas_per_sm), PAIR_T, smem, st>>>(
-        jobs, n_jobs, counter);
+    launch_k_pairs_multi<DP, BF16, COLOR, 0>(jobs, n_jobs, counter, num_sms, ctas_per_sm, st);
 }
 
 // Calls F.template operator()<DP, BF16>() for the label layout of gp
@@ -1920,7 +1994,7 @@ void launch_query_gather(const uint32_t* qkey_sorted, const int* qval_sorted, co
 void launch_units(const uint32_t* qkey_sorted, const int* bin_first, long long Q, int uq, int sub, int* unit_start,
                   int* n_units, const int* done, cudaStream_t st) {
     if (Q <= 0) return;
-    if (uq < 1 || uq > UQ) uq = UQ;
+    if (uq < 1 || uq > 64) uq = UQ;
     k_units<<<blocks_for(Q, 256), 256, 0, st>>>(qkey_sorted, bin_first, Q, uq, sub, unit_start, n_units, done);
     count_launch();
 }
@@ -1940,27 +2014,30 @@ struct MultiLaunch {
     int n_jobs;
     bool color;
     bool dense;
+    int max_uq;
     int* counter;
     int num_sms, ctas_per_sm;
     cudaStream_t st;
     template <int DP, bool BF16>
     void operator()() const {
-        if (color) run_pairs_multi<DP, BF16, true>(jobs, n_jobs, counter, num_sms, ctas_per_sm, dense, st);
-        else run_pairs_multi<DP, BF16, false>(jobs, n_jobs, counter, num_sms, ctas_per_sm, dense, st);
+        if (color) run_pairs_multi<DP, BF16, true>(jobs, n_jobs, counter, num_sms, ctas_per_sm, dense, max_uq, st);
+        else run_pairs_multi<DP, BF16, false>(jobs, n_jobs, counter, num_sms, ctas_per_sm, dense, max_uq, st);
     }
 };
 }  // namespace
+
+int pair_unit_max(const GridParams& gp) { return (dense_path(gp) && gp.sem_bf16) ? 64 : UQ; }
 
 void launch_pairs(const PairLaunch& L, const PairArgs& A) {
     if (A.Q <= 0) return;
     if (with_label_layout(A.gp, SingleLaunch{L, A})) count_launch();
 }
 
-bool launch_pairs_multi(const PairJob* jobs, int n_jobs, const GridParams& layout, int* counter, int num_sms,
-                        int ctas_per_sm, cudaStream_t st) {
+bool launch_pairs_multi(const PairJob* jobs, int n_jobs, const GridParams& layout, int max_uq, int* counter,
+                        int num_sms, int ctas_per_sm, cudaStream_t st) {
     if (n_jobs <= 0 || n_jobs > MAX_PAIR_JOBS || layout.top_k > 0) return false;
     const bool ok = with_label_layout(layout, MultiLaunch{jobs, n_jobs, layout.color != 0, dense_path(layout),
-                                                          counter, num_sms, ctas_per_sm, st});
+                                                          max_uq, counter, num_sms, ctas_per_sm, st});
     if (ok) count_launch();
     return ok;
 }
@@ -1972,7 +2049,7 @@ void launch_emit_pairs(const int* unit_start, const int* n_units, int* unit_coun
                        int* i_out, int* j_out, unsigned long long* n_out, int num_sms,
                        cudaStream_t st) {
     if (Q <= 0) return;
-    if (uq < 1 || uq > UQ) uq = UQ;
+    if (uq < 1 || uq > 64) uq = UQ;
     k_emit_pairs<<<num_sms * 2, PAIR_T, 0, st>>>(unit_start, n_units, unit_counter, qkey, slots, Q, edges, E,
                                                  frames, cell_start, pts4, gp, edge_sel, perm_local, capacity, uq,
                                                  i_out, j_out, n_out);

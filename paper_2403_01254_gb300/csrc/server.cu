@@ -403,7 +403,7 @@ bool rkhsba_server::tuning_for(Req* r, rkhsba_tuning* t) {
 // neighbour-limited variant (its own kernel) run whole iterations on their
 // streams.
 void rkhsba_server::issue_round(const std::vector<Req*>& batch, int n_iter) {
-    struct Group { int key; GridParams layout; int ctas; std::vector<Req*> reqs; };
+    struct Group { int key; GridParams layout; int ctas; int max_uq; std::vector<Req*> reqs; };
     std::vector<Group> groups;
     for (Req* r : batch) {
         const GridParams g = ctx_layout(r->ctx);
@@ -421,10 +421,11 @@ void rkhsba_server::issue_round(const std::vector<Req*>& batch, int n_iter) {
         for (Group& x : groups)
             if (x.key == key && (int)x.reqs.size() < MAX_PAIR_JOBS) grp = &x;
         if (!grp) {
-            groups.push_back({key, g, ctx_tune_ctas(r->ctx), {}});
+            groups.push_back({key, g, ctx_tune_ctas(r->ctx), 0, {}});
             grp = &groups.back();
         }
         grp->reqs.push_back(r);
+        grp->max_uq = std::max(grp->max_uq, ctx_tune_uq(r->ctx));
     }
     if (groups.empty()) return;
     RoundSlot* rs_free = nullptr;
@@ -455,7 +456,7 @@ void rkhsba_server::issue_round(const std::vector<Req*>& batch, int n_iter) {
             const int n = (int)grp.reqs.size();
             for (Req* r : grp.reqs) cudaStreamWaitEvent(rst, r->ev, 0);
             cudaMemsetAsync(counters + gi, 0, sizeof(int), rst);
-            launch_pairs_multi(jobs + off, n, grp.layout, counters + gi, num_sms, grp.ctas, rst);
+            launch_pairs_multi(jobs + off, n, grp.layout, grp.max_uq, counters + gi, num_sms, grp.ctas, rst);
             off += n;
             ++gi;
         }

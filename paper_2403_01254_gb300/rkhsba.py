@@ -373,12 +373,12 @@ def rkhsba_autotune(n_points, xyz, sem, rgb, edges, params, poses, stream=None, 
     else:
         px, ps, pr = (None if a is None else a.ctypes.data for a in (xyz, sem, rgb))
     best = Tuning()
-    table = (Tuning * 16)()
+    table = (Tuning * 32)()
     nt = C.c_int32()
     _check(lib.rkhsba_autotune(K, _ptr(n, C.c_int64), px, ps, pr, len(e) // 2, _ptr(e, C.c_int32),
                                C.byref(params), int(bool(on_device)), _ptr(T, C.c_double), stream, int(reps),
-                               C.byref(best), table, 16, C.byref(nt)))
-    return _tuning_dict(best), [_tuning_dict(table[i]) for i in range(min(nt.value, 16))]
+                               C.byref(best), table, 32, C.byref(nt)))
+    return _tuning_dict(best), [_tuning_dict(table[i]) for i in range(min(nt.value, 32))]
 
 
 def rkhsba_launch_count():

@@ -107,3 +107,60 @@ def test_tuning_rejects_bad_values(pk):
         g.close()
     with pytest.raises(pk.RkhsbaError):
         pk.Problem.from_scene(prob, cell_scale=0.5)
+
+
+@pytest.mark.parametrize("uq", [64, 48, 33])
+def test_units_of_up_to_64_queries_match_the_oracle(pk, uq):
+    # BF16 labels without colour take the dense tile kernel, whose units hold
+    # up to 64 queries of one home cell (four m tiles); a dense scene gives
+    # home cells with more than 32 queries
+    prob = scenes.window_problem(seed=75, window=3, n_points=12000)
+    T = prob["poses0"]
+    ref = O.evaluate(prob, T)
+    g = pk.Problem.from_scene(prob)
+    try:
+        g.set_tuning(uq, 0)
+        out = g.eval(T, want_H=True, want_blocks=True)
+        gi, gj, n = g.edge_pairs(T, 1)
+    finally:
+        g.close()
+    assert np.abs(out["edge_pairs"] - ref["edge_pairs"]).sum() <= 3
+    assert abs(out["loss"] - ref["loss"]) <= LOSS_TOL * abs(ref["loss"])
+    assert _reln(out["grad"], ref["grad"]) <= GRAD_TOL
+    assert _reln(out["H"], ref["H"]) <= H_TOL
+    # the pair list (same units) holds every pair of the edge once
+    ri, rj = O.edge_pairs(prob, T, 1)
+    got = set(zip(gi.tolist(), gj.tolist()))
+    assert len(got) == len(gi) and len(got ^ set(zip(ri.tolist(), rj.tolist()))) <= 3
+
+
+def test_64_query_units_only_where_the_kernel_takes_them(pk):
+    bf = scenes.lidar_street_problem(seed=76, n_frames=2, n_points=2000, sem_bf16=1)
+    fp = scenes.lidar_street_problem(seed=76, n_frames=2, n_points=2000, sem_bf16=0)
+    g = pk.Problem.from_scene(bf)
+    try:
+        g.set_tuning(64, 0)
+        assert g.tuning()["unit_queries"] == 64
+        with pytest.raises(pk.RkhsbaError):
+            g.set_tuning(65, 0)
+    finally:
+        g.close()
+    g = pk.Problem.from_scene(fp)
+    try:
+        with pytest.raises(pk.RkhsbaError):
+            g.set_tuning(64, 0)
+    finally:
+        g.close()
+
+
+def test_autotune_with_bf16_labels_tries_64_query_units(pk):
+    from paper_2403_01254_gb300 import rkhsba as rb
+    prob = scenes.window_problem(seed=77, window=3, n_points=5000)
+    n = np.array([len(x) for x in prob["xyz"]], np.int64)
+    xyz = np.ascontiguousarray(np.concatenate(prob["xyz"]))
+    sem = np.ascontiguousarray(np.concatenate(prob["sem"]).astype(np.float32))
+    params = pk.make_params(0.3, sem_dim=sem.shape[1], sem_bf16=1)
+    best, table = rb.rkhsba_autotune(n, xyz, sem, None, prob["edges"], params, prob["poses0"], reps=2)
+    assert len(table) == 18
+    assert {t["unit_queries"] for t in table} == {16, 32, 64}
+    assert (table[0]["cell_scale"], table[0]["unit_queries"], table[0]["ctas_per_sm"]) == (1.0, 32, 0)
