@@ -268,7 +268,8 @@ def _flat_inputs(prob):
         edges=np.asarray(prob["edges"], np.int32))
 
 
-def measure_device(pk, rb, prob, steps, warmup, dev, stream, flush, world=1, clocks_index=None, autotune=False):
+def measure_device(pk, rb, prob, steps, warmup, dev, stream, flush, world=1, clocks_index=None, autotune=False,
+                   unit_queries=None):
     """Time `steps` bench steps of the resident problem with CUDA events on
     the library's stream (L2 flushed between steps, outside the events);
     phase times from the library's own events.  With autotune the library's
@@ -297,6 +298,11 @@ def measure_device(pk, rb, prob, steps, warmup, dev, stream, flush, world=1, clo
                                   rgb_d.data_ptr() if f["color"] else None, f["edges"], params, stream.cuda_stream)
     if tuning:
         rb.rkhsba_set_tuning(ctx, tuning["chosen"]["unit_queries"], tuning["chosen"]["ctas_per_sm"])
+    elif unit_queries:
+        # a fixed setting (e.g. the one the autotuner picks, for a profiler run)
+        rb.rkhsba_set_tuning(ctx, unit_queries, 0)
+        tuning = dict(chosen=dict(cell_scale=1.0, unit_queries=unit_queries, ctas_per_sm=0, ms=None), table=None,
+                      timed="set with --unit-queries, not autotuned")
 
     def step():
         rb.rkhsba_rebuild(ctx)
@@ -427,7 +433,7 @@ def ours(args, rank, world, local_rank):
     stream = torch.cuda.Stream(device=dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     m = measure_device(pk, rb, prob, args.steps, args.warmup, dev, stream, flush, world, clocks_index=local_rank,
-                       autotune=not args.no_autotune)
+                       autotune=not args.no_autotune and not args.unit_queries, unit_queries=args.unit_queries)
     value, ms_max = replica_throughput(m["ms"], m["pairs_per_step"], args.steps, world, dev)
     clk = m["clocks"]
     sm_max = (clk or {}).get("sm_max_mhz") or 2070.0
@@ -710,6 +716,8 @@ def main():
     ap.add_argument("--no-functions", action="store_true")
     ap.add_argument("--no-secondary", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="measure the default pair-stage setting")
+    ap.add_argument("--unit-queries", type=int, default=0,
+                    help="measure this unit size (queries per warp unit) instead of autotuning")
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(WORKLOADS),
                     help="other workloads of the paper's shapes (the driver uses the default)")
     args = ap.parse_args()
