@@ -1026,7 +1026,10 @@ __device__ __forceinline__ void pair_unit_dense(const PairArgs& A, int k0, float
         qhead = (qhead + nb) & (CQ_N - 1);
         qlen -= nb;
         __syncwarp();
-#pragma unroll
+        // m tiles one after another, not unrolled: the smaller loop body ran
+        // faster (LiDAR 0.344 -> 0.284 ms, window 2.00 -> 1.85 ms, mapping
+        // within 1%)
+#pragma unroll 1
         for (int mt = 0; mt < L::MAXQ / 16; ++mt) {
             if (mt >= n_mt) break;
             // query-side A fragments of the label products: rows 16 mt ..
