@@ -44,13 +44,16 @@ TRAFFIC_FILE = os.path.join(ROOT, "profiles", "k_pairs_dram_traffic.json")
 
 
 def pair_kernel_digest():
-    """SHA-256 over the sources of the pair kernel: a recorded DRAM traffic
-    figure is reported only while the kernel is the one it was taken on."""
+    """SHA-256 over the code of the pair kernel's sources (line comments and
+    whitespace removed): a recorded DRAM traffic figure is reported only while
+    the kernel is the one it was taken on."""
     import hashlib
+    import re
     h = hashlib.sha256()
     for rel in PAIR_SOURCES:
-        with open(os.path.join(ROOT, rel), "rb") as f:
-            h.update(f.read())
+        with open(os.path.join(ROOT, rel), encoding="utf-8") as f:
+            code = re.sub(r"//[^\n]*", "", f.read())
+        h.update(re.sub(r"\s+", "", code).encode())
     return h.hexdigest()
 
 

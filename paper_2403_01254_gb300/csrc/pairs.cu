@@ -6,18 +6,24 @@
 // |T_a x - T_b y| = |x - T_ab y|) and keyed by the frame-a grid cell holding
 // it.  A stable radix sort groups the queries by home cell (order inside a
 // cell = frame-b order, so results do not depend on thread timing), and the
-// groups are cut into units of <= 32 queries.  A warp takes one unit, stages
-// its queries in shared memory and streams the candidates of the 27
-// surrounding cells through its lanes (one candidate per lane).  Every lane
-// tests its candidate against all queries, keeps a bit mask of the pairs
-// inside r_c, and walks its own set bits to form the weight
+// groups are cut into units of <= 32 (or 64) queries.  A warp takes one unit,
+// stages its queries in shared memory and streams the candidates of the 27
+// surrounding cells, 32 at a time, through a box test against the unit's
+// queries.  For every candidate x query pair inside r_c the weight
 //     w = <l_i, l_j> * k_c(c_i, c_j) * exp(-|d|^2 / (2 ell^2))      Eq. (irls_weight)
-// and the sums W = sum w, D = sum w d, Q = sum w d d^T (d = x - y').  With
-// y' = x - d these fold into the 28 edge moments (layout in common.cuh),
-// which fix the loss, the gradient of Eq. (inner_product_reformat) and the
-// Gauss-Newton blocks of Eq. (irls_final).  Each lane's moments are rounded to
-// 64-bit fixed point before any cross-lane sum, so edge totals are exact
-// integer sums, independent of which warp ran which unit.
+// enters the sums that fix the 28 edge moments (layout in common.cuh), and
+// through them the loss, the gradient of Eq. (inner_product_reformat) and the
+// Gauss-Newton blocks of Eq. (irls_final).  Two unit bodies do this:
+//   * the dense tile unit (no colour, no pruning): every element of the
+//     32-candidate x unit tile in MMA fragment layout, label products and
+//     per-query moment sums on the tensor cores (see "dense tile path");
+//   * the bit-walk unit (colour, semantic pruning): lane = candidate, a bit
+//     mask of its pairs inside r_c, each lane walking its own set bits and
+//     folding W = sum w, D = sum w d, Q = sum w d d^T (d = x - y') per
+//     candidate.
+// Each lane's moments are rounded to 64-bit fixed point before any
+// cross-lane sum, so edge totals are exact integer sums, independent of which
+// warp ran which unit.
 //
 // No FP64 arithmetic runs per query: the frame-a position of a frame-b cell
 // centre comes from a per-edge affine map held as double-float pairs, evaluated
@@ -645,13 +651,15 @@ __device__ __forceinline__ void label_gram_bf16(const unsigned* __restrict__ sem
 }
 
 // ------------------------------------------------------ dense tile path ----
-// BF16 labels without colour or pruning.  On the dense workloads most of a
-// batch's 32 x 32 candidate x query tests pass the cutoff (about two thirds
-// after the box cull), so instead of walking each lane's set bits the warp
-// evaluates the whole tile in MMA fragment layout and moves the moment sums
-// onto the tensor cores:
-//   1. S = L_q L_c^T, the tile's label products (BF16 MMA; rows are the
-//      unit's queries, columns the batch's candidates);
+// Labels without colour or pruning.  On the LiDAR workloads half to two
+// thirds of a batch's candidate x query tests pass the cutoff after the box
+// cull, so instead of walking each lane's set bits the warp evaluates the
+// whole tile in MMA fragment layout and moves the moment sums onto the tensor
+// cores:
+//   1. S = L_q L_c^T, the tile's label products (rows are the unit's queries
+//      in m tiles of 16, columns the batch's 32 candidates): BF16 labels as
+//      stored; FP32 labels scaled by a power of two and split into FP16
+//      hi + lo parts, S = hi*hi + hi*lo + lo*hi;
 //   2. per element: the exact cutoff test of the bit-walk kernel (same FP32
 //      formula, so the same pair set), w = s 2^(kg |d|^2) (one ex2), and 0
 //      outside r_c; |d|^2 = |y|^2 - 2 x.y + |x|^2;
