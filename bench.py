@@ -111,11 +111,11 @@ def workload(name=None):
 def _oracle_edges(prob, name):
     """Frame pairs of the CPU samples: for the mapping workload the first
     odometry edge (0,1) and the first loop-closure edge (0,16); otherwise the
-    first two edges."""
+    first two edges (the only one of a single-edge problem)."""
     E = np.asarray(prob["edges"])
     if name.startswith("mapping"):
         return [0, int(np.nonzero(E[:, 1] - E[:, 0] > 7)[0][0])]
-    return [0, 1]
+    return [0, 1] if len(E) > 1 else [0]
 
 
 def _truncated(prob, e, n_b):
