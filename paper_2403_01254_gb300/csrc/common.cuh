@@ -117,7 +117,7 @@ struct PairArgs {
     const float4* col4;       // colours in the same order, or NULL
     long long* acc;           // [E][ACC_N] fixed-point moments
     int E;
-    int uq;                   // queries per unit (1..32)
+    int uq;                   // queries per unit (1..32; up to 64 for the dense kernel with BF16 labels)
     GridParams gp;
 };
 

@@ -76,7 +76,7 @@ struct rkhsba_ctx {
     float4* d_qrec = nullptr;          // per query: offset from home centre, point index
     float4* d_slots = nullptr;         // the same in sorted order
     int* d_bin_first = nullptr;        // first sorted query of each home cell
-    int* d_unit_start = nullptr;       // units of <= 32 queries of one home cell
+    int* d_unit_start = nullptr;       // units of <= tune_uq queries of one home cell
     int* d_ucount = nullptr;           // [2]: number of units, unit counter
     const uint32_t* q_sorted_key = nullptr;
     long long* d_acc = nullptr;
