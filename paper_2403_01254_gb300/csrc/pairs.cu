@@ -372,9 +372,15 @@ constexpr int PAIR_T = 256;
 #ifndef RK_PAIR_MINB
 #define RK_PAIR_MINB 2              // resident CTAs per SM the register budget targets
 #endif
-#ifndef RK_DENSE_MINB
-#define RK_DENSE_MINB 2             // resident CTAs per SM of the dense tile kernels
-#endif
+// Resident CTAs per SM the register budget of a dense tile kernel targets:
+// three for BF16 rows of <= 24 values and units of <= 32 queries (75 KB of
+// shared memory per CTA, so three fit; 80 registers with a few bytes of
+// spills: window workload 1.85 -> 1.73 ms per evaluation), else two (the
+// larger layouts fit only two CTAs' shared memory).
+template <int DP, bool BF16, int DENSE>
+__host__ __device__ constexpr int dense_min_blocks() {
+    return (BF16 && DENSE == 1 && DP <= 24) ? 3 : 2;
+}
 constexpr int UQ = UNIT_Q;          // queries per unit: one 32-bit mask word
 static_assert(UQ == 32, "units hold 32 queries");
 
@@ -1533,7 +1539,8 @@ __device__ __forceinline__ void run_unit(const PairArgs& A, int k0, float* wb, i
 }
 
 template <int DP, bool BF16, bool COLOR, int DENSE>
-__global__ void __launch_bounds__(PAIR_T, DENSE ? RK_DENSE_MINB : ((BF16 && DP > 0) ? 2 : RK_PAIR_MINB))
+__global__ void __launch_bounds__(PAIR_T, DENSE ? dense_min_blocks<DP, BF16, DENSE>()
+                                                  : ((BF16 && DP > 0) ? 2 : RK_PAIR_MINB))
 k_pairs(const int* __restrict__ unit_start, const int* __restrict__ n_units, int* unit_counter,
         const PairArgs A, const int* done) {
     if (done && *done) return;
@@ -1558,7 +1565,8 @@ k_pairs(const int* __restrict__ unit_start, const int* __restrict__ n_units, int
 // job's arrays.  Every job adds into its own fixed-point accumulators, so a
 // problem's results do not depend on which other problems share the launch.
 template <int DP, bool BF16, bool COLOR, int DENSE>
-__global__ void __launch_bounds__(PAIR_T, DENSE ? RK_DENSE_MINB : ((BF16 && DP > 0) ? 2 : RK_PAIR_MINB))
+__global__ void __launch_bounds__(PAIR_T, DENSE ? dense_min_blocks<DP, BF16, DENSE>()
+                                                  : ((BF16 && DP > 0) ? 2 : RK_PAIR_MINB))
 k_pairs_multi(const PairJob* __restrict__ jobs, int n_jobs, int* unit_counter) {
     __shared__ int s_pref[MAX_PAIR_JOBS + 1];
     extern __shared__ float4 smem4[];
