@@ -34,6 +34,13 @@ def _problems():
         out.append(p)
     out.append(scenes.tiny_problem(seed=77, n_frames=3, n=300, extent=1.0, ell=0.15, color=True))
     out[-1]["params"] = dict(out[-1]["params"], max_iters=25)
+    # BF16 labels: their own group of the batched rounds (dense kernel at
+    # three CTAs per SM)
+    for k, (K, n) in enumerate([(3, 3000), (2, 5000)]):
+        p = scenes.lidar_street_problem(seed=920 + k, n_frames=K, n_points=n, max_deg=3.0, max_trans=0.1,
+                                        sem_bf16=1)
+        p["params"] = dict(p["params"], max_iters=25)
+        out.append(p)
     return out
 
 
