@@ -338,3 +338,23 @@ def test_solve_parity_large_system(pk):
     assert dr <= POSE_TOL and dt <= POSE_TOL, (dr, dt, info, ref["status"])
     moved = max(O.pose_error(a, b)[1] for a, b in zip(ref["poses"], init))
     assert moved > 100 * POSE_TOL
+
+
+@pytest.mark.parametrize("bf16", [False, True])
+@pytest.mark.parametrize("label_scale,ell", [(1e3, 0.15), (1e-3, 0.15), (1.0, 40.0), (1.0, 0.002)])
+def test_dense_kernel_scaling_extremes(pk, bf16, label_scale, ell):
+    """The dense kernel carries weights, features and (FP32) label parts in
+    FP16 under power-of-two scales chosen from the label norms and the cell
+    size; labels far from unit norm and lengthscales far from the workloads'
+    must still match the oracle."""
+    prob = scenes.tiny_problem(seed=91, n_frames=3, n=300, extent=1.0, ell=0.15)
+    geo = ell / 0.15
+    prob["xyz"] = [x * geo for x in prob["xyz"]]
+    prob["poses0"] = prob["poses0"].copy()
+    prob["poses0"][:, :3, 3] *= geo
+    lab = [np.asarray(s, np.float32) * np.float32(label_scale) for s in prob["sem"]]
+    if bf16:
+        lab = [scenes.round_to_bf16(s) for s in lab]
+    prob["sem"] = lab
+    prob["params"] = dict(prob["params"], ell=ell, sem_bf16=int(bf16))
+    check_eval(pk, prob, prob["poses0"])
