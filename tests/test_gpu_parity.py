@@ -51,11 +51,13 @@ def _band_pairs(prob, poses, e):
     return set(zip(i[m].tolist(), j[m].tolist()))
 
 
-def check_eval(pk, prob, poses, edge_subset=None, n_band_max=None):
+def check_eval(pk, prob, poses, edge_subset=None, n_band_max=None, uq=None):
     sub = prob if edge_subset is None else dict(prob, edges=np.asarray(prob["edges"])[edge_subset])
     ref = O.evaluate(sub, poses)
     g = pk.Problem.from_scene(sub)
     try:
+        if uq:
+            g.set_tuning(uq, 0)
         out = g.eval(poses, want_H=True, want_blocks=True)
     finally:
         g.close()
@@ -85,13 +87,17 @@ def test_tiny_eval_parity(pk, variant):
     check_eval(pk, prob, prob["poses0"])
 
 
-def test_ragged_sizes_and_many_tiles(pk):
+@pytest.mark.parametrize("bf16,uq", [(0, None), (1, 64)])
+def test_ragged_sizes_and_many_tiles(pk, bf16, uq):
     prob = scenes.tiny_problem(seed=32, n_frames=3, n=777, extent=2.5, ell=0.1)
     prob["xyz"][1] = prob["xyz"][1][:531]
     prob["sem"][1] = prob["sem"][1][:531]
     prob["xyz"][2] = prob["xyz"][2][:1]
     prob["sem"][2] = prob["sem"][2][:1]
-    check_eval(pk, prob, prob["poses0"])
+    if bf16:
+        prob["sem"] = [scenes.round_to_bf16(s) for s in prob["sem"]]
+        prob["params"] = dict(prob["params"], sem_bf16=1)
+    check_eval(pk, prob, prob["poses0"], uq=uq)
 
 
 def test_pair_sets_bit_exact_outside_band(pk):
@@ -153,17 +159,22 @@ def test_full_size_gauge_invariance(pk):
 
 
 # --------------------------------------------------------------- edge cases -
-def test_degenerate_inputs(pk):
+@pytest.mark.parametrize("bf16,uq", [(0, None), (1, 32), (1, 64), (1, 7)])
+def test_degenerate_inputs(pk, bf16, uq):
+    # one cell holding 500 points (home cells of many full units), an empty
+    # frame, a far frame; FP32 labels and BF16 labels at several unit sizes
     rng = np.random.default_rng(7)
     blob = np.full((500, 3), 0.25) + rng.normal(scale=1e-4, size=(500, 3))   # one cell
     far = rng.uniform(100, 101, size=(50, 3))
     lab = scenes.dirichlet_labels(rng, rng.integers(0, 4, 500), 4)
+    if bf16:
+        lab = scenes.round_to_bf16(lab)
     prob = dict(xyz=[blob, blob[:200] + 0.01, np.zeros((0, 3)), far],
                 sem=[lab, lab[:200], np.zeros((0, 4), np.float32), lab[:50]], rgb=None,
                 edges=np.array([[0, 1], [1, 2], [0, 3], [2, 3]], np.int32),
-                params=dict(ell=0.1, cutoff_mult=3.0, sigma=1.0, ell_color=0.0, sem_bf16=0))
+                params=dict(ell=0.1, cutoff_mult=3.0, sigma=1.0, ell_color=0.0, sem_bf16=bf16))
     T = np.stack([np.eye(4)] * 4)
-    out, ref = check_eval(pk, prob, T)
+    out, ref = check_eval(pk, prob, T, uq=uq)
     assert out["edge_pairs"][1] == 0 and out["edge_pairs"][2] == 0 and out["edge_pairs"][3] == 0
 
 
