@@ -352,6 +352,42 @@ def measure_device(pk, rb, prob, steps, warmup, dev, stream, flush, world=1, clo
                 flat=f, tuning=tuning, params=params)
 
 
+def measured_hbm_gbs():
+    """The measured copy bandwidth of the GB300s (MEASURED_PEAKS.json),
+    else the profiling recipe's fallback figure, and which one it is."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured"
+    except (OSError, ValueError, KeyError, TypeError):
+        return 6800.0, "fallback"
+
+
+def label_row_bytes(sem_dim, bf16):
+    """Bytes of one stored label row (FP32 rows padded to 4..32 floats, BF16
+    rows to 8..32 values)."""
+    if sem_dim <= 0:
+        return 0
+    pads = (8, 16, 24, 32) if bf16 else (4, 8, 12, 16, 20, 24, 32)
+    pad = next((p for p in pads if sem_dim <= p), pads[-1])
+    return pad * (2 if bf16 else 4)
+
+
+def pair_bounds(flat, pair_terms_per_launch, peak_tflops):
+    """Both roofline bounds of the pair kernel in pair-terms/s: FP32 issue
+    (peak / 110 flops per pair-term) and HBM (every point of both frames of
+    every edge read once per launch: 16 B of position + its label row, at the
+    measured copy bandwidth).  The lower one bounds the kernel."""
+    n = flat["n_points"]
+    E = np.asarray(flat["edges"])
+    row = 16 + label_row_bytes(flat["sem_dim"], flat["P"].get("sem_bf16", 0)) + (16 if flat["color"] else 0)
+    alg_bytes = float(sum(int(n[a]) + int(n[b]) for a, b in E)) * row
+    gbs, src = measured_hbm_gbs()
+    hbm = pair_terms_per_launch / (alg_bytes / (gbs * 1e9)) if alg_bytes > 0 else None
+    fp32 = peak_tflops * 1e12 / FLOPS_PER_PAIR
+    return dict(fp32_pair_terms_per_s=fp32, hbm_pair_terms_per_s=hbm, hbm_gbs=gbs, hbm_source=src,
+                algorithmic_bytes_per_launch=alg_bytes, lower="fp32" if hbm is None or fp32 <= hbm else "hbm")
+
+
 def roofline_of(name, m, steps, dev, sm_max):
     """Roofline of the dominant kernel (the pair kernel, bound by instruction
     issue): achieved = algorithmic flops (110 per pair-term) of the
@@ -372,6 +408,7 @@ def roofline_of(name, m, steps, dev, sm_max):
                 pair_terms_per_launch=m["pairs_per_step"] / 2,
                 pair_kernel_ms_per_launch=pair_ms / max(pair_n, 1),
                 pair_terms_per_s_in_kernel=terms / (pair_ms / 1e3) if pair_ms > 0 else None,
+                bounds=pair_bounds(m["flat"], m["pairs_per_step"] / 2, peak),
                 phases_ms_per_step={k: v[0] / steps for k, v in m["prof"].items()})
 
 

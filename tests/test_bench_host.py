@@ -40,3 +40,16 @@ def test_traffic_record_is_well_formed():
         assert ent["bytes_per_launch"] == ent["read"] + ent["write"] > 0
         assert "--clock-control none" in ent["command"] and "-c 1" in ent["command"]
         assert len(ent["source_sha256"]) == 64
+
+
+def test_both_roofline_bounds():
+    import numpy as np
+    assert bench.label_row_bytes(19, 1) == 48 and bench.label_row_bytes(19, 0) == 80
+    assert bench.label_row_bytes(0, 0) == 0 and bench.label_row_bytes(4, 0) == 16
+    flat = dict(n_points=np.array([100, 200, 300]), edges=np.array([[0, 1], [1, 2]]), sem_dim=19,
+                P=dict(sem_bf16=1), color=False)
+    b = bench.pair_bounds(flat, 1e6, 80.0)
+    assert b["algorithmic_bytes_per_launch"] == (300 + 500) * (16 + 48)
+    assert abs(b["fp32_pair_terms_per_s"] - 80e12 / bench.FLOPS_PER_PAIR) < 1.0
+    assert b["hbm_pair_terms_per_s"] == 1e6 / (b["algorithmic_bytes_per_launch"] / (b["hbm_gbs"] * 1e9))
+    assert b["lower"] in ("fp32", "hbm")
