@@ -353,8 +353,9 @@ def measure_device(pk, rb, prob, steps, warmup, dev, stream, flush, world=1, clo
 
 
 def measured_hbm_gbs():
-    """The measured copy bandwidth of the GB300s (MEASURED_PEAKS.json),
-    else the profiling recipe's fallback figure, and which one it is."""
+    """The measured copy bandwidth of the GB300 (MEASURED_PEAKS.json, a
+    STREAM-style copy), else 6.8 TB/s from an earlier copy measurement on a
+    GB300, and which of the two it is."""
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
             return float(json.load(fh)["hbm_gbs"]), "measured"
@@ -759,7 +760,7 @@ def main():
     ap.add_argument("--unit-queries", type=int, default=0,
                     help="measure this unit size (queries per warp unit) instead of autotuning")
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(WORKLOADS),
-                    help="other workloads of the paper's shapes (the driver uses the default)")
+                    help="other workloads of the paper's shapes (the default is the headline workload)")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
